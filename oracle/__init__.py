@@ -1,0 +1,217 @@
+"""CPU oracle for integer-pel block matching (FSBM and ACBM).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the independent, slow, plain-C
+reference (``me_oracle.c``) that the CUDA library is checked against.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import this package; the library in ``paper_0710_4819_gb300``
+never does, and shares no code with it.
+
+The functions here only marshal numpy arrays into the C functions; every step
+of the computation is in ``me_oracle.c`` (see its header for the paper
+sections each part follows).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "me_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libme_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class AcbmParams(ctypes.Structure):
+    """alpha, beta, gamma = gamma_num/gamma_den, Qp and refinement switch (Sec. 3.2)."""
+
+    _fields_ = [
+        ("alpha", ctypes.c_int32),
+        ("beta", ctypes.c_int32),
+        ("gamma_num", ctypes.c_int32),
+        ("gamma_den", ctypes.c_int32),
+        ("qp", ctypes.c_int32),
+        ("refine", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-Wall", "-Wextra",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i16p = ctypes.POINTER(ctypes.c_int16)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        c_int, c_u32 = ctypes.c_int, ctypes.c_uint32
+        lib.oracle_lambda_q8.argtypes = [c_int]
+        lib.oracle_lambda_q8.restype = c_u32
+        lib.oracle_mv_bits.argtypes = [c_int]
+        lib.oracle_mv_bits.restype = c_int
+        lib.oracle_intra_sad.argtypes = [u8p, c_int, c_int, c_int, c_int, u32p]
+        lib.oracle_intra_sad.restype = c_int
+        lib.oracle_fsbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                    i16p, u32p, u32p, c_int]
+        lib.oracle_fsbm.restype = c_int
+        lib.oracle_fsbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                           i32p, c_int, i16p, u32p, u32p, c_int]
+        lib.oracle_fsbm_blocks.restype = c_int
+        prm_p = ctypes.POINTER(AcbmParams)
+        lib.oracle_acbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                    i16p, prm_p, i16p, u32p, u8p, u32p, u32p]
+        lib.oracle_acbm.restype = c_int
+        lib.oracle_acbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                           i16p, i16p, prm_p, i32p, c_int, i16p, u32p, u8p,
+                                           u32p, u32p]
+        lib.oracle_acbm_blocks.restype = c_int
+        _lib = lib
+        return lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _ptr(a: np.ndarray | None, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _frame(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    if a.ndim != 2:
+        raise ValueError("frames are 2-D uint8 arrays [H, W]")
+    return a
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise OracleError(f"{what} returned status {st}")
+
+
+def lambda_q8(qp: int) -> int:
+    return int(_load().oracle_lambda_q8(int(qp)))
+
+
+def mv_bits(v: int) -> int:
+    return int(_load().oracle_mv_bits(int(v)))
+
+
+def intra_sad(cur, N: int, M: int) -> np.ndarray:
+    """Scaled Intra_SAD (NM * Intra_SAD) per block, shape [BH, BW] uint32."""
+    cur = _frame(cur)
+    H, W = cur.shape
+    out = np.zeros((max(H // M, 1), max(W // N, 1)), np.uint32)
+    _check(_load().oracle_intra_sad(_ptr(cur, ctypes.c_uint8), W, H, N, M,
+                                    _ptr(out, ctypes.c_uint32)), "oracle_intra_sad")
+    return out
+
+
+def fsbm(cur, ref, N: int, M: int, p: int, lam_q8: int, nthreads: int = 1):
+    """Full search.  Returns (mv [BH,BW,2] int16, J [BH,BW] u32, sad [BH,BW] u32)."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    if ref.shape != cur.shape:
+        raise ValueError("cur and ref differ in shape")
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    mv = np.zeros((BH, BW, 2), np.int16)
+    J = np.zeros((BH, BW), np.uint32)
+    sad = np.zeros((BH, BW), np.uint32)
+    _check(_load().oracle_fsbm(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N, M,
+                               p, lam_q8, _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                               _ptr(sad, ctypes.c_uint32), nthreads), "oracle_fsbm")
+    return mv, J, sad
+
+
+def fsbm_blocks(cur, ref, N: int, M: int, p: int, lam_q8: int, blocks, nthreads: int = 1):
+    """Full search for the listed block indices (by*BW+bx). Returns (mv [k,2], J [k], sad [k])."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    k = blocks.size
+    mv = np.zeros((k, 2), np.int16)
+    J = np.zeros(k, np.uint32)
+    sad = np.zeros(k, np.uint32)
+    _check(_load().oracle_fsbm_blocks(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H,
+                                      N, M, p, lam_q8, _ptr(blocks, ctypes.c_int32), k,
+                                      _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                                      _ptr(sad, ctypes.c_uint32), nthreads),
+           "oracle_fsbm_blocks")
+    return mv, J, sad
+
+
+def params(alpha=1000, beta=8, gamma_num=1, gamma_den=4, qp=28, refine=1) -> AcbmParams:
+    """The paper's defaults alpha=1000, beta=8, gamma=1/4 (Sec. 4)."""
+    return AcbmParams(int(alpha), int(beta), int(gamma_num), int(gamma_den), int(qp), int(refine))
+
+
+def acbm(cur, ref, N: int, M: int, p: int, lam_q8: int, prm: AcbmParams, prev_mv=None):
+    """ACBM over a frame.  Returns (mv, J, mask, sad, load), block-grid shaped."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    if prev_mv is not None:
+        prev_mv = np.ascontiguousarray(prev_mv, dtype=np.int16)
+        if prev_mv.shape != (BH, BW, 2):
+            raise ValueError("prev_mv must be [BH, BW, 2] int16")
+    mv = np.zeros((BH, BW, 2), np.int16)
+    J = np.zeros((BH, BW), np.uint32)
+    mask = np.zeros((BH, BW), np.uint8)
+    sad = np.zeros((BH, BW), np.uint32)
+    load = np.zeros((BH, BW), np.uint32)
+    _check(_load().oracle_acbm(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N, M, p,
+                               lam_q8, _ptr(prev_mv, ctypes.c_int16), ctypes.byref(prm),
+                               _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                               _ptr(mask, ctypes.c_uint8), _ptr(sad, ctypes.c_uint32),
+                               _ptr(load, ctypes.c_uint32)), "oracle_acbm")
+    return mv, J, mask, sad, load
+
+
+def acbm_blocks(cur, ref, N: int, M: int, p: int, lam_q8: int, prm: AcbmParams, cur_field,
+                blocks, prev_mv=None):
+    """ACBM for the listed blocks, with spatial predictors read from cur_field."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    cur_field = np.ascontiguousarray(cur_field, dtype=np.int16)
+    if cur_field.shape != (BH, BW, 2):
+        raise ValueError("cur_field must be [BH, BW, 2] int16")
+    if prev_mv is not None:
+        prev_mv = np.ascontiguousarray(prev_mv, dtype=np.int16)
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    k = blocks.size
+    mv = np.zeros((k, 2), np.int16)
+    J = np.zeros(k, np.uint32)
+    mask = np.zeros(k, np.uint8)
+    sad = np.zeros(k, np.uint32)
+    load = np.zeros(k, np.uint32)
+    _check(_load().oracle_acbm_blocks(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H,
+                                      N, M, p, lam_q8, _ptr(prev_mv, ctypes.c_int16),
+                                      _ptr(cur_field, ctypes.c_int16), ctypes.byref(prm),
+                                      _ptr(blocks, ctypes.c_int32), k, _ptr(mv, ctypes.c_int16),
+                                      _ptr(J, ctypes.c_uint32), _ptr(mask, ctypes.c_uint8),
+                                      _ptr(sad, ctypes.c_uint32), _ptr(load, ctypes.c_uint32)),
+           "oracle_acbm_blocks")
+    return mv, J, mask, sad, load

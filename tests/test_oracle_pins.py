@@ -1,0 +1,407 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, independent of the oracle's own code.
+
+* eq. J / eq. SAD (Sec. 2.1) and FSBM (Sec. 2.3): brute force over the whole
+  SAD volume in numpy (sliding windows, lexicographic argmin) on tiny frames,
+  exact recovery of an integer shift, tie-break adversaries.
+* R(mv): the code lengths come from an Exp-Golomb encoder built bit by bit and
+  checked to decode back (a prefix code), not from a length formula.
+* eq. Intra_SAD (Sec. 3.1): exact rational mean (fractions.Fraction) and the
+  closed forms for flat and two-level blocks.
+* ACBM (Sec. 3.2): each stopping condition at its equality boundary (strict
+  "<"), forced / suppressed full search, and probes that show which
+  neighbouring vectors the PBM stage uses (Sec. 2.2, Fig. 2).
+* Constants printed in the paper: alpha, beta, gamma (Sec. 4) and the
+  961 + 8 = 969 FSBM positions at p = 15 (Sec. 2.3, Sec. 4).
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def eg_encode_signed(v: int) -> str:
+    """Signed Exp-Golomb code as a bit string, built constructively."""
+    k = 2 * v - 1 if v > 0 else -2 * v
+    info = bin(k + 1)[2:]               # '1' followed by the info bits
+    return "0" * (len(info) - 1) + info
+
+
+def eg_decode_stream(bits: str) -> list[int]:
+    out, i = [], 0
+    while i < len(bits):
+        z = 0
+        while bits[i] == "0":
+            z += 1
+            i += 1
+        k = int(bits[i:i + z + 1], 2) - 1
+        i += z + 1
+        out.append((k + 1) // 2 if k % 2 == 1 else -(k // 2))
+    return out
+
+
+def brute_fsbm(cur, ref, N, M, p, lam):
+    """Whole SAD volume by sliding windows over an edge-padded reference,
+    then a lexicographic argmin (J, |mv|_1, mvy, mvx)."""
+    H, W = cur.shape
+    BH, BW = H // M, W // N
+    rp = np.pad(ref.astype(np.int64), p, mode="edge")
+    c = cur.astype(np.int64)
+    n = 2 * p + 1
+    vol = np.zeros((n, n, BH, BW), np.int64)
+    for a in range(n):
+        for b in range(n):
+            sh = rp[a:a + H, b:b + W]          # ref(x + mvx, y + mvy), mvy = a - p, mvx = b - p
+            vol[a, b] = np.abs(c - sh).reshape(BH, M, BW, N).sum(axis=(1, 3))
+    mvs = np.arange(-p, p + 1)
+    bits = np.array([len(eg_encode_signed(int(v))) for v in mvs], np.int64)
+    R = bits[:, None] + bits[None, :]         # [mvy, mvx]
+    J = 256 * vol + lam * R[:, :, None, None]
+    MY, MX = np.meshgrid(mvs, mvs, indexing="ij")
+    L1 = np.abs(MY) + np.abs(MX)
+    mv = np.zeros((BH, BW, 2), np.int64)
+    Jb = np.zeros((BH, BW), np.int64)
+    Sb = np.zeros((BH, BW), np.int64)
+    for by in range(BH):
+        for bx in range(BW):
+            j = J[:, :, by, bx].ravel()
+            order = np.lexsort((MX.ravel(), MY.ravel(), L1.ravel(), j))
+            k = order[0]
+            mv[by, bx] = (MX.ravel()[k], MY.ravel()[k])
+            Jb[by, bx] = j[k]
+            Sb[by, bx] = vol[:, :, by, bx].ravel()[k]
+    return mv, Jb, Sb
+
+
+def per_block_motion(ref, N, M, disp):
+    """cur block b = ref moved by disp[by, bx] (edge clamp): SAD 0 at mv = -disp."""
+    H, W = ref.shape
+    cur = np.empty_like(ref)
+    for by in range(H // M):
+        for bx in range(W // N):
+            dx, dy = disp[by][bx]
+            sh = synth.shifted_copy(ref, dx, dy)
+            cur[by * M:(by + 1) * M, bx * N:(bx + 1) * N] = sh[by * M:(by + 1) * M,
+                                                                bx * N:(bx + 1) * N]
+    return cur
+
+
+# ----------------------------------------------------------------- lambda, R
+def test_lambda_is_092_qp_in_q8(orc):
+    for qp in range(0, 1024):
+        exact = Fraction(92, 100) * qp * 256
+        got = orc.lambda_q8(qp)
+        assert abs(Fraction(got) - exact) <= Fraction(1, 2)
+        # round half up
+        assert got == int(exact + Fraction(1, 2))
+    assert [orc.lambda_q8(q) for q in (22, 28, 34, 40)] == [5181, 6595, 8008, 9421]
+
+
+def test_mv_bits_match_exp_golomb_encoder(orc):
+    vals = list(range(-300, 301))
+    for v in vals:
+        assert orc.mv_bits(v) == len(eg_encode_signed(v)), v
+    rng = np.random.default_rng(3)
+    seq = [int(x) for x in rng.integers(-70, 71, size=500)]
+    assert eg_decode_stream("".join(eg_encode_signed(v) for v in seq)) == seq
+    assert [orc.mv_bits(v) for v in (0, 1, -1, 2, 3, -3, 4, 7, 8, 15, 16)] == \
+        [1, 3, 3, 5, 5, 5, 7, 7, 9, 9, 11]
+
+
+# ----------------------------------------------------------------- Intra_SAD
+@pytest.mark.parametrize("N,M", [(16, 16), (8, 4), (4, 16)])
+def test_intra_sad_exact_rational_mean(orc, N, M):
+    rng = np.random.default_rng(N * 31 + M)
+    cur = rng.integers(0, 256, size=(3 * M, 2 * N), dtype=np.uint8)
+    got = orc.intra_sad(cur, N, M)
+    for by in range(3):
+        for bx in range(2):
+            blk = [int(v) for v in cur[by * M:(by + 1) * M, bx * N:(bx + 1) * N].ravel()]
+            mu = Fraction(sum(blk), len(blk))
+            intra = sum(abs(Fraction(v) - mu) for v in blk)
+            assert Fraction(int(got[by, bx]), N * M) == intra
+
+
+def test_intra_sad_closed_forms(orc):
+    flat = np.full((16, 16), 93, np.uint8)
+    assert orc.intra_sad(flat, 16, 16)[0, 0] == 0
+    a, b = 100, 110
+    two = np.full((16, 16), a, np.uint8)
+    two[:, 8:] = b
+    # half the pixels a, half b: mean (a+b)/2, Intra_SAD = NM*|a-b|/2
+    assert orc.intra_sad(two, 16, 16)[0, 0] == 256 * (256 * abs(a - b) // 2)
+
+
+# ----------------------------------------------------------------- FSBM
+@pytest.mark.parametrize("W,H,N,M,p", [
+    (32, 32, 16, 16, 1), (32, 32, 16, 16, 3), (48, 32, 16, 16, 4),
+    (32, 32, 8, 8, 2), (48, 32, 8, 16, 3), (32, 32, 4, 4, 2), (24, 16, 4, 8, 4),
+])
+def test_fsbm_matches_brute_force(orc, W, H, N, M, p):
+    for trial, lam in enumerate([0, 3000, 6595, 120000]):
+        rng = np.random.default_rng(1000 * p + 10 * N + trial)
+        if trial % 2 == 0:
+            ref = synth.texture(rng, W, H)
+            cur = synth.shifted_copy(ref, int(rng.integers(-3, 4)), int(rng.integers(-3, 4)))
+            cur = np.clip(cur.astype(int) + rng.integers(-3, 4, size=cur.shape), 0, 255)
+        else:
+            ref = rng.integers(0, 256, size=(H, W))
+            cur = rng.integers(0, 256, size=(H, W))
+        cur, ref = cur.astype(np.uint8), ref.astype(np.uint8)
+        mv, J, sad = orc.fsbm(cur, ref, N, M, p, lam)
+        bmv, bJ, bS = brute_fsbm(cur, ref, N, M, p, lam)
+        assert np.array_equal(mv, bmv)
+        assert np.array_equal(J, bJ)
+        assert np.array_equal(sad, bS)
+
+
+def test_fsbm_threads_do_not_change_result(orc):
+    rng = np.random.default_rng(5)
+    ref = synth.texture(rng, 64, 48)
+    cur = synth.shifted_copy(ref, 2, -1)
+    a = orc.fsbm(cur, ref, 16, 16, 5, 6595, nthreads=1)
+    b = orc.fsbm(cur, ref, 16, 16, 5, 6595, nthreads=4)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("dx,dy", [(3, -2), (-5, 1), (0, 4), (2, 2)])
+def test_fsbm_recovers_exact_shift(orc, dx, dy):
+    ref = synth.random_frame(11, 64, 48)
+    cur = synth.shifted_copy(ref, dx, dy)
+    mv, J, sad = orc.fsbm(cur, ref, 16, 16, 6, 0)
+    assert np.all(mv[..., 0] == -dx) and np.all(mv[..., 1] == -dy)
+    assert np.all(sad == 0) and np.all(J == 0)
+    # the rate term does not move a zero-SAD match on sharp texture
+    mv2, J2, _ = orc.fsbm(cur, ref, 16, 16, 6, orc.lambda_q8(28))
+    assert np.array_equal(mv, mv2)
+    assert np.all(J2 == orc.lambda_q8(28) * (len(eg_encode_signed(-dx)) +
+                                             len(eg_encode_signed(-dy))))
+
+
+def test_fsbm_tie_breaks(orc):
+    # constant frames: every SAD is equal, so J is smallest at (0,0)
+    c = np.full((32, 32), 50, np.uint8)
+    r = np.full((32, 32), 60, np.uint8)
+    mv, J, sad = orc.fsbm(c, r, 16, 16, 4, 0)
+    assert np.all(mv == 0) and np.all(sad == 256 * 10)
+    # horizontal period 4, vertically constant, content moved by 2: SAD 0 at
+    # mvx = +-2 (and +-6) for every mvy; smallest |mv|_1 leaves (-2,0),(2,0);
+    # the raster order (smaller mvy, then smaller mvx) picks (-2,0)
+    pat = np.array([10, 200, 60, 140], np.uint8)
+    ref = np.tile(pat, (48, 16))[:, :64]
+    cur = np.roll(ref, 2, axis=1)
+    mv, J, sad = orc.fsbm(cur, ref, 16, 16, 6, 0)
+    assert tuple(mv[1, 1]) == (-2, 0) and tuple(mv[1, 2]) == (-2, 0)
+    assert sad[1, 1] == 0
+    # the same pattern vertically: (0,-2) wins over (0,2)
+    refv = ref.T.copy()
+    curv = np.roll(refv, 2, axis=0)
+    mv, J, sad = orc.fsbm(curv, refv, 16, 16, 6, 0)
+    assert tuple(mv[1, 1]) == (0, -2) and tuple(mv[2, 1]) == (0, -2)
+    # rate decides between equal SADs when lambda > 0: (2,0) and (-2,0) cost
+    # the same, (-2,0) still wins by raster; with lambda both beat (+-6,0)
+    mv, J, sad = orc.fsbm(cur, ref, 16, 16, 6, 6595)
+    assert tuple(mv[1, 1]) == (-2, 0)
+
+
+def test_fsbm_rejects_bad_shapes(orc):
+    c = np.zeros((32, 32), np.uint8)
+    with pytest.raises(orc.OracleError):
+        orc.fsbm(c[:, :30], c[:, :30], 16, 16, 2, 0)    # W % N != 0
+    with pytest.raises(orc.OracleError):
+        orc.fsbm(c, c, 16, 16, 0, 0)                    # p < 1
+    with pytest.raises(orc.OracleError):
+        orc.fsbm(c, c, 12, 16, 2, 0)                    # N not in {4,8,16}
+
+
+# ----------------------------------------------------------------- paper constants
+def test_paper_constants(orc):
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        g = json.load(f)
+    d = orc.params()
+    assert (d.alpha, d.beta, d.gamma_num, d.gamma_den) == (
+        g["acbm_defaults"]["alpha"], g["acbm_defaults"]["beta"],
+        g["acbm_defaults"]["gamma_num"], g["acbm_defaults"]["gamma_den"])
+    fp = g["fsbm_positions"]
+    assert fp["integer_positions"] + fp["half_pel_positions"] == fp["total_positions"]
+    # a forced full search at p = 15 evaluates the 961 integer positions of the
+    # paper's 969 (the 8 half-pel ones are outside the integer-pel search)
+    ref = synth.random_frame(2, 32, 32)
+    cur = synth.shifted_copy(ref, 1, 1)
+    _, _, mask, _, load = orc.acbm(cur, ref, 16, 16, fp["p"], 0,
+                                   orc.params(alpha=0, beta=0, gamma_num=0))
+    assert np.all(mask == 1) and np.all(load == fp["integer_positions"])
+
+
+# ----------------------------------------------------------------- ACBM conditions
+def _single(orc, cur, ref, prm, p=1):
+    return orc.acbm(cur, ref, 16, 16, p, 0, prm)
+
+
+def test_acbm_cond1_strict_and_scaled(orc):
+    cur = np.full((16, 16), 101, np.uint8)
+    ref = np.full((16, 16), 100, np.uint8)   # Intra_SAD 0, SAD_PBM = 256
+    # cond 1: 0 + 256 < alpha + beta*Qp^2 (gamma 0 switches cond 2 off)
+    for alpha, expect_fs in [(256, 1), (257, 0)]:
+        _, _, mask, sad, load = _single(orc, cur, ref, orc.params(alpha, 0, 0, 1, 28, 0))
+        assert mask[0, 0] == expect_fs and sad[0, 0] == 256
+        assert load[0, 0] == (9 if expect_fs else 1)
+    for qp, expect_fs in [(16, 1), (17, 0)]:       # 256 < Qp^2 with beta = 1
+        _, _, mask, _, _ = _single(orc, cur, ref, orc.params(0, 1, 0, 1, qp, 0))
+        assert mask[0, 0] == expect_fs
+    # Intra_SAD enters unscaled: two-level block has Intra_SAD = 1280
+    two = np.full((16, 16), 100, np.uint8)
+    two[:, 8:] = 110
+    ref2 = two + 1
+    for alpha, expect_fs in [(1536, 1), (1537, 0)]:
+        _, _, mask, sad, _ = _single(orc, two, ref2, orc.params(alpha, 0, 0, 1, 28, 0))
+        assert sad[0, 0] == 256 or expect_fs
+        assert mask[0, 0] == expect_fs
+
+
+def test_acbm_cond2_strict_and_scaled(orc):
+    two = np.full((16, 16), 100, np.uint8)
+    two[:, 8:] = 110                         # Intra_SAD = 1280; gamma*Intra = 320
+    for k, expect_fs in [(64, 1), (63, 0)]:
+        ref = two.astype(np.int32) + 1
+        ref.ravel()[:k] += 1                 # SAD_PBM at (0,0) = 256 + k
+        ref = ref.astype(np.uint8)
+        _, _, mask, _, _ = _single(orc, two, ref, orc.params(0, 0, 1, 4, 28, 0))
+        assert mask[0, 0] == expect_fs, k
+
+
+# ----------------------------------------------------------------- ACBM invariants
+def _acbm_inputs(seed, W=96, H=64):
+    seq = synth.scene_sequence(seed, W, H, 3, n_objects=3, vmax=4)
+    return seq
+
+
+@pytest.mark.parametrize("N,M,p", [(16, 16, 4), (8, 8, 3), (16, 8, 5)])
+def test_acbm_forced_fs_equals_fsbm(orc, N, M, p):
+    seq = _acbm_inputs(N + M + p)
+    lam = orc.lambda_q8(28)
+    mv, J, sad = orc.fsbm(seq[1], seq[0], N, M, p, lam)
+    amv, aJ, mask, asad, load = orc.acbm(seq[1], seq[0], N, M, p, lam,
+                                         orc.params(alpha=0, beta=0, gamma_num=0))
+    assert np.array_equal(mv, amv) and np.array_equal(J, aJ) and np.array_equal(sad, asad)
+    assert np.all(mask == 1) and np.all(load == (2 * p + 1) ** 2)
+
+
+def test_acbm_invariants_on_a_sequence(orc):
+    seq = _acbm_inputs(77, 128, 96)
+    lam = orc.lambda_q8(28)
+    prev = None
+    for t in range(1, seq.shape[0]):
+        for prm in [orc.params(), orc.params(refine=0), orc.params(alpha=2 ** 30)]:
+            mv, J, sad = orc.fsbm(seq[t], seq[t - 1], 16, 16, 8, lam)
+            amv, aJ, mask, asad, load = orc.acbm(seq[t], seq[t - 1], 16, 16, 8, lam, prm, prev)
+            assert np.all(J <= aJ)                                   # FSBM optimal
+            fs = mask == 1
+            assert np.array_equal(amv[fs], mv[fs]) and np.array_equal(aJ[fs], J[fs])
+            assert np.all(load[fs] == 17 * 17)
+            cap = 22 if prm.refine else 14
+            assert np.all((load[~fs] >= 1) & (load[~fs] <= cap))
+            if prm.alpha == 2 ** 30:
+                assert not fs.any()
+        prev = orc.acbm(seq[t], seq[t - 1], 16, 16, 8, lam, orc.params(), prev)[0]
+
+
+# ----------------------------------------------------------------- ACBM predictor probes
+D = (4, -3)          # probed block's motion; its match is at mv = (-4, 3)
+U = (-3, 4)          # everybody else; match at (3, -4)
+MARK = (5, 5)        # previous-field marker far from both matches and from 0
+P6 = 6
+CFG = dict(alpha=0, beta=0, gamma_num=1, gamma_den=4, qp=28, refine=1)   # cond 2 only
+
+
+def _probe(orc, disp, prev, W=80, H=48):
+    ref = synth.random_frame(99, W, H)
+    cur = per_block_motion(ref, 16, 16, disp)
+    return orc.acbm(cur, ref, 16, 16, P6, 0, orc.params(**CFG), prev)
+
+
+def _field(val, BW=5, BH=3):
+    f = np.zeros((BH, BW, 2), np.int16)
+    f[..., 0], f[..., 1] = val
+    return f
+
+
+@pytest.mark.parametrize("nb,helps", [
+    ((1, 1), True), ((1, 0), True), ((2, 0), True), ((3, 0), True),   # left, up-left, up, up-right
+    ((0, 0), False), ((4, 0), False), ((0, 1), False), ((3, 1), False), ((2, 2), False),
+])
+def test_pbm_spatial_predictors(orc, nb, helps):
+    """Block (2,1) moves by D, all others by U except neighbour nb (also D).
+    The block finds its match without full search only through a spatial
+    predictor that is computed before it (Sec. 2.2: mv5_t..mv8_t are not)."""
+    disp = [[U] * 5 for _ in range(3)]
+    disp[1][2] = D
+    disp[nb[1]][nb[0]] = D
+    mv, J, mask, sad, load = _probe(orc, disp, _field(MARK))
+    assert tuple(mv[1, 2]) == (-D[0], -D[1]) and sad[1, 2] == 0
+    assert mask[1, 2] == (0 if helps else 1)
+
+
+@pytest.mark.parametrize("off,helps", [((dx, dy), True) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+                         + [((2, 0), False), ((-2, 0), False), ((2, 1), False), ((-2, -1), False)])
+def test_pbm_temporal_predictors(orc, off, helps):
+    """Block (2,1) moves by D, all others by U; the previous field holds the
+    right vector only at (2,1)+off: it helps exactly for the 3x3 neighbourhood."""
+    disp = [[U] * 5 for _ in range(3)]
+    disp[1][2] = D
+    prev = _field(MARK)
+    prev[1 + off[1], 2 + off[0]] = (-D[0], -D[1])
+    mv, J, mask, sad, load = _probe(orc, disp, prev)
+    assert tuple(mv[1, 2]) == (-D[0], -D[1])
+    assert mask[1, 2] == (0 if helps else 1)
+
+
+def test_pbm_zero_predictor_and_ring(orc):
+    # block (0,0) still: only the zero predictor finds it
+    disp = [[U] * 5 for _ in range(3)]
+    disp[0][0] = (0, 0)
+    mv, J, mask, sad, load = _probe(orc, disp, _field(MARK))
+    assert mask[0, 0] == 0 and tuple(mv[0, 0]) == (0, 0)
+    # motion (1,-1) with a zero previous field: the only predictor of block
+    # (0,0) is (0,0), and the +-1 ring around it reaches the match (-1,1)
+    disp[0][0] = (1, -1)
+    mv, J, mask, sad, load = _probe(orc, disp, None)
+    assert mask[0, 0] == 0 and tuple(mv[0, 0]) == (-1, 1) and load[0, 0] == 9
+    ref = synth.random_frame(99, 80, 48)
+    cur = per_block_motion(ref, 16, 16, disp)
+    prm = orc.params(**dict(CFG, refine=0))
+    mv, J, mask, sad, load = orc.acbm(cur, ref, 16, 16, P6, 0, prm, None)
+    assert mask[0, 0] == 1 and tuple(mv[0, 0]) == (-1, 1)
+
+
+def test_pbm_load_counts_distinct_positions(orc):
+    """Flat frames: every SAD is 0, the winner is (0,0), so the load is the
+    number of distinct predictors plus the new ring positions."""
+    W, H, BW, BH = 80, 48, 5, 3
+    flat = np.full((H, W), 77, np.uint8)
+    prev = np.zeros((BH, BW, 2), np.int16)
+    for by in range(BH):
+        for bx in range(BW):
+            prev[by, bx] = (by * BW + bx - 7, 8)     # 15 distinct markers, far from 0
+    nbrs = np.array([[sum(1 for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                          if 0 <= bx + dx < BW and 0 <= by + dy < BH)
+                      for bx in range(BW)] for by in range(BH)])
+    _, _, mask, _, load = orc.acbm(flat, flat, 16, 16, 8, 0, orc.params(), prev)
+    assert np.all(mask == 0)
+    assert np.array_equal(load, 9 + nbrs)                      # 13 / 15 / 18
+    _, _, _, _, load0 = orc.acbm(flat, flat, 16, 16, 8, 0, orc.params(refine=0), prev)
+    assert np.array_equal(load0, 1 + nbrs)
+    # markers beyond p are clipped to the window edge and then counted once
+    far = np.zeros((BH, BW, 2), np.int16)
+    far[..., 0] = 30
+    far[0, 0] = (20, 0)
+    _, _, _, _, load1 = orc.acbm(flat, flat, 16, 16, 8, 0, orc.params(refine=0), far)
+    assert np.all(load1 == 2)                                  # (0,0) and (8,0)
