@@ -1,0 +1,143 @@
+/*
+ * me.h -- C ABI of the GB300 (sm_103a) block-matching motion-estimation
+ * library: integer-pel full search (FSBM) and adaptive cost block matching
+ * (ACBM) after Lopez, Callico, Lopez and Sarmiento, "A High Quality/Low
+ * Computational Cost Technique for Block Matching Motion Estimation".
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Frames: 8-bit luma, row-major, W columns by H rows, pitch W bytes.
+ * Blocks: N x M pixels with N the width and M the height (the SAD of Sec. 2.1
+ *   sums i < N with i paired with mvx).  N, M in {4, 8, 16}; W % N == 0 and
+ *   H % M == 0 (the caller pads, e.g. 1080 -> 1088 rows).  BW = W/N blocks
+ *   per row, BH = H/M block rows; per-block outputs are [BH][BW] row-major.
+ * Search range: mv in [-p, p]^2, 1 <= p <= 64.  A reference pixel outside
+ *   the frame takes the value of the nearest edge pixel.
+ * Motion vectors: int16 pairs (mvx, mvy), [BH][BW][2].  The candidate block
+ *   of mv is ref(x0+i+mvx, y0+j+mvy): content that moved right by d is
+ *   matched at mvx = -d.
+ * Cost (Sec. 2.1, eq. J): J = SAD + lambda*R, carried in Q8 fixed point as
+ *   J_q8 = 256*SAD + lambda_q8*R, R(mv) = L(mvx) + L(mvy), L = length of the
+ *   signed Exp-Golomb code of a component (1, 3, 3, 5, 5, 5, 5, 7, ...).
+ *   lambda_q8 <= 2^20.  Ties: lowest J_q8, then smallest |mvx|+|mvy|, then
+ *   smaller mvy, then smaller mvx -- one exact answer per block.
+ * Pointers: every array argument of the frame calls is a DEVICE pointer of the
+ *   current device, owned by the caller; "nullable" outputs may be NULL.
+ *   Frame pointers (cur, ref) must be 4-byte aligned.  Work is enqueued on
+ *   `stream` (a cudaStream_t; NULL = legacy default stream) and the call
+ *   returns without waiting unless stated.  Scratch memory, where a call needs
+ *   it, comes from a library-owned stream-ordered pool of the current device
+ *   (allocated and released on `stream`, cached between calls).
+ * Errors: every call returns an me_status; on ME_ERR_ARG / ME_ERR_SHAPE
+ *   nothing was enqueued.  ME_ERR_CUDA reports a failed CUDA call (the text
+ *   of the last one is available from me_last_error()).
+ * Threads: the frame calls may be used from several host threads at once;
+ *   a batch or server object belongs to one host thread at a time.
+ */
+#ifndef ME_H_
+#define ME_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *me_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    ME_OK = 0,
+    ME_ERR_ARG = 1,      /* NULL pointer, N/M/p/lambda/params out of range */
+    ME_ERR_SHAPE = 2,    /* W % N or H % M nonzero, or W/H out of range     */
+    ME_ERR_CUDA = 3,     /* a CUDA call failed                               */
+    ME_ERR_NOMEM = 4,    /* device or host allocation failed / over budget   */
+    ME_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                    */
+    ME_ERR_BUSY = 6,     /* request not finished yet / queue full            */
+    ME_ERR_NOTFOUND = 7  /* unknown stream or request id                     */
+} me_status;
+
+/* Text for a status code (static storage). */
+const char *me_status_string(int status);
+/* Text of the last CUDA error seen by this host thread ("" if none). */
+const char *me_last_error(void);
+
+/* ----------------------------------------------------------------- cost */
+
+/* lambda of eq. J, "proportional to Qp" (Sec. 2.1); read as 0.92*Qp and
+ * returned in Q8: (23552*qp + 50) / 100.  qp in [0, 1023], else 0. */
+uint32_t me_lambda_q8(int32_t qp);
+
+/* L(v): bits of the signed Exp-Golomb code of one MV component (the R term of
+ * eq. J is L(mvx) + L(mvy)).  Any int16 v. */
+int32_t me_mv_bits(int32_t v);
+
+/* ACBM parameters (Sec. 3.2).  cond. 1: Intra_SAD + SAD_PBM < alpha + beta*qp^2;
+ * cond. 2: SAD_PBM < (gamma_num/gamma_den)*Intra_SAD; both tested in exact
+ * integers.  refine = 1 adds the +-1 integer ring around the best predictor
+ * (Sec. 2.2, third PBM step), 0 skips it.  Valid: gamma_den >= 1,
+ * gamma_num >= 0, qp in [0, 1023], refine in {0, 1}. */
+typedef struct {
+    int32_t alpha, beta, gamma_num, gamma_den;
+    int32_t qp;
+    int32_t refine;
+} me_acbm_params;
+
+/* The paper's choice alpha = 1000, beta = 8, gamma = 1/4 (Sec. 4), refine 1. */
+me_acbm_params me_acbm_default_params(int32_t qp);
+
+/* ----------------------------------------------------------------- frame calls */
+
+/* Edge-clamped copy of a reference frame with a margin of P = 16*ceil(p/16)
+ * pixels on every side, laid out with a 16-byte aligned pitch
+ * (the first step of every search; exposed for tests).  out[(y+P)*pitch + x+P]
+ * = ref[clamp(y)*W + clamp(x)] for y in [-P, H+P), x in [-P, pitch-P).
+ * me_padded_geometry gives pitch, rows = H + 2P, and P.  out must hold
+ * pitch*rows bytes. */
+int me_padded_geometry(int W, int H, int p, int *pitch, int *rows, int *P);
+int me_pad_ref(const uint8_t *ref, int W, int H, int p, uint8_t *out, me_stream_t stream);
+
+/* Scaled Intra_SAD of every block (Sec. 3.1, eq. Intra_SAD):
+ * out[b] = sum |N*M*pix - S| = N*M*Intra_SAD with S the block sum, so the
+ * block mean needs no rounding.  out is [BH][BW] uint32. */
+int me_intra_sad(const uint8_t *cur, int W, int H, int N, int M, uint32_t *out,
+                 me_stream_t stream);
+
+/* FSBM (Sec. 2.3): for each block the minimum of J over all (2p+1)^2 integer
+ * positions.  mv_out [BH][BW][2], J_out [BH][BW] (J_q8), sad_out [BH][BW]
+ * (nullable).  One kernel launch; no scratch memory. */
+int me_fsbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+            uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
+            me_stream_t stream);
+
+/* ACBM (Sec. 3.2) for one frame pair.  Per block: Intra_SAD, then PBM over the
+ * predictors (final vectors of the left, up-left, up and up-right blocks of
+ * this frame; the 3x3 blocks around it in prev_mv_field; (0,0)), each clipped
+ * to [-p,p] and evaluated once, best by J, then the +-1 ring; then cond. 1 /
+ * cond. 2; a block meeting neither gets the full search.
+ * prev_mv_field [BH][BW][2] is the previous frame's output (NULL = zeros).
+ * Outputs: mv_out, J_out, fullsearch_mask_out (1 = full search ran),
+ * sad_out (nullable), load_out (nullable; distinct positions evaluated,
+ * (2p+1)^2 for a full-searched block).  The blocks are processed as
+ * anti-diagonal waves x + 2y = w so every predictor is final when read.
+ * Scratch (stream-ordered pool): the padded reference plus 4 bytes per block
+ * and per wave, about pitch*rows + 8*BW*BH bytes. */
+int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+            uint32_t lambda_q8, const int16_t *prev_mv_field, const me_acbm_params *prm,
+            int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,
+            uint32_t *load_out, me_stream_t stream);
+
+/* ----------------------------------------------------------------- peak probe */
+
+/* Measures the integer-pipe rate of a packed-SAD instruction form on the
+ * current device with no memory traffic (the roofline denominator of the SAD
+ * kernels).  variant 0: vabsdiff4 with accumulate; 1: per-byte absolute
+ * difference + dp4a byte sum.  Writes absolute differences per second, and
+ * lane-operations per SM clock (from the SM cycle counter).  Synchronous. */
+int me_sad_peak(int variant, double *absdiff_per_s, double *lane_ops_per_clk_per_sm,
+                me_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ME_H_ */

@@ -1,0 +1,281 @@
+"""GB300 (sm_103a) block-matching motion estimation: FSBM and ACBM.
+
+A thin ctypes binding over the C ABI in ``include/me.h`` (``libme.so``).  The
+functions keep the C names (``me_fsbm``, ``me_acbm``, ...) and take torch CUDA
+tensors; this module only checks shapes and dtypes, allocates outputs and
+passes device pointers and the current CUDA stream.  Every step of the
+computation runs in the library's CUDA kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from . import build as _build
+
+__all__ = [
+    "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
+    "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
+    "me_fsbm", "me_acbm", "me_sad_peak", "Batch", "STATUS",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ME_OK", 1: "ME_ERR_ARG", 2: "ME_ERR_SHAPE", 3: "ME_ERR_CUDA",
+          4: "ME_ERR_NOMEM", 5: "ME_ERR_TIMEOUT", 6: "ME_ERR_BUSY", 7: "ME_ERR_NOTFOUND"}
+
+
+class MeError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = f"{what}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class AcbmParams(ctypes.Structure):
+    """me_acbm_params: alpha, beta, gamma = gamma_num/gamma_den, qp, refine (Sec. 3.2)."""
+
+    _fields_ = [("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("gamma_num", ctypes.c_int32), ("gamma_den", ctypes.c_int32),
+                ("qp", ctypes.c_int32), ("refine", ctypes.c_int32)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("prev_mv", ctypes.c_void_p),
+                ("mv_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
+                ("mask_out", ctypes.c_void_p), ("sad_out", ctypes.c_void_p),
+                ("load_out", ctypes.c_void_p), ("lambda_q8", ctypes.c_uint32),
+                ("prm", AcbmParams)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libme.so (building it first if asked).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"libme.so missing at {path}; run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, c_int, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
+        sig = {
+            "me_status_string": ([c_int], ctypes.c_char_p),
+            "me_last_error": ([], ctypes.c_char_p),
+            "me_lambda_q8": ([ctypes.c_int32], u32),
+            "me_mv_bits": ([ctypes.c_int32], ctypes.c_int32),
+            "me_acbm_default_params": ([ctypes.c_int32], AcbmParams),
+            "me_padded_geometry": ([c_int, c_int, c_int, ctypes.POINTER(c_int),
+                                    ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
+            "me_pad_ref": ([vp, c_int, c_int, c_int, vp, vp], c_int),
+            "me_intra_sad": ([vp, c_int, c_int, c_int, c_int, vp, vp], c_int),
+            "me_fsbm": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp], c_int),
+            "me_acbm": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp,
+                         ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
+            "me_sad_peak": ([c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), vp], c_int),
+            "me_batch_create": ([ctypes.POINTER(vp)], c_int),
+            "me_batch_add_stream": ([vp, c_int, c_int, c_int, c_int, c_int,
+                                     ctypes.POINTER(c_int)], c_int),
+            "me_batch_run": ([vp, c_int, ctypes.POINTER(BatchItem), c_int, vp], c_int),
+            "me_batch_sync": ([vp, vp], c_int),
+            "me_batch_destroy": ([vp], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        detail = ""
+        if st == 3:
+            detail = load_library().me_last_error().decode()
+        raise MeError(st, what, detail)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _frame_args(cur, ref):
+    torch = _torch()
+    for t, nm in ((cur, "cur"), (ref, "ref")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8
+                and t.dim() == 2 and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous 2-D uint8 CUDA tensor [H, W]")
+    if cur.shape != ref.shape:
+        raise ValueError("cur and ref differ in shape")
+    H, W = cur.shape
+    return int(W), int(H)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def me_lambda_q8(qp: int) -> int:
+    return int(load_library().me_lambda_q8(int(qp)))
+
+
+def me_mv_bits(v: int) -> int:
+    return int(load_library().me_mv_bits(int(v)))
+
+
+def me_acbm_default_params(qp: int) -> AcbmParams:
+    return load_library().me_acbm_default_params(int(qp))
+
+
+def params(alpha=1000, beta=8, gamma_num=1, gamma_den=4, qp=28, refine=1) -> AcbmParams:
+    return AcbmParams(int(alpha), int(beta), int(gamma_num), int(gamma_den), int(qp), int(refine))
+
+
+def me_padded_geometry(W: int, H: int, p: int):
+    pitch, rows, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().me_padded_geometry(W, H, p, ctypes.byref(pitch), ctypes.byref(rows),
+                                             ctypes.byref(P)), "me_padded_geometry")
+    return pitch.value, rows.value, P.value
+
+
+def me_pad_ref(ref, p: int, out=None, stream=None):
+    torch = _torch()
+    W, H = _frame_args(ref, ref)
+    pitch, rows, _ = me_padded_geometry(W, H, p)
+    if out is None:
+        out = torch.empty((rows, pitch), dtype=torch.uint8, device=ref.device)
+    _check(load_library().me_pad_ref(_ptr(ref), W, H, p, _ptr(out), _stream_ptr(stream)),
+           "me_pad_ref")
+    return out
+
+
+def me_intra_sad(cur, N: int, M: int, out=None, stream=None):
+    torch = _torch()
+    W, H = _frame_args(cur, cur)
+    if out is None:
+        out = torch.empty((max(H // M, 1), max(W // N, 1)), dtype=torch.int32, device=cur.device)
+    _check(load_library().me_intra_sad(_ptr(cur), W, H, N, M, _ptr(out), _stream_ptr(stream)),
+           "me_intra_sad")
+    return out
+
+
+@dataclass
+class FsbmResult:
+    mv: "object"     # int16 [BH, BW, 2]
+    J: "object"      # int32 view of uint32 [BH, BW]
+    sad: "object"    # int32 view of uint32 [BH, BW]
+
+
+def _outs(H, W, N, M, device):
+    torch = _torch()
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    mv = torch.empty((BH, BW, 2), dtype=torch.int16, device=device)
+    J = torch.empty((BH, BW), dtype=torch.int32, device=device)
+    sad = torch.empty((BH, BW), dtype=torch.int32, device=device)
+    return mv, J, sad
+
+
+def me_fsbm(cur, ref, N: int, M: int, p: int, lambda_q8: int, out=None, stream=None) -> FsbmResult:
+    """Full search of every block (Sec. 2.3).  Outputs: mv int16 [BH,BW,2],
+    J and SAD as int32 tensors holding the uint32 values."""
+    W, H = _frame_args(cur, ref)
+    mv, J, sad = out if out is not None else _outs(H, W, N, M, cur.device)
+    _check(load_library().me_fsbm(_ptr(cur), _ptr(ref), W, H, N, M, p, int(lambda_q8), _ptr(mv),
+                                  _ptr(J), _ptr(sad), _stream_ptr(stream)), "me_fsbm")
+    return FsbmResult(mv, J, sad)
+
+
+@dataclass
+class AcbmResult:
+    mv: "object"
+    J: "object"
+    mask: "object"   # uint8 [BH, BW]
+    sad: "object"
+    load: "object"
+
+
+def me_acbm(cur, ref, N: int, M: int, p: int, lambda_q8: int, prm: AcbmParams, prev_mv=None,
+            out=None, stream=None) -> AcbmResult:
+    """ACBM (Sec. 3.2) for one frame pair; prev_mv is the previous output field."""
+    torch = _torch()
+    W, H = _frame_args(cur, ref)
+    if out is None:
+        mv, J, sad = _outs(H, W, N, M, cur.device)
+        mask = torch.empty(J.shape, dtype=torch.uint8, device=cur.device)
+        load = torch.empty(J.shape, dtype=torch.int32, device=cur.device)
+    else:
+        mv, J, mask, sad, load = out
+    if prev_mv is not None and (prev_mv.dtype != torch.int16 or tuple(prev_mv.shape) != tuple(mv.shape)
+                                or not prev_mv.is_contiguous()):
+        raise ValueError("prev_mv must be a contiguous int16 [BH, BW, 2] CUDA tensor")
+    _check(load_library().me_acbm(_ptr(cur), _ptr(ref), W, H, N, M, p, int(lambda_q8),
+                                  _ptr(prev_mv), ctypes.byref(prm), _ptr(mv), _ptr(J), _ptr(mask),
+                                  _ptr(sad), _ptr(load), _stream_ptr(stream)), "me_acbm")
+    return AcbmResult(mv, J, mask, sad, load)
+
+
+def me_sad_peak(variant: int = 0, stream=None):
+    """(absdiff/s, lane-ops per clock per SM) of a packed-SAD instruction form."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().me_sad_peak(variant, ctypes.byref(a), ctypes.byref(b),
+                                      _stream_ptr(stream)), "me_sad_peak")
+    return a.value, b.value
+
+
+class Batch:
+    """me_batch: many streams of uneven size, one persistent launch per step."""
+
+    def __init__(self):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.me_batch_create(ctypes.byref(h)), "me_batch_create")
+        self._h = h
+        self.shapes = []
+
+    def add_stream(self, W: int, H: int, N: int, M: int, p: int) -> int:
+        idx = ctypes.c_int()
+        _check(self._lib.me_batch_add_stream(self._h, W, H, N, M, p, ctypes.byref(idx)),
+               "me_batch_add_stream")
+        self.shapes.append((W, H, N, M, p))
+        return idx.value
+
+    def run(self, mode: int, items, stream=None):
+        arr = (BatchItem * len(items))(*items)
+        _check(self._lib.me_batch_run(self._h, int(mode), arr, len(items), _stream_ptr(stream)),
+               "me_batch_run")
+
+    def sync(self, stream=None):
+        _check(self._lib.me_batch_sync(self._h, _stream_ptr(stream)), "me_batch_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.me_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,240 @@
+// me_device.cuh -- device building blocks of the block-matching kernels:
+// the packed-byte SAD step, the rate term, the packed argmin key and the
+// CTA-wide full search of one block.  Included by the .cu files of the
+// library only (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace me {
+
+constexpr int kMaxP = 64;
+constexpr int kMaxThreads = 512;
+constexpr unsigned long long kNoKey = ~0ull;
+
+// One packed-byte SAD step: c + sum_k |a.byte[k] - b.byte[k]|  (eq. SAD, Sec. 2.1,
+// four pixels at a time).  One instruction of the integer pipe at 16 lanes per
+// clock per SM sub-partition on sm_103a.
+__device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Bits of the signed Exp-Golomb code of one MV component: 1 for 0, else
+// 2*floor(log2|v|) + 3.  R(mv) of eq. J is mv_bits(mvx) + mv_bits(mvy).
+__host__ __device__ __forceinline__ int mv_bits(int v) {
+  unsigned a = v < 0 ? (unsigned)(-v) : (unsigned)v;
+  if (a == 0) return 1;
+#ifdef __CUDA_ARCH__
+  return 2 * (31 - __clz((int)a)) + 3;
+#else
+  int lg = 0;
+  while (a > 1u) { a >>= 1; lg++; }
+  return 2 * lg + 3;
+#endif
+}
+
+// The total order on candidates as one 64-bit key (smaller wins):
+// J_q8 in the high word; then |mvx|+|mvy|; then the raster index of the
+// position in the (2p+1)^2 window, (mvy+p)*(2p+1) + (mvx+p), which orders by
+// mvy, then mvx.  J_q8 < 2^26, |mv|_1 <= 128, raster < 2^15.
+__host__ __device__ __forceinline__ unsigned long long make_key(uint32_t J, int mvx, int mvy, int p) {
+  uint32_t l1 = (uint32_t)((mvx < 0 ? -mvx : mvx) + (mvy < 0 ? -mvy : mvy));
+  uint32_t r = (uint32_t)((mvy + p) * (2 * p + 1) + (mvx + p));
+  return ((unsigned long long)J << 32) | ((unsigned long long)l1 << 17) | r;
+}
+
+struct Decoded {
+  int mvx, mvy;
+  uint32_t J, sad;
+};
+
+// Inverse of make_key; SAD follows exactly from J = 256*SAD + lambda*R.
+__host__ __device__ __forceinline__ Decoded decode_key(unsigned long long key, int p, uint32_t lam) {
+  Decoded d;
+  uint32_t r = (uint32_t)(key & 0x1FFFFu);
+  int n = 2 * p + 1;
+  d.mvy = (int)(r / (uint32_t)n) - p;
+  d.mvx = (int)(r % (uint32_t)n) - p;
+  d.J = (uint32_t)(key >> 32);
+  d.sad = (d.J - lam * (uint32_t)(mv_bits(d.mvx) + mv_bits(d.mvy))) >> 8;
+  return d;
+}
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = umin64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ---------------------------------------------------------------------------
+// CTA-wide full search (Sec. 2.3) of a group of horizontally adjacent blocks.
+//
+// The CTA stages the union of the blocks' search windows from the (unpadded)
+// reference with edge clamping, then re-lays it out as "shifted words":
+// sh[r][o] holds window bytes o..o+3 of row r, so a candidate at any
+// horizontal offset reads its reference row as N/4 aligned 32-bit words with
+// no byte shuffling, and 32 consecutive offsets hit 32 consecutive banks.
+//
+// Work split: a task is (block, mvx column, run of T consecutive mvy).  The
+// thread keeps the N x M current block in registers (M*N/4 words) and streams
+// the T+M-1 reference rows of its run once: reference row r serves every
+// candidate k of the run with j = r - k in [0, M).  Each reference word is
+// therefore loaded once per run and reused by up to min(T, M) candidates.
+// ---------------------------------------------------------------------------
+struct FsGeom {
+  int p, n;          // search range, n = 2p+1 positions per axis
+  int nseg;          // runs per column: ceil(n / T)
+  int bpc;           // blocks per CTA (adjacent, same block row)
+  int rows;          // staged window rows: nseg*T + M - 1
+  int pos;           // shifted-word positions per row
+  int wbw;           // words per staged raw row
+  int tasks;         // bpc * n * nseg
+};
+
+template <int N, int M, int T>
+__host__ __device__ inline FsGeom fs_geom(int p, int bpc) {
+  FsGeom g;
+  g.p = p;
+  g.n = 2 * p + 1;
+  g.nseg = (g.n + T - 1) / T;
+  g.bpc = bpc;
+  g.rows = g.nseg * T + M - 1;
+  // positions o = blk*N + col (col < n) read words o..o+N-1 bytes
+  g.pos = (bpc - 1) * N + g.n + N - 4;
+  // raw bytes per row: pos + 3, plus 3 bytes of alignment slack, in words, +1
+  g.wbw = (g.pos + 3 + 3) / 4 + 1;
+  g.tasks = bpc * g.n * g.nseg;
+  return g;
+}
+
+// Shared-memory bytes used by fs_group for a geometry.
+template <int N, int M, int T>
+__host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
+  size_t words = (size_t)g.bpc * M * (N / 4)        // current blocks
+               + (size_t)g.rows * g.wbw             // raw window
+               + (size_t)g.rows * g.pos             // shifted words
+               + (size_t)g.rows * 2;                // per-row rate/key tables
+  return words * 4 + (kMaxThreads / 32) * 8 * 2;
+}
+
+// Full search of `g.bpc` adjacent blocks whose first block has top-left pixel
+// (x0, y0); results (one key per block) go to keys_out[0..bpc) in shared
+// memory (visible to all threads on return).  All threads of the CTA call it.
+template <int N, int M, int T>
+__device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
+                         int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
+                         uint32_t* smem, unsigned long long* keys_out) {
+  constexpr int NW = N / 4;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int p = g.p, n = g.n;
+  uint32_t* curw = smem;                                   // [bpc][M][NW]
+  uint32_t* wb = curw + g.bpc * M * NW;                    // [rows][wbw]
+  uint32_t* sh = wb + g.rows * g.wbw;                      // [rows][pos]
+  uint32_t* tabJ = sh + g.rows * g.pos;                    // [rows] lambda*L(mvy)
+  uint32_t* tabK = tabJ + g.rows;                          // [rows] key low bits of mvy
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(tabK + g.rows);
+  red = reinterpret_cast<unsigned long long*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+
+  // 1. current blocks (4-byte aligned rows: W % 4 == 0, x0 % 4 == 0)
+  if (tid < g.bpc) red[tid] = kNoKey;
+  for (int i = tid; i < g.bpc * M * NW; i += nthr) {
+    int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
+    curw[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w);
+  }
+  // 2. raw window, edge clamped; window column c is reference x = x0 - p + c
+  const int wx0 = x0 - p, wy0 = y0 - p;
+  const int rawbytes = g.wbw * 4;
+  for (int i = tid; i < g.rows * rawbytes; i += nthr) {
+    int r = i / rawbytes, c = i % rawbytes;
+    int gy = clampi(wy0 + r, 0, H - 1), gx = clampi(wx0 + c, 0, W - 1);
+    reinterpret_cast<uint8_t*>(wb)[i] = ref[(size_t)gy * W + gx];
+  }
+  // rate / key tables per staged row r (mvy = r - p; rows past 2p are padding)
+  for (int r = tid; r < g.rows; r += nthr) {
+    int mvy = r - p;
+    int a = mvy < 0 ? -mvy : mvy;
+    tabJ[r] = lam * (uint32_t)mv_bits(mvy);
+    tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
+  }
+  __syncthreads();
+  // 3. shifted words
+  for (int i = tid; i < g.rows * g.pos; i += nthr) {
+    int r = i / g.pos, o = i % g.pos;
+    const uint32_t* row = wb + r * g.wbw;
+    sh[i] = __funnelshift_r(row[o >> 2], row[(o >> 2) + 1], 8 * (o & 3));
+  }
+  __syncthreads();
+
+  // 4. tasks
+  unsigned long long best[1] = {kNoKey};
+  int cur_blk = -1;
+  uint32_t c[M][NW];
+  const int per_blk = n * g.nseg;
+  for (int t = tid; t < g.tasks; t += nthr) {
+    const int blk = t / per_blk, rem = t % per_blk;
+    const int seg = rem / n, col = rem % n;
+    if (blk != cur_blk) {
+      // flush the previous block's best into the CTA reduction slot
+      if (cur_blk >= 0) {
+        atomicMin(&red[cur_blk], best[0]);
+        best[0] = kNoKey;
+      }
+      cur_blk = blk;
+#pragma unroll
+      for (int j = 0; j < M; j++)
+#pragma unroll
+        for (int w = 0; w < NW; w++) c[j][w] = curw[(blk * M + j) * NW + w];
+    }
+    const int row0 = seg * T;
+    const uint32_t* shp = sh + row0 * g.pos + blk * N + col;
+    uint32_t acc[T];
+#pragma unroll
+    for (int k = 0; k < T; k++) acc[k] = 0;
+#pragma unroll
+    for (int r = 0; r < T + M - 1; r++) {
+      uint32_t rw[NW];
+#pragma unroll
+      for (int w = 0; w < NW; w++) rw[w] = shp[r * g.pos + 4 * w];
+#pragma unroll
+      for (int k = 0; k < T; k++) {
+        const int j = r - k;
+        if (j >= 0 && j < M) {
+#pragma unroll
+          for (int w = 0; w < NW; w++) acc[k] = sad4(c[j][w], rw[w], acc[k]);
+        }
+      }
+    }
+    // cost and key of each candidate of the run (mvx = col - p)
+    const int mvx = col - p;
+    const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
+    const uint32_t kx = ((uint32_t)(mvx < 0 ? -mvx : mvx) << 17) + (uint32_t)col;
+#pragma unroll
+    for (int k = 0; k < T; k++) {
+      const int r = row0 + k;
+      if (r < n) {
+        uint32_t J = acc[k] * 256u + jx + tabJ[r];
+        unsigned long long key = ((unsigned long long)J << 32) | (kx + tabK[r]);
+        best[0] = umin64(best[0], key);
+      }
+    }
+  }
+  // 5. reduction: per-thread keys -> per-block minimum in shared memory
+  //    (warp minimum per block first, then one shared atomic per warp)
+  for (int b = 0; b < g.bpc; b++) {
+    unsigned long long v = warp_min64(cur_blk == b ? best[0] : kNoKey);
+    if ((tid & 31) == 0 && v != kNoKey) atomicMin(&red[b], v);
+  }
+  __syncthreads();
+  if (tid < g.bpc) keys_out[tid] = red[tid];
+  __syncthreads();
+}
+
+}  // namespace me

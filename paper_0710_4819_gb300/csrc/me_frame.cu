@@ -1,0 +1,457 @@
+// me_frame.cu -- the per-frame C ABI: padding, Intra_SAD, FSBM and ACBM for
+// one frame pair, with their kernels.
+//
+//   me_fsbm : k_fsbm (one launch; full search of every block, Sec. 2.3)
+//   me_acbm : k_pad_ref, k_intra_sad, then for each anti-diagonal wave
+//             w = x + 2y of the block grid: k_pbm_wave (PBM + the Sec. 3.2 test,
+//             compaction of the failing blocks) and k_fs_list (full search of
+//             the compacted list).  Wave w+1 starts after wave w's full
+//             searches, so every spatial predictor is final when it is read.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "me_device.cuh"
+#include "me_host.h"
+#include "me_search.cuh"
+
+namespace me {
+
+__global__ void k_pad_ref(const uint8_t* __restrict__ ref, int W, int H, PadGeom g,
+                          uint8_t* __restrict__ out) {
+  const int chunks = g.pitch / 16;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)g.rows * chunks) return;
+  const int y = (int)(i / chunks), cx = (int)(i % chunks) * 16;
+  const uint8_t* src = ref + (size_t)clampi(y - g.P, 0, H - 1) * W;
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) v |= (uint32_t)src[clampi(cx + 4 * k + b - g.P, 0, W - 1)] << (8 * b);
+    w[k] = v;
+  }
+  *reinterpret_cast<uint4*>(out + (size_t)y * g.pitch + cx) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int N, int M>
+__global__ void __launch_bounds__(256) k_intra_sad(const uint8_t* __restrict__ cur, int W, int H,
+                                                   uint32_t* __restrict__ out) {
+  const int BW = W / N, nb = BW * (H / M);
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (b >= nb) return;
+  const uint32_t v = warp_intra_sad<N, M>(cur, W, (b % BW) * N, (b / BW) * M);
+  if ((threadIdx.x & 31) == 0) out[b] = v;
+}
+
+// FSBM over a whole frame: CTA = `bpc` adjacent blocks of one block row.
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kMaxThreads) k_fsbm(const uint8_t* __restrict__ cur,
+                                                      const uint8_t* __restrict__ ref, int W, int H,
+                                                      int p, int bpc, uint32_t lam,
+                                                      int16_t* __restrict__ mv_out,
+                                                      uint32_t* __restrict__ J_out,
+                                                      uint32_t* __restrict__ sad_out) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  const int BW = W / N;
+  const int gpr = (BW + bpc - 1) / bpc;
+  const int by = blockIdx.x / gpr, bx0 = (blockIdx.x % gpr) * bpc;
+  const int nb = min(bpc, BW - bx0);
+  const FsGeom g = fs_geom<N, M, T>(p, nb);
+  fs_group<N, M, T>(cur, ref, W, H, bx0 * N, by * M, g, lam, smem, keys);
+  if ((int)threadIdx.x < nb) {
+    const Decoded d = decode_key(keys[threadIdx.x], p, lam);
+    const int b = by * BW + bx0 + threadIdx.x;
+    mv_out[2 * b] = (int16_t)d.mvx;
+    mv_out[2 * b + 1] = (int16_t)d.mvy;
+    J_out[b] = d.J;
+    if (sad_out) sad_out[b] = d.sad;
+  }
+}
+
+// ACBM, PBM stage of wave w: one warp per block of the wave.  Passing blocks
+// get their final outputs; failing ones are appended to the wave's list.
+template <int N, int M>
+__global__ void __launch_bounds__(128) k_pbm_wave(AcbmArgs a, const uint8_t* __restrict__ refpad,
+                                                  PadGeom pg, const uint32_t* __restrict__ intra,
+                                                  int W, int H, int p, int w, int ylo, int count,
+                                                  int* __restrict__ fail_count,
+                                                  int* __restrict__ fail_list) {
+  __shared__ uint32_t curs[4][M * (N / 4)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * 4 + warp;
+  if (idx >= count) return;
+  const int by = ylo + idx, bx = w - 2 * by;
+  const int BW = W / N, b = by * BW + bx;
+  const PbmResult r = warp_pbm<N, M>(a.cur, refpad, pg, W, H, p, a.lam, a.mv, a.prev, bx, by,
+                                     intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp, a.refine,
+                                     curs[warp]);
+  if (lane == 0) {
+    if (r.pass) {
+      const Decoded d = decode_key(r.key, p, a.lam);
+      a.mv[2 * b] = (int16_t)d.mvx;
+      a.mv[2 * b + 1] = (int16_t)d.mvy;
+      a.J[b] = d.J;
+      a.mask[b] = 0;
+      if (a.sad) a.sad[b] = d.sad;
+      if (a.load) a.load[b] = (uint32_t)r.load;
+    } else {
+      const int slot = atomicAdd(fail_count, 1);
+      fail_list[slot] = b;
+    }
+  }
+}
+
+// ACBM full-search fallback of one wave: CTA i searches list entry i.
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kMaxThreads) k_fs_list(AcbmArgs a, int W, int H, int p,
+                                                         const int* __restrict__ fail_count,
+                                                         const int* __restrict__ fail_list) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  if ((int)blockIdx.x >= *fail_count) return;
+  const int BW = W / N;
+  const int b = fail_list[blockIdx.x];
+  const FsGeom g = fs_geom<N, M, T>(p, 1);
+  fs_group<N, M, T>(a.cur, a.ref, W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
+  if (threadIdx.x == 0) {
+    const Decoded d = decode_key(keys[0], p, a.lam);
+    a.mv[2 * b] = (int16_t)d.mvx;
+    a.mv[2 * b + 1] = (int16_t)d.mvy;
+    a.J[b] = d.J;
+    a.mask[b] = 1;
+    if (a.sad) a.sad[b] = d.sad;
+    if (a.load) a.load[b] = (uint32_t)((2 * p + 1) * (2 * p + 1));
+  }
+}
+
+// ------------------------------------------------------------------ plan
+
+static const int kT16[] = {8, 11, 13, 16};  // run lengths instantiated for 16x16
+static const int kTOther[] = {8};
+
+template <int N, int M, int T>
+static size_t smem_for(int p, int bpc) {
+  FsGeom g = fs_geom<N, M, T>(p, bpc);
+  return fs_smem_bytes<N, M, T>(g);
+}
+
+static size_t smem_dispatch(int N, int M, int T, int p, int bpc) {
+#define ME_SM(n, m, t) \
+  if (N == n && M == m && T == t) return smem_for<n, m, t>(p, bpc);
+  ME_SM(16, 16, 8) ME_SM(16, 16, 11) ME_SM(16, 16, 13) ME_SM(16, 16, 16)
+  ME_SM(16, 8, 8) ME_SM(16, 4, 8) ME_SM(8, 16, 8) ME_SM(8, 8, 8) ME_SM(8, 4, 8)
+  ME_SM(4, 16, 8) ME_SM(4, 8, 8) ME_SM(4, 4, 8)
+#undef ME_SM
+  return 0;
+}
+
+FsPlan fs_plan(int N, int M, int p, int bpc_max) {
+  const int n = 2 * p + 1, NW = N / 4;
+  const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
+  const int nT = (N == 16 && M == 16) ? 4 : 1;
+  // fallback (always valid): the first run length, one block per CTA
+  FsPlan best{Ts[0], 1, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  double best_cost = 1e300;
+  for (int ti = 0; ti < nT; ti++) {
+    const int T = Ts[ti];
+    const int nseg = (n + T - 1) / T;
+    for (int bpc = 1; bpc <= std::min(bpc_max, 8); bpc++) {
+      const size_t smem = smem_dispatch(N, M, T, p, bpc);
+      if (smem > 110 * 1024) break;
+      const int tasks = bpc * n * nseg;
+      for (int thr = 64; thr <= kMaxThreads; thr += 32) {
+        const int rounds = (tasks + thr - 1) / thr;
+        // instructions per thread: SAD + loads + epilogue per task, plus staging
+        const double task_cost = (double)T * M * NW + (double)(T + M - 1) * NW + 6.0 * T + 30.0;
+        FsGeom dummy;
+        dummy.rows = nseg * T + M - 1;
+        const double stage = (double)dummy.rows * ((bpc - 1) * N + n + N) * 2.0 / thr;
+        const double per_thread = rounds * task_cost + stage;
+        // CTA time ~ per_thread * threads (issue-bound); per useful candidate,
+        // discounted when too few warps are resident to keep the SAD pipe fed
+        // (128 registers per thread, 228 KB of shared memory per SM)
+        const int warps = (thr + 31) / 32;
+        int ctas = std::min(64 / warps, 65536 / (thr * 128));
+        ctas = std::min(ctas, (int)((228 * 1024) / (smem + 1024)));
+        const double occ = std::min(1.0, (double)(ctas * warps) / 16.0);
+        if (ctas < 1) continue;
+        const double cost = per_thread * thr / ((double)bpc * n * n) / occ;
+        if (cost < best_cost * 0.999) {
+          best_cost = cost;
+          best = FsPlan{T, bpc, thr, smem};
+        }
+      }
+    }
+  }
+  return best;
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+// Optional plan override "T,bpc,threads" (for tile sweeps); ignored unless
+// the run length is one instantiated for the block shape.
+static bool plan_override(int N, int M, FsPlan* pl, int p, int bpc_max) {
+  const char* e = std::getenv("ME_FS_PLAN");
+  if (!e) return false;
+  int T = 0, bpc = 0, thr = 0;
+  if (std::sscanf(e, "%d,%d,%d", &T, &bpc, &thr) != 3) return false;
+  const size_t smem = smem_dispatch(N, M, T, p, bpc);
+  if (smem == 0 || bpc < 1 || bpc > std::min(bpc_max, 8) || thr < 32 || thr > kMaxThreads ||
+      thr % 32 || smem > 200 * 1024)
+    return false;
+  *pl = FsPlan{T, bpc, thr, smem};
+  return true;
+}
+
+template <int N, int M, int T>
+static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, int p, uint32_t lam,
+                         int16_t* mv, uint32_t* J, uint32_t* sad, const FsPlan& pl, cudaStream_t s) {
+  auto kern = k_fsbm<N, M, T>;
+  ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  const int BW = W / N, BH = H / M;
+  const int grid = ((BW + pl.bpc - 1) / pl.bpc) * BH;
+  kern<<<grid, pl.threads, pl.smem, s>>>(cur, ref, W, H, p, pl.bpc, lam, mv, J, sad);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+template <int N, int M, int T>
+static int launch_fs_list_t(const AcbmArgs& a, int W, int H, int p, const int* cnt, const int* list,
+                            int grid, const FsPlan& pl, cudaStream_t s) {
+  auto kern = k_fs_list<N, M, T>;
+  ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  kern<<<grid, pl.threads, pl.smem, s>>>(a, W, H, p, cnt, list);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+#define ME_DISPATCH_FS(FN, ...)                                                      \
+  do {                                                                               \
+    if (N == 16 && M == 16) {                                                        \
+      switch (pl.T) {                                                                \
+        case 8: return FN<16, 16, 8>(__VA_ARGS__);                                   \
+        case 11: return FN<16, 16, 11>(__VA_ARGS__);                                 \
+        case 13: return FN<16, 16, 13>(__VA_ARGS__);                                 \
+        case 16: return FN<16, 16, 16>(__VA_ARGS__);                                 \
+      }                                                                              \
+    }                                                                                \
+    if (N == 16 && M == 8) return FN<16, 8, 8>(__VA_ARGS__);                         \
+    if (N == 16 && M == 4) return FN<16, 4, 8>(__VA_ARGS__);                         \
+    if (N == 8 && M == 16) return FN<8, 16, 8>(__VA_ARGS__);                         \
+    if (N == 8 && M == 8) return FN<8, 8, 8>(__VA_ARGS__);                           \
+    if (N == 8 && M == 4) return FN<8, 4, 8>(__VA_ARGS__);                           \
+    if (N == 4 && M == 16) return FN<4, 16, 8>(__VA_ARGS__);                         \
+    if (N == 4 && M == 8) return FN<4, 8, 8>(__VA_ARGS__);                           \
+    if (N == 4 && M == 4) return FN<4, 4, 8>(__VA_ARGS__);                           \
+    return ME_ERR_ARG;                                                               \
+  } while (0)
+
+int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
+                uint32_t lam, int16_t* mv, uint32_t* J, uint32_t* sad, cudaStream_t s) {
+  FsPlan pl = fs_plan(N, M, p, W / N);
+  plan_override(N, M, &pl, p, W / N);
+  ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
+}
+
+// Plan for searching single blocks where latency matters (the ACBM
+// fallback sits on the wave chain): one block per CTA, as many threads as
+// there are tasks (up to the maximum), the run length with the fewest
+// instructions per thread.
+FsPlan fs_plan_latency(int N, int M, int p) {
+  const int n = 2 * p + 1, NW = N / 4;
+  const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
+  const int nT = (N == 16 && M == 16) ? 4 : 1;
+  FsPlan best{Ts[0], 1, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  double best_lat = 1e300;
+  for (int ti = 0; ti < nT; ti++) {
+    const int T = Ts[ti];
+    const size_t smem = smem_dispatch(N, M, T, p, 1);
+    if (smem > 200 * 1024) continue;
+    const int nseg = (n + T - 1) / T, tasks = n * nseg;
+    const int thr = std::min(kMaxThreads, (tasks + 31) / 32 * 32);
+    const int rounds = (tasks + thr - 1) / thr;
+    const double task_cost = (double)T * M * NW + (double)(T + M - 1) * NW + 6.0 * T + 30.0;
+    const double lat = rounds * task_cost + (double)(nseg * T + M - 1) * (n + N) * 2.0 / thr;
+    if (lat < best_lat * 0.999) {
+      best_lat = lat;
+      best = FsPlan{T, 1, thr, smem};
+    }
+  }
+  return best;
+}
+
+static int launch_fs_list(int N, int M, const AcbmArgs& a, int W, int H, int p, const int* cnt,
+                          const int* list, int grid, cudaStream_t s) {
+  const FsPlan pl = fs_plan_latency(N, M, p);
+  ME_DISPATCH_FS(launch_fs_list_t, a, W, H, p, cnt, list, grid, pl, s);
+}
+
+#define ME_DISPATCH_NM(FN, ...)                                  \
+  do {                                                           \
+    if (N == 16 && M == 16) return FN<16, 16>(__VA_ARGS__);      \
+    if (N == 16 && M == 8) return FN<16, 8>(__VA_ARGS__);        \
+    if (N == 16 && M == 4) return FN<16, 4>(__VA_ARGS__);        \
+    if (N == 8 && M == 16) return FN<8, 16>(__VA_ARGS__);        \
+    if (N == 8 && M == 8) return FN<8, 8>(__VA_ARGS__);          \
+    if (N == 8 && M == 4) return FN<8, 4>(__VA_ARGS__);          \
+    if (N == 4 && M == 16) return FN<4, 16>(__VA_ARGS__);        \
+    if (N == 4 && M == 8) return FN<4, 8>(__VA_ARGS__);          \
+    if (N == 4 && M == 4) return FN<4, 4>(__VA_ARGS__);          \
+    return ME_ERR_ARG;                                           \
+  } while (0)
+
+template <int N, int M>
+static int launch_intra_t(const uint8_t* cur, int W, int H, uint32_t* out, cudaStream_t s) {
+  const int nb = (W / N) * (H / M);
+  k_intra_sad<N, M><<<(nb + 7) / 8, 256, 0, s>>>(cur, W, H, out);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+int launch_intra(const uint8_t* cur, int W, int H, int N, int M, uint32_t* out, cudaStream_t s) {
+  ME_DISPATCH_NM(launch_intra_t, cur, W, H, out, s);
+}
+
+int launch_pad(const uint8_t* ref, int W, int H, int p, uint8_t* out, cudaStream_t s) {
+  const PadGeom g = pad_geom(W, H, p);
+  const long long n = (long long)g.rows * (g.pitch / 16);
+  k_pad_ref<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ref, W, H, g, out);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+template <int N, int M>
+static int launch_pbm_wave_t(const AcbmArgs& a, const uint8_t* refpad, const PadGeom& pg,
+                             const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
+                             int* cnt, int* list, cudaStream_t s) {
+  k_pbm_wave<N, M><<<(count + 3) / 4, 128, 0, s>>>(a, refpad, pg, intra, W, H, p, w, ylo, count, cnt,
+                                                   list);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+static int launch_pbm_wave(int N, int M, const AcbmArgs& a, const uint8_t* refpad,
+                           const PadGeom& pg, const uint32_t* intra, int W, int H, int p, int w,
+                           int ylo, int count, int* cnt, int* list, cudaStream_t s) {
+  ME_DISPATCH_NM(launch_pbm_wave_t, a, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, s);
+}
+
+// Scratch layout of one ACBM frame call.
+struct AcbmScratch {
+  size_t off_pad, off_intra, off_cnt, off_list, total;
+};
+static AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
+  const PadGeom pg = pad_geom(W, H, p);
+  const int nb = (W / N) * (H / M);
+  const Waves wv = make_waves(W / N, H / M);
+  AcbmScratch l;
+  l.off_pad = 0;
+  l.off_intra = align_up((size_t)pg.pitch * pg.rows, 256);
+  l.off_cnt = align_up(l.off_intra + 4 * (size_t)nb, 256);
+  l.off_list = align_up(l.off_cnt + 4 * (size_t)wv.n, 256);
+  l.total = align_up(l.off_list + 4 * (size_t)nb, 256);
+  return l;
+}
+
+// Enqueues the whole ACBM frame given scratch memory of acbm_scratch_layout.
+static int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* scratch,
+                        cudaStream_t s) {
+  const AcbmScratch l = acbm_scratch_layout(W, H, N, M, p);
+  const PadGeom pg = pad_geom(W, H, p);
+  uint8_t* refpad = scratch + l.off_pad;
+  uint32_t* intra = reinterpret_cast<uint32_t*>(scratch + l.off_intra);
+  int* cnt = reinterpret_cast<int*>(scratch + l.off_cnt);
+  int* list = reinterpret_cast<int*>(scratch + l.off_list);
+  const Waves wv = make_waves(W / N, H / M);
+  int st = launch_pad(a.ref, W, H, p, refpad, s);
+  if (st) return st;
+  st = launch_intra(a.cur, W, H, N, M, intra, s);
+  if (st) return st;
+  ME_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * wv.n, s));
+  int off = 0;
+  for (int w = 0; w < wv.n; w++) {
+    const int c = wv.count(w);
+    if (c == 0) continue;
+    st = launch_pbm_wave(N, M, a, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w, list + off, s);
+    if (st) return st;
+    st = launch_fs_list(N, M, a, W, H, p, cnt + w, list + off, c, s);
+    if (st) return st;
+    off += c;
+  }
+  return ME_OK;
+}
+
+}  // namespace me
+
+using namespace me;
+
+extern "C" {
+
+int me_padded_geometry(int W, int H, int p, int* pitch, int* rows, int* P) {
+  if (W < 1 || H < 1 || W > 16384 || H > 16384) return ME_ERR_SHAPE;
+  if (p < 1 || p > kMaxP) return ME_ERR_ARG;
+  const PadGeom g = pad_geom(W, H, p);
+  if (pitch) *pitch = g.pitch;
+  if (rows) *rows = g.rows;
+  if (P) *P = g.P;
+  return ME_OK;
+}
+
+int me_pad_ref(const uint8_t* ref, int W, int H, int p, uint8_t* out, me_stream_t stream) {
+  if (!ref || !out) return ME_ERR_ARG;
+  if (W < 1 || H < 1 || W > 16384 || H > 16384) return ME_ERR_SHAPE;
+  if (p < 1 || p > kMaxP || (reinterpret_cast<uintptr_t>(out) & 15u)) return ME_ERR_ARG;
+  return launch_pad(ref, W, H, p, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int me_intra_sad(const uint8_t* cur, int W, int H, int N, int M, uint32_t* out, me_stream_t stream) {
+  if (!cur || !out) return ME_ERR_ARG;
+  int st = check_frame_args(W, H, N, M, 1, 0);
+  if (st) return st;
+  return launch_intra(cur, W, H, N, M, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int me_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
+            uint32_t lambda_q8, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out,
+            me_stream_t stream) {
+  if (!cur || !ref || !mv_out || !J_out) return ME_ERR_ARG;
+  if (!aligned4(cur) || !aligned4(ref)) return ME_ERR_ARG;
+  int st = check_frame_args(W, H, N, M, p, lambda_q8);
+  if (st) return st;
+  return launch_fsbm(cur, ref, W, H, N, M, p, lambda_q8, mv_out, J_out, sad_out,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+int me_acbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
+            uint32_t lambda_q8, const int16_t* prev_mv_field, const me_acbm_params* prm,
+            int16_t* mv_out, uint32_t* J_out, uint8_t* fullsearch_mask_out, uint32_t* sad_out,
+            uint32_t* load_out, me_stream_t stream) {
+  if (!cur || !ref || !mv_out || !J_out || !fullsearch_mask_out) return ME_ERR_ARG;
+  if (!aligned4(cur) || !aligned4(ref)) return ME_ERR_ARG;
+  int st = check_frame_args(W, H, N, M, p, lambda_q8);
+  if (st) return st;
+  st = check_acbm_params(prm);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  AcbmArgs a;
+  a.cur = cur; a.ref = ref; a.prev = prev_mv_field;
+  a.mv = mv_out; a.J = J_out; a.mask = fullsearch_mask_out; a.sad = sad_out; a.load = load_out;
+  a.lam = lambda_q8;
+  a.alpha = prm->alpha; a.beta = prm->beta; a.gnum = prm->gamma_num; a.gden = prm->gamma_den;
+  a.qp = prm->qp; a.refine = prm->refine;
+  const AcbmScratch l = acbm_scratch_layout(W, H, N, M, p);
+  void* scratch = nullptr;
+  st = scratch_alloc(&scratch, l.total, s);
+  if (st) return st;
+  st = enqueue_acbm(a, W, H, N, M, p, static_cast<uint8_t*>(scratch), s);
+  int st2 = scratch_free(scratch, s);
+  return st ? st : st2;
+}
+
+}  // extern "C"

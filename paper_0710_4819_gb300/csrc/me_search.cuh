@@ -1,0 +1,231 @@
+// me_search.cuh -- kernels of the frame path shared by the per-frame calls and
+// the batched/persistent paths: reference padding, Intra_SAD, the PBM stage of
+// ACBM for one block (one warp), and the full-search plan (tile choice).
+#pragma once
+#include "me_device.cuh"
+
+namespace me {
+
+// Per-call arguments of ACBM (device pointers and parameters).
+struct AcbmArgs {
+  const uint8_t* cur;
+  const uint8_t* ref;
+  const int16_t* prev;     // may be null (= zero field)
+  int16_t* mv;
+  uint32_t* J;
+  uint8_t* mask;
+  uint32_t* sad;           // may be null
+  uint32_t* load;          // may be null
+  uint32_t lam;
+  int32_t alpha, beta, gnum, gden, qp, refine;
+};
+
+// Padded-reference geometry: margin P = 16*ceil(p/16) on every side, pitch a
+// multiple of 16 with 16 extra bytes on the right so that a row segment read
+// as whole words (one word past its end) stays inside the row.
+struct PadGeom {
+  int P, pitch, rows;
+};
+__host__ __device__ inline PadGeom pad_geom(int W, int H, int p) {
+  PadGeom g;
+  g.P = (p + 15) / 16 * 16;
+  g.pitch = (W + 15) / 16 * 16 + 2 * g.P + 16;
+  g.rows = H + 2 * g.P;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// a1: edge-clamped padded reference, one thread per 16 output bytes.
+// ---------------------------------------------------------------------------
+__global__ void k_pad_ref(const uint8_t* __restrict__ ref, int W, int H, PadGeom g,
+                          uint8_t* __restrict__ out);
+
+// ---------------------------------------------------------------------------
+// a2: scaled Intra_SAD per block (eq. Intra_SAD, Sec. 3.1): one warp per block.
+// ---------------------------------------------------------------------------
+template <int N, int M>
+__device__ __forceinline__ uint32_t warp_intra_sad(const uint8_t* __restrict__ cur, int W, int x0,
+                                                   int y0) {
+  constexpr int NM = N * M;
+  const int lane = threadIdx.x & 31;
+  int v[(NM + 31) / 32];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < (NM + 31) / 32; k++) {
+    int i = lane + 32 * k;
+    v[k] = i < NM ? (int)cur[(size_t)(y0 + i / N) * W + x0 + (i % N)] : 0;
+    s += v[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  int d = 0;
+#pragma unroll
+  for (int k = 0; k < (NM + 31) / 32; k++) {
+    int i = lane + 32 * k;
+    if (i < NM) d += abs(NM * v[k] - s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  return (uint32_t)d;
+}
+
+// ---------------------------------------------------------------------------
+// One candidate's SAD computed by a single lane from the padded reference:
+// M rows of N/4 words, each row fetched as N/4+1 aligned words and shifted
+// into place with a funnel shift.  curs holds the current block (M x N/4).
+// ---------------------------------------------------------------------------
+template <int N, int M>
+__device__ __forceinline__ uint32_t lane_sad(const uint32_t* curs, const uint8_t* __restrict__ refpad,
+                                             const PadGeom& pg, int x0, int y0, int mvx, int mvy) {
+  constexpr int NW = N / 4;
+  const int xs = x0 + pg.P + mvx, ys = y0 + pg.P + mvy;
+  const uint32_t* rowp = reinterpret_cast<const uint32_t*>(refpad + (size_t)ys * pg.pitch) + (xs >> 2);
+  const int stride = pg.pitch >> 2;
+  const unsigned sh = 8u * (unsigned)(xs & 3);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < M; j++) {
+    uint32_t wv[NW + 1];
+#pragma unroll
+    for (int w = 0; w <= NW; w++) wv[w] = __ldg(rowp + j * stride + w);
+#pragma unroll
+    for (int w = 0; w < NW; w++) acc = sad4(curs[j * NW + w], __funnelshift_r(wv[w], wv[w + 1], sh), acc);
+  }
+  return acc;
+}
+
+template <int N, int M>
+__device__ __forceinline__ unsigned long long lane_key(const uint32_t* curs, const uint8_t* refpad,
+                                                       const PadGeom& pg, int x0, int y0, int mvx,
+                                                       int mvy, int p, uint32_t lam) {
+  uint32_t s = lane_sad<N, M>(curs, refpad, pg, x0, y0, mvx, mvy);
+  uint32_t J = 256u * s + lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy));
+  return make_key(J, mvx, mvy, p);
+}
+
+// Result of the PBM stage for one block (valid in every lane of the warp).
+struct PbmResult {
+  unsigned long long key;  // best PBM candidate
+  int load;                // distinct positions evaluated
+  bool pass;               // cond. 1 or cond. 2 holds
+};
+
+// ---------------------------------------------------------------------------
+// a5 + a6 + a9: the PBM stage of ACBM for block (bx, by), done by one warp
+// (Sec. 2.2 steps 1-3 with the predictor set of the current-frame field
+// `field` and the previous field `prev`; then the two conditions of Sec. 3.2).
+// Lanes 0-3 take the spatial predictors (left, up-left, up, up-right), lanes
+// 4-12 the 3x3 temporal ones, lane 13 the zero vector; each lane evaluates its
+// candidate unless a lower lane holds the same clipped position.  The ring
+// (lanes 0-7) skips positions already evaluated.  curs: this warp's staging
+// area for the current block (M*N/4 words of shared memory).
+// ---------------------------------------------------------------------------
+template <int N, int M>
+__device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ refpad,
+                              const PadGeom& pg, int W, int H, int p, uint32_t lam,
+                              const int16_t* field, const int16_t* __restrict__ prev,
+                              int bx, int by, uint32_t intra_x, int32_t alpha, int32_t beta,
+                              int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
+                              uint32_t* curs) {
+  constexpr int NW = N / 4;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int BW = W / N, BH = H / M;
+  const int x0 = bx * N, y0 = by * M;
+  for (int i = lane; i < M * NW; i += 32)
+    curs[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
+  __syncwarp();
+
+  // step 1: predictors
+  int cx = 0, cy = 0;
+  bool valid = false;
+  if (lane < 4) {
+    const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
+    const int dy = (lane == 0) ? 0 : -1;
+    const int nx = bx + dx, ny = by + dy;
+    if (nx >= 0 && nx < BW && ny >= 0) {
+      // final vectors of earlier waves; volatile so a concurrent writer's
+      // published value is re-read from memory (persistent kernels)
+      const volatile int16_t* f = field + 2 * (ny * BW + nx);
+      cx = f[0];
+      cy = f[1];
+      valid = true;
+    }
+  } else if (lane < 13) {
+    const int t = lane - 4, dx = t % 3 - 1, dy = t / 3 - 1;
+    const int nx = bx + dx, ny = by + dy;
+    if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+      if (prev) {
+        cx = prev[2 * (ny * BW + nx)];
+        cy = prev[2 * (ny * BW + nx) + 1];
+      }
+      valid = true;
+    }
+  } else if (lane == 13) {
+    valid = true;
+  }
+  cx = clampi(cx, -p, p);
+  cy = clampi(cy, -p, p);
+  const int code = valid ? ((cy + p) << 8) + (cx + p) : -1 - lane;
+  bool dup = false;
+#pragma unroll
+  for (int l = 0; l < 14; l++) {
+    const int v = __shfl_sync(FULL, code, l);
+    dup |= (l < lane) && (v == code);
+  }
+  const bool eval = valid && !dup;
+  // step 2: best predictor by J
+  unsigned long long key = eval ? lane_key<N, M>(curs, refpad, pg, x0, y0, cx, cy, p, lam) : kNoKey;
+  unsigned long long best = warp_min64(key);
+  int load = __popc(__ballot_sync(FULL, eval));
+  // step 3: +-1 integer ring around the best predictor
+  if (refine) {
+    const Decoded d = decode_key(best, p, lam);
+    int rx = 0, ry = 0, rcode = -100 - lane;
+    if (lane < 8) {
+      const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
+      rx = clampi(d.mvx + o % 3 - 1, -p, p);
+      ry = clampi(d.mvy + o / 3 - 1, -p, p);
+      rcode = ((ry + p) << 8) + (rx + p);
+    }
+    const int ecode = eval ? code : -1;
+    bool rdup = false;
+#pragma unroll
+    for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
+#pragma unroll
+    for (int l = 0; l < 8; l++) {
+      const int v = __shfl_sync(FULL, rcode, l);
+      rdup |= (l < lane) && (v == rcode);
+    }
+    const bool reval = lane < 8 && !rdup;
+    unsigned long long k2 = reval ? lane_key<N, M>(curs, refpad, pg, x0, y0, rx, ry, p, lam) : kNoKey;
+    best = umin64(best, warp_min64(k2));
+    load += __popc(__ballot_sync(FULL, reval));
+  }
+  // Sec. 3.2 conditions in exact integers (intra_x = NM * Intra_SAD)
+  const Decoded d = decode_key(best, p, lam);
+  const long long NM = N * M, sad = d.sad, q = qp;
+  const bool c1 = (long long)intra_x + NM * sad < NM * ((long long)alpha + (long long)beta * q * q);
+  const bool c2 = (long long)gden * NM * sad < (long long)gnum * (long long)intra_x;
+  PbmResult r;
+  r.key = best;
+  r.load = load;
+  r.pass = c1 || c2;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Full-search tile plan: run length T, blocks per CTA and threads per CTA.
+// ---------------------------------------------------------------------------
+struct FsPlan {
+  int T, bpc, threads;
+  size_t smem;
+};
+
+// Chooses among the instantiated run lengths with a small cost model
+// (SAD, load and epilogue instructions per useful candidate, lanes idle in the
+// last round, shared-memory staging).  bpc_max = 1 forces one block per CTA.
+FsPlan fs_plan(int N, int M, int p, int bpc_max);
+FsPlan fs_plan_latency(int N, int M, int p);
+
+}  // namespace me

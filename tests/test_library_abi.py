@@ -1,0 +1,89 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every function
+include/*.h declares, and the host-only entry points (cost helpers, argument
+validation before any launch) behave as documented.  No GPU needed."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_0710_4819_gb300 as me
+    return me.load_library(build_if_missing=True)
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(me_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_0710_4819_gb300 as me
+    out = subprocess.run(["nm", "-D", "--defined-only", me.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    names = declared_functions()
+    assert "me_fsbm" in names and "me_acbm" in names
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_lambda_and_bits_match_oracle(lib, orc):
+    import paper_0710_4819_gb300 as me
+    for qp in range(0, 1024, 7):
+        assert me.me_lambda_q8(qp) == orc.lambda_q8(qp)
+    for v in range(-300, 301):
+        assert me.me_mv_bits(v) == orc.mv_bits(v)
+    d = me.me_acbm_default_params(28)
+    assert (d.alpha, d.beta, d.gamma_num, d.gamma_den, d.qp, d.refine) == (1000, 8, 1, 4, 28, 1)
+
+
+def test_padded_geometry(lib):
+    import paper_0710_4819_gb300 as me
+    pitch, rows, P = me.me_padded_geometry(1920, 1088, 32)
+    assert P == 32 and pitch % 16 == 0 and pitch >= 1920 + 2 * P and rows == 1088 + 2 * P
+    pitch, rows, P = me.me_padded_geometry(36, 20, 5)
+    assert P == 16 and pitch % 16 == 0 and pitch >= 36 + 2 * 16 + 4
+
+
+def test_argument_errors_before_launch(lib):
+    """Invalid shapes and parameters are rejected on the host (no CUDA call)."""
+    vp = ctypes.c_void_p
+    fake = vp(256)   # never dereferenced: validation fails first
+    # N not in {4,8,16}
+    assert lib.me_fsbm(fake, fake, 64, 64, 12, 16, 4, 0, fake, fake, None, None) == 1
+    # p out of range
+    assert lib.me_fsbm(fake, fake, 64, 64, 16, 16, 0, 0, fake, fake, None, None) == 1
+    assert lib.me_fsbm(fake, fake, 64, 64, 16, 16, 65, 0, fake, fake, None, None) == 1
+    # lambda too large
+    assert lib.me_fsbm(fake, fake, 64, 64, 16, 16, 4, (1 << 20) + 1, fake, fake, None, None) == 1
+    # W % N != 0 -> shape error
+    assert lib.me_fsbm(fake, fake, 60, 64, 16, 16, 4, 0, fake, fake, None, None) == 2
+    # NULL pointers
+    assert lib.me_fsbm(None, fake, 64, 64, 16, 16, 4, 0, fake, fake, None, None) == 1
+    # misaligned frame pointer
+    assert lib.me_fsbm(vp(257), fake, 64, 64, 16, 16, 4, 0, fake, fake, None, None) == 1
+    import paper_0710_4819_gb300 as me
+    bad = me.params(gamma_den=0)
+    assert lib.me_acbm(fake, fake, 64, 64, 16, 16, 4, 0, None, ctypes.byref(bad), fake, fake, fake,
+                       None, None, None) == 1
+    bad = me.params(qp=2000)
+    assert lib.me_acbm(fake, fake, 64, 64, 16, 16, 4, 0, None, ctypes.byref(bad), fake, fake, fake,
+                       None, None, None) == 1
+    assert lib.me_acbm(fake, fake, 64, 64, 16, 16, 4, 0, None, None, fake, fake, fake,
+                       None, None, None) == 1
+    assert lib.me_status_string(2).decode().startswith("frame size")
