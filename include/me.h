@@ -127,6 +127,28 @@ int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
             int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,
             uint32_t *load_out, me_stream_t stream);
 
+/* The same ACBM as me_acbm, for callers that cannot allocate device memory:
+ * a host application or engine that owns every device allocation under a
+ * fixed budget, a plugin loaded into another process's CUDA context, or code
+ * that must not allocate after start-up.  The paper has no counterpart; this
+ * is a deployment variant.  It allocates nothing: its scratch memory is one
+ * fixed device array of 4 MiB inside the library (enough for frames up to
+ * about 1920x1088 at any p), which every GPU that loads the library holds
+ * until the process exits.  Arguments, outputs and errors are those of
+ * me_acbm; a frame whose scratch would exceed the array returns ME_ERR_NOMEM
+ * before anything is enqueued.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array, and a call leaves its contents
+ * behind (the parts that must start at zero are cleared by each call on its
+ * stream).  Calls whose GPU work overlaps -- on different streams, or from
+ * several host threads -- race on the array and give wrong results: issue
+ * them on one stream, or order them with events. */
+int me_acbm_noalloc(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+                    uint32_t lambda_q8, const int16_t *prev_mv_field, const me_acbm_params *prm,
+                    int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out,
+                    uint32_t *sad_out, uint32_t *load_out, me_stream_t stream);
+
 /* ----------------------------------------------------------------- peak probe */
 
 /* Measures the integer-pipe rate of a packed-SAD instruction form on the

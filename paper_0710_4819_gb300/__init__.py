@@ -83,6 +83,8 @@ def load_library(build_if_missing: bool = True):
             "me_fsbm": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp], c_int),
             "me_acbm": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp,
                          ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
+            "me_acbm_noalloc": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp,
+                                 ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
             "me_sad_peak": ([c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), vp], c_int),
             "me_batch_create": ([ctypes.POINTER(vp)], c_int),

@@ -342,11 +342,7 @@ static int launch_pbm_wave(int N, int M, const AcbmArgs& a, const uint8_t* refpa
   ME_DISPATCH_NM(launch_pbm_wave_t, a, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, s);
 }
 
-// Scratch layout of one ACBM frame call.
-struct AcbmScratch {
-  size_t off_pad, off_intra, off_cnt, off_list, total;
-};
-static AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
+AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
   const PadGeom pg = pad_geom(W, H, p);
   const int nb = (W / N) * (H / M);
   const Waves wv = make_waves(W / N, H / M);
@@ -360,7 +356,7 @@ static AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
 }
 
 // Enqueues the whole ACBM frame given scratch memory of acbm_scratch_layout.
-static int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* scratch,
+int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* scratch,
                         cudaStream_t s) {
   const AcbmScratch l = acbm_scratch_layout(W, H, N, M, p);
   const PadGeom pg = pad_geom(W, H, p);

@@ -228,4 +228,17 @@ struct FsPlan {
 FsPlan fs_plan(int N, int M, int p, int bpc_max);
 FsPlan fs_plan_latency(int N, int M, int p);
 
+// Scratch layout of one ACBM frame (padded reference, scaled Intra_SAD per
+// block, failing-block count per wave, compacted failing-block lists), in bytes
+// from the start of one 256-byte aligned region.
+struct AcbmScratch {
+  size_t off_pad, off_intra, off_cnt, off_list, total;
+};
+AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p);
+
+// Enqueues the whole ACBM frame on s, using `scratch` (acbm_scratch_layout
+// bytes; every part that must start at zero is cleared on the stream first).
+int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* scratch,
+                 cudaStream_t s);
+
 }  // namespace me
