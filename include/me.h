@@ -127,6 +127,53 @@ int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
             int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,
             uint32_t *load_out, me_stream_t stream);
 
+/* ----------------------------------------------------------------- batches */
+
+/* Many independent streams of uneven size in one launch per step (an
+ * extension of the per-frame calls; the paper has one sequence at a time).
+ * A batch fixes the list of stream shapes (one block shape N x M for all
+ * streams; W, H and p may differ); each run takes one frame pair per stream
+ * through FSBM or ACBM in a single persistent kernel (with the padding and
+ * Intra_SAD prologue for ACBM), captured once into a CUDA graph and replayed.
+ * Outputs are identical to running each stream alone with me_fsbm / me_acbm.
+ * Device memory (padded references, Intra_SAD, flags) is allocated once at
+ * the first run and released by me_batch_destroy. */
+typedef struct me_batch me_batch;
+
+typedef enum { ME_MODE_FSBM = 0, ME_MODE_ACBM = 1 } me_mode;
+
+typedef struct {
+    const uint8_t *cur, *ref;    /* device frames of this stream                 */
+    const int16_t *prev_mv;      /* ACBM: previous field, NULL = zeros           */
+    int16_t *mv_out;             /* [BH][BW][2]                                  */
+    uint32_t *J_out;             /* [BH][BW]                                     */
+    uint8_t *mask_out;           /* ACBM: [BH][BW] (required), FSBM: ignored     */
+    uint32_t *sad_out;           /* nullable                                     */
+    uint32_t *load_out;          /* nullable                                     */
+    uint32_t lambda_q8;
+    me_acbm_params prm;          /* ACBM only                                    */
+} me_batch_item;
+
+int me_batch_create(me_batch **out);
+/* Adds a stream shape; returns its index in *index.  Not allowed after the
+ * first me_batch_run. */
+int me_batch_add_stream(me_batch *b, int W, int H, int N, int M, int p, int *index);
+/* One step: items[k] belongs to stream k (all streams, in order).  Enqueued on
+ * stream; returns ME_ERR_TIMEOUT (after the stream finished) if a bounded
+ * device wait gave up, in which case the outputs are unspecified. */
+int me_batch_run(me_batch *b, int mode, const me_batch_item *items, int n_items,
+                 me_stream_t stream);
+/* Blocks until the last run on the given stream finished; reports its status
+ * (ME_ERR_TIMEOUT if a bounded wait inside the step gave up). */
+int me_batch_sync(me_batch *b, me_stream_t stream);
+/* Test hook for failure detection, before the first run: every device wait
+ * of the ACBM step gives up after timeout_ns nanoseconds (default 1 s), and
+ * block skip_block of stream skip_stream (-1: none) never publishes its
+ * vector, so the blocks that depend on it time out and the step reports
+ * ME_ERR_TIMEOUT instead of hanging. */
+int me_batch_set_fault(me_batch *b, long long timeout_ns, int skip_stream, int skip_block);
+void me_batch_destroy(me_batch *b);
+
 /* The same ACBM as me_acbm, for callers that cannot allocate device memory:
  * a host application or engine that owns every device allocation under a
  * fixed budget, a plugin loaded into another process's CUDA context, or code

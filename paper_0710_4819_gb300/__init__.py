@@ -93,6 +93,7 @@ def load_library(build_if_missing: bool = True):
             "me_batch_run": ([vp, c_int, ctypes.POINTER(BatchItem), c_int, vp], c_int),
             "me_batch_sync": ([vp, vp], c_int),
             "me_batch_destroy": ([vp], None),
+            "me_batch_set_fault": ([vp, ctypes.c_longlong, c_int, c_int], c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name, None)
@@ -267,6 +268,10 @@ class Batch:
         arr = (BatchItem * len(items))(*items)
         _check(self._lib.me_batch_run(self._h, int(mode), arr, len(items), _stream_ptr(stream)),
                "me_batch_run")
+
+    def set_fault(self, timeout_ns: int, skip_stream: int = -1, skip_block: int = -1):
+        _check(self._lib.me_batch_set_fault(self._h, int(timeout_ns), int(skip_stream),
+                                            int(skip_block)), "me_batch_set_fault")
 
     def sync(self, stream=None):
         _check(self._lib.me_batch_sync(self._h, _stream_ptr(stream)), "me_batch_sync")

@@ -75,43 +75,49 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------------------
-// CTA-wide full search (Sec. 2.3) of a group of horizontally adjacent blocks.
+// Full search (Sec. 2.3) of a group of horizontally adjacent blocks by one CTA.
 //
-// The CTA stages the union of the blocks' search windows from the (unpadded)
-// reference with edge clamping, then re-lays it out as "shifted words":
-// sh[r][o] holds window bytes o..o+3 of row r, so a candidate at any
-// horizontal offset reads its reference row as N/4 aligned 32-bit words with
-// no byte shuffling, and 32 consecutive offsets hit 32 consecutive banks.
+// The CTA stages the union of the blocks' search windows once (rows clamped to
+// the frame; columns read as aligned 32-bit words, clamped byte by byte only
+// when the window crosses the left or right frame edge), then re-lays it out
+// as "shifted words": sh[r][o] holds window bytes o..o+3 of row r, so a
+// candidate at any horizontal offset reads its reference row as N/4 aligned
+// words with no byte shuffling, and consecutive offsets hit consecutive banks.
 //
-// Work split: a task is (block, mvx column, run of T consecutive mvy).  The
-// thread keeps the N x M current block in registers (M*N/4 words) and streams
-// the T+M-1 reference rows of its run once: reference row r serves every
-// candidate k of the run with j = r - k in [0, M).  Each reference word is
-// therefore loaded once per run and reused by up to min(T, M) candidates.
+// Work split: G threads per block (G = 8, 16, 32, or a multiple of 32), so the
+// CTA holds bpc = blockDim/G blocks.  A task is (mvx column, run of T
+// consecutive mvy) of one block.  A thread keeps its N x M current block in
+// registers (loaded once) and streams the T+M-1 reference rows of each run:
+// reference row r serves every candidate k of the run with j = r - k in [0, M),
+// so each reference word is loaded once per run and reused by up to min(T, M)
+// candidates.  Tasks are dealt round-robin to the G threads of the block
+// (consecutive threads take consecutive columns).
 // ---------------------------------------------------------------------------
 struct FsGeom {
   int p, n;          // search range, n = 2p+1 positions per axis
   int nseg;          // runs per column: ceil(n / T)
-  int bpc;           // blocks per CTA (adjacent, same block row)
+  int bpc;           // blocks in this group (adjacent, same block row)
+  int G;             // threads per block
   int rows;          // staged window rows: nseg*T + M - 1
   int pos;           // shifted-word positions per row
-  int wbw;           // words per staged raw row
-  int tasks;         // bpc * n * nseg
+  int wbw;           // 32-bit words per staged raw row
+  int tasks;         // tasks per block: n * nseg
 };
 
 template <int N, int M, int T>
-__host__ __device__ inline FsGeom fs_geom(int p, int bpc) {
+__host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G) {
   FsGeom g;
   g.p = p;
   g.n = 2 * p + 1;
   g.nseg = (g.n + T - 1) / T;
   g.bpc = bpc;
+  g.G = G;
   g.rows = g.nseg * T + M - 1;
-  // positions o = blk*N + col (col < n) read words o..o+N-1 bytes
+  // position o = blk*N + col (col < n) is read as words o .. o+N-4
   g.pos = (bpc - 1) * N + g.n + N - 4;
-  // raw bytes per row: pos + 3, plus 3 bytes of alignment slack, in words, +1
-  g.wbw = (g.pos + 3 + 3) / 4 + 1;
-  g.tasks = bpc * g.n * g.nseg;
+  // raw row: up to 3 bytes of alignment slack, pos+3 bytes, one spare word
+  g.wbw = (g.pos + 6) / 4 + 1;
+  g.tasks = g.n * g.nseg;
   return g;
 }
 
@@ -122,115 +128,129 @@ __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
                + (size_t)g.rows * g.wbw             // raw window
                + (size_t)g.rows * g.pos             // shifted words
                + (size_t)g.rows * 2;                // per-row rate/key tables
-  return words * 4 + (kMaxThreads / 32) * 8 * 2;
+  return words * 4 + 16 * 8 + 8;                    // per-block minima (+ alignment)
 }
 
-// Full search of `g.bpc` adjacent blocks whose first block has top-left pixel
-// (x0, y0); results (one key per block) go to keys_out[0..bpc) in shared
-// memory (visible to all threads on return).  All threads of the CTA call it.
+// Full search of g.bpc adjacent blocks whose first block has top-left pixel
+// (x0, y0).  The per-block winning keys go to keys_out[0..bpc) (shared
+// memory, visible to all threads on return).  Every thread of the CTA calls
+// it; threads beyond bpc*G only help with staging.
 template <int N, int M, int T>
 __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
                          int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
                          uint32_t* smem, unsigned long long* keys_out) {
   constexpr int NW = N / 4;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   const int p = g.p, n = g.n;
   uint32_t* curw = smem;                                   // [bpc][M][NW]
   uint32_t* wb = curw + g.bpc * M * NW;                    // [rows][wbw]
   uint32_t* sh = wb + g.rows * g.wbw;                      // [rows][pos]
   uint32_t* tabJ = sh + g.rows * g.pos;                    // [rows] lambda*L(mvy)
-  uint32_t* tabK = tabJ + g.rows;                          // [rows] key low bits of mvy
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(tabK + g.rows);
-  red = reinterpret_cast<unsigned long long*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  uint32_t* tabK = tabJ + g.rows;                          // [rows] key bits of mvy
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(
+      (reinterpret_cast<uintptr_t>(tabK + g.rows) + 7) & ~uintptr_t(7));
 
-  // 1. current blocks (4-byte aligned rows: W % 4 == 0, x0 % 4 == 0)
+  // 1. current blocks (rows 4-byte aligned: W % 4 == 0, x0 % 4 == 0)
   if (tid < g.bpc) red[tid] = kNoKey;
   for (int i = tid; i < g.bpc * M * NW; i += nthr) {
-    int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
+    const int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
     curw[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w);
   }
-  // 2. raw window, edge clamped; window column c is reference x = x0 - p + c
-  const int wx0 = x0 - p, wy0 = y0 - p;
-  const int rawbytes = g.wbw * 4;
-  for (int i = tid; i < g.rows * rawbytes; i += nthr) {
-    int r = i / rawbytes, c = i % rawbytes;
-    int gy = clampi(wy0 + r, 0, H - 1), gx = clampi(wx0 + c, 0, W - 1);
-    reinterpret_cast<uint8_t*>(wb)[i] = ref[(size_t)gy * W + gx];
+  // 2. raw window rows, from the aligned word at or left of column x0 - p
+  const int wx0 = x0 - p;
+  const int A0 = (wx0 >> 2) << 2;        // floor to a multiple of 4
+  const int s0 = wx0 - A0;
+  const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
+  for (int r = warp; r < g.rows; r += nwarps) {
+    const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W;
+    uint32_t* dst = wb + r * g.wbw;
+    if (inside) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(rowp + A0);
+      for (int q = lane; q < g.wbw; q += 32) dst[q] = src[q];
+    } else {
+      for (int q = lane; q < g.wbw; q += 32) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 4; b++) v |= (uint32_t)rowp[clampi(A0 + 4 * q + b, 0, W - 1)] << (8 * b);
+        dst[q] = v;
+      }
+    }
   }
   // rate / key tables per staged row r (mvy = r - p; rows past 2p are padding)
   for (int r = tid; r < g.rows; r += nthr) {
-    int mvy = r - p;
-    int a = mvy < 0 ? -mvy : mvy;
+    const int mvy = r - p;
+    const int a = mvy < 0 ? -mvy : mvy;
     tabJ[r] = lam * (uint32_t)mv_bits(mvy);
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
   }
   __syncthreads();
-  // 3. shifted words
-  for (int i = tid; i < g.rows * g.pos; i += nthr) {
-    int r = i / g.pos, o = i % g.pos;
+  // 3. shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3
+  for (int r = warp; r < g.rows; r += nwarps) {
     const uint32_t* row = wb + r * g.wbw;
-    sh[i] = __funnelshift_r(row[o >> 2], row[(o >> 2) + 1], 8 * (o & 3));
+    uint32_t* dst = sh + r * g.pos;
+    for (int o = lane; o < g.pos; o += 32) {
+      const int k = s0 + o;
+      dst[o] = __funnelshift_r(row[k >> 2], row[(k >> 2) + 1], 8 * (k & 3));
+    }
   }
   __syncthreads();
 
-  // 4. tasks
-  unsigned long long best[1] = {kNoKey};
-  int cur_blk = -1;
-  uint32_t c[M][NW];
-  const int per_blk = n * g.nseg;
-  for (int t = tid; t < g.tasks; t += nthr) {
-    const int blk = t / per_blk, rem = t % per_blk;
-    const int seg = rem / n, col = rem % n;
-    if (blk != cur_blk) {
-      // flush the previous block's best into the CTA reduction slot
-      if (cur_blk >= 0) {
-        atomicMin(&red[cur_blk], best[0]);
-        best[0] = kNoKey;
-      }
-      cur_blk = blk;
+  // 4. tasks of this thread's block
+  const int blk = tid / g.G, l = tid - blk * g.G;
+  unsigned long long best = kNoKey;
+  if (blk < g.bpc) {
+    uint32_t c[M][NW];
 #pragma unroll
-      for (int j = 0; j < M; j++)
+    for (int j = 0; j < M; j++)
 #pragma unroll
-        for (int w = 0; w < NW; w++) c[j][w] = curw[(blk * M + j) * NW + w];
-    }
-    const int row0 = seg * T;
-    const uint32_t* shp = sh + row0 * g.pos + blk * N + col;
-    uint32_t acc[T];
+      for (int w = 0; w < NW; w++) c[j][w] = curw[(blk * M + j) * NW + w];
+    int seg = l / n, col = l - (l / n) * n;
+    const int dseg = g.G / n, dcol = g.G - (g.G / n) * n;
+    for (int t = l; t < g.tasks; t += g.G) {
+      const int row0 = seg * T;
+      const uint32_t* shp = sh + row0 * g.pos + blk * N + col;
+      uint32_t acc[T];
 #pragma unroll
-    for (int k = 0; k < T; k++) acc[k] = 0;
+      for (int k = 0; k < T; k++) acc[k] = 0;
 #pragma unroll
-    for (int r = 0; r < T + M - 1; r++) {
-      uint32_t rw[NW];
+      for (int r = 0; r < T + M - 1; r++) {
+        uint32_t rw[NW];
 #pragma unroll
-      for (int w = 0; w < NW; w++) rw[w] = shp[r * g.pos + 4 * w];
+        for (int w = 0; w < NW; w++) rw[w] = shp[r * g.pos + 4 * w];
 #pragma unroll
-      for (int k = 0; k < T; k++) {
-        const int j = r - k;
-        if (j >= 0 && j < M) {
+        for (int k = 0; k < T; k++) {
+          const int j = r - k;
+          if (j >= 0 && j < M) {
 #pragma unroll
-          for (int w = 0; w < NW; w++) acc[k] = sad4(c[j][w], rw[w], acc[k]);
+            for (int w = 0; w < NW; w++) acc[k] = sad4(c[j][w], rw[w], acc[k]);
+          }
         }
       }
-    }
-    // cost and key of each candidate of the run (mvx = col - p)
-    const int mvx = col - p;
-    const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
-    const uint32_t kx = ((uint32_t)(mvx < 0 ? -mvx : mvx) << 17) + (uint32_t)col;
+      // cost and key of each candidate of the run (mvx = col - p)
+      const int mvx = col - p;
+      const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
+      const uint32_t kx = ((uint32_t)(mvx < 0 ? -mvx : mvx) << 17) + (uint32_t)col;
 #pragma unroll
-    for (int k = 0; k < T; k++) {
-      const int r = row0 + k;
-      if (r < n) {
-        uint32_t J = acc[k] * 256u + jx + tabJ[r];
-        unsigned long long key = ((unsigned long long)J << 32) | (kx + tabK[r]);
-        best[0] = umin64(best[0], key);
+      for (int k = 0; k < T; k++) {
+        const int r = row0 + k;
+        if (r < n) {
+          const uint32_t J = acc[k] * 256u + jx + tabJ[r];
+          best = umin64(best, ((unsigned long long)J << 32) | (kx + tabK[r]));
+        }
       }
+      seg += dseg;
+      col += dcol;
+      if (col >= n) { col -= n; seg++; }
     }
   }
-  // 5. reduction: per-thread keys -> per-block minimum in shared memory
-  //    (warp minimum per block first, then one shared atomic per warp)
-  for (int b = 0; b < g.bpc; b++) {
-    unsigned long long v = warp_min64(cur_blk == b ? best[0] : kNoKey);
-    if ((tid & 31) == 0 && v != kNoKey) atomicMin(&red[b], v);
+  // 5. per-block minimum
+  if (g.G <= 32) {
+    for (int o = g.G >> 1; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (blk < g.bpc && l == 0) red[blk] = best;
+  } else {
+    best = warp_min64(best);
+    if (lane == 0 && blk < g.bpc && best != kNoKey) atomicMin(&red[blk], best);
   }
   __syncthreads();
   if (tid < g.bpc) keys_out[tid] = red[tid];

@@ -48,21 +48,23 @@ __global__ void __launch_bounds__(256) k_intra_sad(const uint8_t* __restrict__ c
   if ((threadIdx.x & 31) == 0) out[b] = v;
 }
 
-// FSBM over a whole frame: CTA = `bpc` adjacent blocks of one block row.
+// FSBM over a whole frame: CTA = blockDim/G adjacent blocks of one block row,
+// G threads per block.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(kMaxThreads) k_fsbm(const uint8_t* __restrict__ cur,
                                                       const uint8_t* __restrict__ ref, int W, int H,
-                                                      int p, int bpc, uint32_t lam,
+                                                      int p, int G, uint32_t lam,
                                                       int16_t* __restrict__ mv_out,
                                                       uint32_t* __restrict__ J_out,
                                                       uint32_t* __restrict__ sad_out) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   const int BW = W / N;
+  const int bpc = blockDim.x / G;
   const int gpr = (BW + bpc - 1) / bpc;
   const int by = blockIdx.x / gpr, bx0 = (blockIdx.x % gpr) * bpc;
   const int nb = min(bpc, BW - bx0);
-  const FsGeom g = fs_geom<N, M, T>(p, nb);
+  const FsGeom g = fs_geom<N, M, T>(p, nb, G);
   fs_group<N, M, T>(cur, ref, W, H, bx0 * N, by * M, g, lam, smem, keys);
   if ((int)threadIdx.x < nb) {
     const Decoded d = decode_key(keys[threadIdx.x], p, lam);
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fs_list(AcbmArgs a, int W, int 
   if ((int)blockIdx.x >= *fail_count) return;
   const int BW = W / N;
   const int b = fail_list[blockIdx.x];
-  const FsGeom g = fs_geom<N, M, T>(p, 1);
+  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
   fs_group<N, M, T>(a.cur, a.ref, W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
   if (threadIdx.x == 0) {
     const Decoded d = decode_key(keys[0], p, a.lam);
@@ -137,7 +139,7 @@ static const int kTOther[] = {8};
 
 template <int N, int M, int T>
 static size_t smem_for(int p, int bpc) {
-  FsGeom g = fs_geom<N, M, T>(p, bpc);
+  FsGeom g = fs_geom<N, M, T>(p, bpc, 32);
   return fs_smem_bytes<N, M, T>(g);
 }
 
@@ -151,41 +153,104 @@ static size_t smem_dispatch(int N, int M, int T, int p, int bpc) {
   return 0;
 }
 
+// Instructions one thread spends on one task (SAD steps, shifted-word loads,
+// cost/key epilogue, loop overhead).
+static double task_cost(int N, int M, int T) {
+  const int NW = N / 4;
+  return (double)T * M * NW + (double)(T + M - 1) * NW + 7.0 * T + 20.0;
+}
+
+// Staging instructions per CTA (raw words + shifted words + tables).
+static double stage_cost(int N, int M, int T, int p, int bpc) {
+  const int n = 2 * p + 1, rows = ((n + T - 1) / T) * T + M - 1;
+  const int pos = (bpc - 1) * N + n + N - 4;
+  return (double)rows * (pos * 6.0 + (pos / 4 + 2) * 4.0);
+}
+
 FsPlan fs_plan(int N, int M, int p, int bpc_max) {
-  const int n = 2 * p + 1, NW = N / 4;
+  const int n = 2 * p + 1;
   const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
   const int nT = (N == 16 && M == 16) ? 4 : 1;
-  // fallback (always valid): the first run length, one block per CTA
-  FsPlan best{Ts[0], 1, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  // fallback (always valid): the first run length, one block of 128 threads
+  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1)};
   double best_cost = 1e300;
+  static const int kG[] = {8, 16, 32, 64, 128, 256, 512};
+  static const int kThr[] = {64, 128, 256, 512};
   for (int ti = 0; ti < nT; ti++) {
     const int T = Ts[ti];
-    const int nseg = (n + T - 1) / T;
-    for (int bpc = 1; bpc <= std::min(bpc_max, 8); bpc++) {
-      const size_t smem = smem_dispatch(N, M, T, p, bpc);
-      if (smem > 110 * 1024) break;
-      const int tasks = bpc * n * nseg;
-      for (int thr = 64; thr <= kMaxThreads; thr += 32) {
-        const int rounds = (tasks + thr - 1) / thr;
-        // instructions per thread: SAD + loads + epilogue per task, plus staging
-        const double task_cost = (double)T * M * NW + (double)(T + M - 1) * NW + 6.0 * T + 30.0;
-        FsGeom dummy;
-        dummy.rows = nseg * T + M - 1;
-        const double stage = (double)dummy.rows * ((bpc - 1) * N + n + N) * 2.0 / thr;
-        const double per_thread = rounds * task_cost + stage;
-        // CTA time ~ per_thread * threads (issue-bound); per useful candidate,
-        // discounted when too few warps are resident to keep the SAD pipe fed
-        // (128 registers per thread, 228 KB of shared memory per SM)
-        const int warps = (thr + 31) / 32;
+    const int tasks = n * ((n + T - 1) / T);
+    for (int G : kG) {
+      const int rounds = (tasks + G - 1) / G;
+      for (int thr : kThr) {
+        if (thr < G || thr % G) continue;
+        const int bpc = thr / G;
+        if (bpc > std::min(bpc_max, 16)) continue;
+        const size_t smem = smem_dispatch(N, M, T, p, bpc);
+        if (smem > 110 * 1024) continue;
+        const double per_thread = rounds * task_cost(N, M, T) + stage_cost(N, M, T, p, bpc) / thr;
+        // resident warps per SM at 128 registers per thread and 228 KB of
+        // shared memory; fewer than 16 leave the SAD pipe under-fed
+        const int warps = thr / 32;
         int ctas = std::min(64 / warps, 65536 / (thr * 128));
         ctas = std::min(ctas, (int)((228 * 1024) / (smem + 1024)));
-        const double occ = std::min(1.0, (double)(ctas * warps) / 16.0);
         if (ctas < 1) continue;
+        const double occ = std::min(1.0, (double)(ctas * warps) / 16.0);
         const double cost = per_thread * thr / ((double)bpc * n * n) / occ;
         if (cost < best_cost * 0.999) {
           best_cost = cost;
-          best = FsPlan{T, bpc, thr, smem};
+          best = FsPlan{T, G, thr, smem};
         }
+      }
+    }
+  }
+  return best;
+}
+
+// Threads per block for a fixed run length and CTA size (persistent kernels,
+// whose launch fixes both): the G with the lowest modelled cost per candidate.
+FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit) {
+  const int n = 2 * p + 1;
+  const int tasks = n * ((n + T - 1) / T);
+  FsPlan best{T, thr, thr, smem_dispatch(N, M, T, p, 1)};
+  double best_cost = 1e300;
+  static const int kG[] = {8, 16, 32, 64, 128, 256, 512};
+  for (int G : kG) {
+    if (thr < G || thr % G) continue;
+    const int bpc = thr / G;
+    if (bpc > std::min(bpc_max, 16)) continue;
+    const size_t smem = smem_dispatch(N, M, T, p, bpc);
+    if (smem > smem_limit) continue;
+    const int rounds = (tasks + G - 1) / G;
+    const double per_thread = rounds * task_cost(N, M, T) + stage_cost(N, M, T, p, bpc) / thr;
+    const double cost = per_thread * thr / ((double)bpc * n * n);
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best = FsPlan{T, G, thr, smem};
+    }
+  }
+  return best;
+}
+
+// Plan for searching single blocks where latency matters (the ACBM fallback
+// sits on the wave chain): one block per CTA, all threads on it (G = threads),
+// the run length and thread count with the fewest instructions per thread.
+FsPlan fs_plan_latency(int N, int M, int p) {
+  const int n = 2 * p + 1;
+  const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
+  const int nT = (N == 16 && M == 16) ? 4 : 1;
+  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  double best_lat = 1e300;
+  for (int ti = 0; ti < nT; ti++) {
+    const int T = Ts[ti];
+    const size_t smem = smem_dispatch(N, M, T, p, 1);
+    if (smem > 200 * 1024) continue;
+    const int tasks = n * ((n + T - 1) / T);
+    for (int thr = 64; thr <= kMaxThreads; thr += 32) {
+      const int rounds = (tasks + thr - 1) / thr;
+      const double lat = rounds * task_cost(N, M, T) + stage_cost(N, M, T, p, 1) / thr;
+      if (lat < best_lat * 0.999) {
+        best_lat = lat;
+        best = FsPlan{T, thr, thr, smem};
       }
     }
   }
@@ -194,18 +259,20 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max) {
 
 // ------------------------------------------------------------------ launch helpers
 
-// Optional plan override "T,bpc,threads" (for tile sweeps); ignored unless
+// Optional plan override "T,G,threads" (for tile sweeps); ignored unless
 // the run length is one instantiated for the block shape.
 static bool plan_override(int N, int M, FsPlan* pl, int p, int bpc_max) {
   const char* e = std::getenv("ME_FS_PLAN");
   if (!e) return false;
-  int T = 0, bpc = 0, thr = 0;
-  if (std::sscanf(e, "%d,%d,%d", &T, &bpc, &thr) != 3) return false;
-  const size_t smem = smem_dispatch(N, M, T, p, bpc);
-  if (smem == 0 || bpc < 1 || bpc > std::min(bpc_max, 8) || thr < 32 || thr > kMaxThreads ||
-      thr % 32 || smem > 200 * 1024)
+  int T = 0, G = 0, thr = 0;
+  if (std::sscanf(e, "%d,%d,%d", &T, &G, &thr) != 3) return false;
+  if (!(G == 8 || G == 16 || (G >= 32 && G % 32 == 0)) || thr < 32 || thr > kMaxThreads ||
+      thr % 32 || thr % G)
     return false;
-  *pl = FsPlan{T, bpc, thr, smem};
+  const int bpc = thr / G;
+  const size_t smem = smem_dispatch(N, M, T, p, bpc);
+  if (smem == 0 || bpc > std::min(bpc_max, 16) || smem > 200 * 1024) return false;
+  *pl = FsPlan{T, G, thr, smem};
   return true;
 }
 
@@ -215,8 +282,9 @@ static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, i
   auto kern = k_fsbm<N, M, T>;
   ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   const int BW = W / N, BH = H / M;
-  const int grid = ((BW + pl.bpc - 1) / pl.bpc) * BH;
-  kern<<<grid, pl.threads, pl.smem, s>>>(cur, ref, W, H, p, pl.bpc, lam, mv, J, sad);
+  const int bpc = pl.threads / pl.G;
+  const int grid = ((BW + bpc - 1) / bpc) * BH;
+  kern<<<grid, pl.threads, pl.smem, s>>>(cur, ref, W, H, p, pl.G, lam, mv, J, sad);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
@@ -257,33 +325,6 @@ int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int
   FsPlan pl = fs_plan(N, M, p, W / N);
   plan_override(N, M, &pl, p, W / N);
   ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
-}
-
-// Plan for searching single blocks where latency matters (the ACBM
-// fallback sits on the wave chain): one block per CTA, as many threads as
-// there are tasks (up to the maximum), the run length with the fewest
-// instructions per thread.
-FsPlan fs_plan_latency(int N, int M, int p) {
-  const int n = 2 * p + 1, NW = N / 4;
-  const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
-  const int nT = (N == 16 && M == 16) ? 4 : 1;
-  FsPlan best{Ts[0], 1, 128, smem_dispatch(N, M, Ts[0], p, 1)};
-  double best_lat = 1e300;
-  for (int ti = 0; ti < nT; ti++) {
-    const int T = Ts[ti];
-    const size_t smem = smem_dispatch(N, M, T, p, 1);
-    if (smem > 200 * 1024) continue;
-    const int nseg = (n + T - 1) / T, tasks = n * nseg;
-    const int thr = std::min(kMaxThreads, (tasks + 31) / 32 * 32);
-    const int rounds = (tasks + thr - 1) / thr;
-    const double task_cost = (double)T * M * NW + (double)(T + M - 1) * NW + 6.0 * T + 30.0;
-    const double lat = rounds * task_cost + (double)(nseg * T + M - 1) * (n + N) * 2.0 / thr;
-    if (lat < best_lat * 0.999) {
-      best_lat = lat;
-      best = FsPlan{T, 1, thr, smem};
-    }
-  }
-  return best;
 }
 
 static int launch_fs_list(int N, int M, const AcbmArgs& a, int W, int H, int p, const int* cnt,

@@ -218,7 +218,7 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
 // Full-search tile plan: run length T, blocks per CTA and threads per CTA.
 // ---------------------------------------------------------------------------
 struct FsPlan {
-  int T, bpc, threads;
+  int T, G, threads;   // run length, threads per block, threads per CTA
   size_t smem;
 };
 
@@ -227,6 +227,7 @@ struct FsPlan {
 // last round, shared-memory staging).  bpc_max = 1 forces one block per CTA.
 FsPlan fs_plan(int N, int M, int p, int bpc_max);
 FsPlan fs_plan_latency(int N, int M, int p);
+FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit);
 
 // Scratch layout of one ACBM frame (padded reference, scaled Intra_SAD per
 // block, failing-block count per wave, compacted failing-block lists), in bytes
