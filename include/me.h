@@ -120,8 +120,14 @@ int me_fsbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
  * sad_out (nullable), load_out (nullable; distinct positions evaluated,
  * (2p+1)^2 for a full-searched block).  The blocks are processed as
  * anti-diagonal waves x + 2y = w so every predictor is final when read.
- * Scratch (stream-ordered pool): the padded reference plus 4 bytes per block
- * and per wave, about pitch*rows + 8*BW*BH bytes. */
+ * The frame's launches (a prologue, then two kernels per wave) are captured
+ * once per (device, W, H, N, M, p) into a CUDA graph with its own scratch
+ * (the padded reference plus 4 bytes per block and per wave, about
+ * pitch*rows + 8*BW*BH bytes, allocated at the first call with that shape and
+ * kept until the process exits) and replayed by later calls; calls with the
+ * same shape therefore run one after another on the GPU, whatever their
+ * streams.  The first call with a new shape allocates and captures, so make
+ * it outside any stream capture of your own. */
 int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
             uint32_t lambda_q8, const int16_t *prev_mv_field, const me_acbm_params *prm,
             int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,

@@ -95,6 +95,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // ---------------------------------------------------------------------------
 struct FsGeom {
   int p, n;          // search range, n = 2p+1 positions per axis
+  int rb;            // bits of the per-run tie rank (0: use 64-bit keys throughout)
   int nseg;          // runs per column: ceil(n / T)
   int bpc;           // blocks in this group (adjacent, same block row)
   int G;             // threads per block
@@ -104,10 +105,28 @@ struct FsGeom {
   int tasks;         // tasks per block: n * nseg
 };
 
+// Bits of the rank 2|mvy| - [mvy < 0] (0 .. 2p) that orders equal costs
+// within a run (fixed mvx): smaller |mvy| first, then the negative one.
+__host__ __device__ inline int rank_bits(int p) {
+  int b = 0;
+  while ((1 << b) <= 2 * p) b++;
+  return b;
+}
+
+// Whether (J_q8 << rank_bits) + rank fits in 32 bits for every candidate, so a
+// run can be reduced with 32-bit minima: J_q8 <= 256*255*N*M + lambda*R_max.
+__host__ __device__ inline bool fast32_ok(int N, int M, int p, uint32_t lam) {
+  const unsigned long long jmax =
+      256ull * 255ull * (unsigned long long)(N * M) + (unsigned long long)lam * (2ull * mv_bits(p));
+  const int rb = rank_bits(p);
+  return ((jmax << rb) | ((1ull << rb) - 1)) < (1ull << 32);
+}
+
 template <int N, int M, int T>
 __host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G) {
   FsGeom g;
   g.p = p;
+  g.rb = 0;
   g.n = 2 * p + 1;
   g.nseg = (g.n + T - 1) / T;
   g.bpc = bpc;
@@ -127,7 +146,7 @@ __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
   size_t words = (size_t)g.bpc * M * (N / 4)        // current blocks
                + (size_t)g.rows * g.wbw             // raw window
                + (size_t)g.rows * g.pos             // shifted words
-               + (size_t)g.rows * 2;                // per-row rate/key tables
+               + (size_t)g.rows * 3;                // per-row rate/key tables
   return words * 4 + 16 * 8 + 8;                    // per-block minima (+ alignment)
 }
 
@@ -148,8 +167,11 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   uint32_t* sh = wb + g.rows * g.wbw;                      // [rows][pos]
   uint32_t* tabJ = sh + g.rows * g.pos;                    // [rows] lambda*L(mvy)
   uint32_t* tabK = tabJ + g.rows;                          // [rows] key bits of mvy
+  uint32_t* tabQ = tabK + g.rows;                          // [rows] 32-bit run key of mvy
   unsigned long long* red = reinterpret_cast<unsigned long long*>(
-      (reinterpret_cast<uintptr_t>(tabK + g.rows) + 7) & ~uintptr_t(7));
+      (reinterpret_cast<uintptr_t>(tabQ + g.rows) + 7) & ~uintptr_t(7));
+  const bool fast = fast32_ok(N, M, p, lam);
+  const int rb = rank_bits(p);
 
   // 1. current blocks (rows 4-byte aligned: W % 4 == 0, x0 % 4 == 0)
   if (tid < g.bpc) red[tid] = kNoKey;
@@ -183,6 +205,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     const int a = mvy < 0 ? -mvy : mvy;
     tabJ[r] = lam * (uint32_t)mv_bits(mvy);
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
+    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
   }
   __syncthreads();
   // 3. shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3
@@ -218,25 +241,44 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
         uint32_t rw[NW];
 #pragma unroll
         for (int w = 0; w < NW; w++) rw[w] = shp[r * g.pos + 4 * w];
+        // word-major order: consecutive SAD steps go to different candidates
 #pragma unroll
-        for (int k = 0; k < T; k++) {
-          const int j = r - k;
-          if (j >= 0 && j < M) {
+        for (int w = 0; w < NW; w++) {
 #pragma unroll
-            for (int w = 0; w < NW; w++) acc[k] = sad4(c[j][w], rw[w], acc[k]);
+          for (int k = 0; k < T; k++) {
+            const int j = r - k;
+            if (j >= 0 && j < M) acc[k] = sad4(c[j][w], rw[w], acc[k]);
           }
         }
       }
       // cost and key of each candidate of the run (mvx = col - p)
       const int mvx = col - p;
+      const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
       const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
-      const uint32_t kx = ((uint32_t)(mvx < 0 ? -mvx : mvx) << 17) + (uint32_t)col;
+      if (fast) {
+        // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the
+        // same for the whole run and is added after the minimum
+        uint32_t m = 0xffffffffu;
 #pragma unroll
-      for (int k = 0; k < T; k++) {
-        const int r = row0 + k;
-        if (r < n) {
-          const uint32_t J = acc[k] * 256u + jx + tabJ[r];
-          best = umin64(best, ((unsigned long long)J << 32) | (kx + tabK[r]));
+        for (int k = 0; k < T; k++) {
+          const int r = row0 + k;
+          if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
+        }
+        m += jx << rb;
+        const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
+        const int mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
+        const uint32_t lo = ((amx + (uint32_t)(mvy < 0 ? -mvy : mvy)) << 17) +
+                            (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)col;
+        best = umin64(best, ((unsigned long long)J << 32) | lo);
+      } else {
+        const uint32_t kx = (amx << 17) + (uint32_t)col;
+#pragma unroll
+        for (int k = 0; k < T; k++) {
+          const int r = row0 + k;
+          if (r < n) {
+            const uint32_t J = acc[k] * 256u + jx + tabJ[r];
+            best = umin64(best, ((unsigned long long)J << 32) | (kx + tabK[r]));
+          }
         }
       }
       seg += dseg;

@@ -13,6 +13,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "me_device.cuh"
 #include "me_host.h"
@@ -76,10 +79,46 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm(const uint8_t* __restrict_
   }
 }
 
+// ACBM prologue of one frame, one launch: stores the call's arguments in the
+// device slot the wave kernels read, pads the reference (a1), computes the
+// scaled Intra_SAD of every block (a2) and clears the per-wave counters.
+template <int N, int M>
+__global__ void __launch_bounds__(256) k_acbm_prologue(AcbmArgs a, AcbmArgs* __restrict__ slot,
+                                                       PadGeom pg, int W, int H,
+                                                       uint8_t* __restrict__ refpad,
+                                                       uint32_t* __restrict__ intra,
+                                                       int* __restrict__ cnt, int nwaves) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  if (gtid == 0) *slot = a;
+  for (long long i = gtid; i < nwaves; i += nthr) cnt[i] = 0;
+  const int chunks = pg.pitch / 16;
+  for (long long i = gtid; i < (long long)pg.rows * chunks; i += nthr) {
+    const int y = (int)(i / chunks), cx = (int)(i % chunks) * 16;
+    const uint8_t* src = a.ref + (size_t)clampi(y - pg.P, 0, H - 1) * W;
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; b++) v |= (uint32_t)src[clampi(cx + 4 * k + b - pg.P, 0, W - 1)] << (8 * b);
+      w[k] = v;
+    }
+    *reinterpret_cast<uint4*>(refpad + (size_t)y * pg.pitch + cx) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  const int BW = W / N, nb = BW * (H / M);
+  const long long warps = nthr / 32;
+  for (long long b = gtid / 32; b < nb; b += warps) {
+    const uint32_t v = warp_intra_sad<N, M>(a.cur, W, (int)(b % BW) * N, (int)(b / BW) * M);
+    if ((threadIdx.x & 31) == 0) intra[b] = v;
+  }
+}
+
 // ACBM, PBM stage of wave w: one warp per block of the wave.  Passing blocks
 // get their final outputs; failing ones are appended to the wave's list.
 template <int N, int M>
-__global__ void __launch_bounds__(128) k_pbm_wave(AcbmArgs a, const uint8_t* __restrict__ refpad,
+__global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ ap,
+                                                  const uint8_t* __restrict__ refpad,
                                                   PadGeom pg, const uint32_t* __restrict__ intra,
                                                   int W, int H, int p, int w, int ylo, int count,
                                                   int* __restrict__ fail_count,
@@ -88,6 +127,7 @@ __global__ void __launch_bounds__(128) k_pbm_wave(AcbmArgs a, const uint8_t* __r
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * 4 + warp;
   if (idx >= count) return;
+  const AcbmArgs a = *ap;
   const int by = ylo + idx, bx = w - 2 * by;
   const int BW = W / N, b = by * BW + bx;
   const PbmResult r = warp_pbm<N, M>(a.cur, refpad, pg, W, H, p, a.lam, a.mv, a.prev, bx, by,
@@ -111,12 +151,14 @@ __global__ void __launch_bounds__(128) k_pbm_wave(AcbmArgs a, const uint8_t* __r
 
 // ACBM full-search fallback of one wave: CTA i searches list entry i.
 template <int N, int M, int T>
-__global__ void __launch_bounds__(kMaxThreads) k_fs_list(AcbmArgs a, int W, int H, int p,
+__global__ void __launch_bounds__(kMaxThreads) k_fs_list(const AcbmArgs* __restrict__ ap, int W,
+                                                         int H, int p,
                                                          const int* __restrict__ fail_count,
                                                          const int* __restrict__ fail_list) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   if ((int)blockIdx.x >= *fail_count) return;
+  const AcbmArgs a = *ap;
   const int BW = W / N;
   const int b = fail_list[blockIdx.x];
   const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
@@ -290,11 +332,11 @@ static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, i
 }
 
 template <int N, int M, int T>
-static int launch_fs_list_t(const AcbmArgs& a, int W, int H, int p, const int* cnt, const int* list,
-                            int grid, const FsPlan& pl, cudaStream_t s) {
+static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* cnt,
+                            const int* list, int grid, const FsPlan& pl, cudaStream_t s) {
   auto kern = k_fs_list<N, M, T>;
   ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-  kern<<<grid, pl.threads, pl.smem, s>>>(a, W, H, p, cnt, list);
+  kern<<<grid, pl.threads, pl.smem, s>>>(ap, W, H, p, cnt, list);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
@@ -327,10 +369,10 @@ int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int
   ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
 }
 
-static int launch_fs_list(int N, int M, const AcbmArgs& a, int W, int H, int p, const int* cnt,
+static int launch_fs_list(int N, int M, const AcbmArgs* ap, int W, int H, int p, const int* cnt,
                           const int* list, int grid, cudaStream_t s) {
   const FsPlan pl = fs_plan_latency(N, M, p);
-  ME_DISPATCH_FS(launch_fs_list_t, a, W, H, p, cnt, list, grid, pl, s);
+  ME_DISPATCH_FS(launch_fs_list_t, ap, W, H, p, cnt, list, grid, pl, s);
 }
 
 #define ME_DISPATCH_NM(FN, ...)                                  \
@@ -368,19 +410,37 @@ int launch_pad(const uint8_t* ref, int W, int H, int p, uint8_t* out, cudaStream
 }
 
 template <int N, int M>
-static int launch_pbm_wave_t(const AcbmArgs& a, const uint8_t* refpad, const PadGeom& pg,
+static int launch_pbm_wave_t(const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
                              const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
                              int* cnt, int* list, cudaStream_t s) {
-  k_pbm_wave<N, M><<<(count + 3) / 4, 128, 0, s>>>(a, refpad, pg, intra, W, H, p, w, ylo, count, cnt,
-                                                   list);
+  k_pbm_wave<N, M><<<(count + 3) / 4, 128, 0, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo, count,
+                                                   cnt, list);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
-static int launch_pbm_wave(int N, int M, const AcbmArgs& a, const uint8_t* refpad,
+static int launch_pbm_wave(int N, int M, const AcbmArgs* ap, const uint8_t* refpad,
                            const PadGeom& pg, const uint32_t* intra, int W, int H, int p, int w,
                            int ylo, int count, int* cnt, int* list, cudaStream_t s) {
-  ME_DISPATCH_NM(launch_pbm_wave_t, a, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, s);
+  ME_DISPATCH_NM(launch_pbm_wave_t, ap, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, s);
+}
+
+template <int N, int M>
+static int launch_prologue_t(const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg, int W, int H,
+                             uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
+                             cudaStream_t s) {
+  const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16),
+                                             32LL * (W / N) * (H / M));
+  const int grid = (int)std::min<long long>((work + 255) / 256, 152 * 8);
+  k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, cnt, nwaves);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+static int launch_prologue(int N, int M, const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg,
+                           int W, int H, uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
+                           cudaStream_t s) {
+  ME_DISPATCH_NM(launch_prologue_t, a, slot, pg, W, H, refpad, intra, cnt, nwaves, s);
 }
 
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
@@ -388,8 +448,9 @@ AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
   const int nb = (W / N) * (H / M);
   const Waves wv = make_waves(W / N, H / M);
   AcbmScratch l;
-  l.off_pad = 0;
-  l.off_intra = align_up((size_t)pg.pitch * pg.rows, 256);
+  l.off_args = 0;
+  l.off_pad = align_up(sizeof(AcbmArgs), 256);
+  l.off_intra = align_up(l.off_pad + (size_t)pg.pitch * pg.rows, 256);
   l.off_cnt = align_up(l.off_intra + 4 * (size_t)nb, 256);
   l.off_list = align_up(l.off_cnt + 4 * (size_t)wv.n, 256);
   l.total = align_up(l.off_list + 4 * (size_t)nb, 256);
@@ -401,26 +462,108 @@ int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* 
                         cudaStream_t s) {
   const AcbmScratch l = acbm_scratch_layout(W, H, N, M, p);
   const PadGeom pg = pad_geom(W, H, p);
+  AcbmArgs* slot = reinterpret_cast<AcbmArgs*>(scratch + l.off_args);
   uint8_t* refpad = scratch + l.off_pad;
   uint32_t* intra = reinterpret_cast<uint32_t*>(scratch + l.off_intra);
   int* cnt = reinterpret_cast<int*>(scratch + l.off_cnt);
   int* list = reinterpret_cast<int*>(scratch + l.off_list);
   const Waves wv = make_waves(W / N, H / M);
-  int st = launch_pad(a.ref, W, H, p, refpad, s);
+  int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, cnt, wv.n, s);
   if (st) return st;
-  st = launch_intra(a.cur, W, H, N, M, intra, s);
-  if (st) return st;
-  ME_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * wv.n, s));
   int off = 0;
   for (int w = 0; w < wv.n; w++) {
     const int c = wv.count(w);
     if (c == 0) continue;
-    st = launch_pbm_wave(N, M, a, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w, list + off, s);
+    st = launch_pbm_wave(N, M, slot, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w,
+                         list + off, s);
     if (st) return st;
-    st = launch_fs_list(N, M, a, W, H, p, cnt + w, list + off, c, s);
+    st = launch_fs_list(N, M, slot, W, H, p, cnt + w, list + off, c, s);
     if (st) return st;
     off += c;
   }
+  return ME_OK;
+}
+
+// ------------------------------------------------------------------ ACBM plans
+// One cached plan per (device, W, H, N, M, p): scratch memory and a CUDA graph
+// of the whole frame (prologue + two kernels per wave), captured once and
+// replayed.  A call updates the prologue node's by-value arguments and
+// launches the graph; CUDA orders launches of one executable graph, so calls
+// that share a plan (even on different streams) never overlap on the GPU.
+struct AcbmPlan {
+  int dev, W, H, N, M, p;
+  uint8_t* scratch = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t prologue = nullptr;
+  cudaKernelNodeParams kp{};
+  std::mutex mu;
+};
+
+static std::mutex g_plan_mu;
+static std::vector<AcbmPlan*> g_plans;
+
+static int build_plan(AcbmPlan* pl) {
+  const AcbmScratch l = acbm_scratch_layout(pl->W, pl->H, pl->N, pl->M, pl->p);
+  ME_CUDA(cudaMalloc(&pl->scratch, l.total));
+  cudaStream_t cs;
+  ME_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  AcbmArgs dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  dummy.gden = 1;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int st = ME_OK;
+  if (e == cudaSuccess) {
+    st = enqueue_acbm(dummy, pl->W, pl->H, pl->N, pl->M, pl->p, pl->scratch, cs);
+    e = cudaStreamEndCapture(cs, &pl->graph);
+  }
+  cudaStreamDestroy(cs);
+  if (st) return st;
+  ME_CUDA(e);
+  size_t nroot = 1;
+  ME_CUDA(cudaGraphGetRootNodes(pl->graph, &pl->prologue, &nroot));
+  if (nroot != 1) return ME_ERR_CUDA;
+  ME_CUDA(cudaGraphKernelNodeGetParams(pl->prologue, &pl->kp));
+  ME_CUDA(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+  return ME_OK;
+}
+
+static int get_plan(int W, int H, int N, int M, int p, AcbmPlan** out) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (AcbmPlan* pl : g_plans)
+    if (pl->dev == dev && pl->W == W && pl->H == H && pl->N == N && pl->M == M && pl->p == p) {
+      *out = pl;
+      return ME_OK;
+    }
+  AcbmPlan* pl = new AcbmPlan();
+  pl->dev = dev; pl->W = W; pl->H = H; pl->N = N; pl->M = M; pl->p = p;
+  int st = build_plan(pl);
+  if (st) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->scratch) cudaFree(pl->scratch);
+    delete pl;
+    return st;
+  }
+  g_plans.push_back(pl);
+  *out = pl;
+  return ME_OK;
+}
+
+static int launch_plan(AcbmPlan* pl, const AcbmArgs& a, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(pl->mu);
+  // the prologue's first parameter is the AcbmArgs value; the rest stay
+  void* argv[16];
+  for (int i = 0; i < 9; i++) argv[i] = pl->kp.kernelParams[i];
+  AcbmArgs val = a;
+  argv[0] = &val;
+  cudaKernelNodeParams kp = pl->kp;
+  kp.kernelParams = argv;
+  kp.extra = nullptr;
+  ME_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pl->prologue, &kp));
+  ME_CUDA(cudaGraphLaunch(pl->exec, s));
   return ME_OK;
 }
 
@@ -482,13 +625,10 @@ int me_acbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, 
   a.lam = lambda_q8;
   a.alpha = prm->alpha; a.beta = prm->beta; a.gnum = prm->gamma_num; a.gden = prm->gamma_den;
   a.qp = prm->qp; a.refine = prm->refine;
-  const AcbmScratch l = acbm_scratch_layout(W, H, N, M, p);
-  void* scratch = nullptr;
-  st = scratch_alloc(&scratch, l.total, s);
+  AcbmPlan* pl = nullptr;
+  st = get_plan(W, H, N, M, p, &pl);
   if (st) return st;
-  st = enqueue_acbm(a, W, H, N, M, p, static_cast<uint8_t*>(scratch), s);
-  int st2 = scratch_free(scratch, s);
-  return st ? st : st2;
+  return launch_plan(pl, a, s);
 }
 
 }  // extern "C"

@@ -229,11 +229,11 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max);
 FsPlan fs_plan_latency(int N, int M, int p);
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit);
 
-// Scratch layout of one ACBM frame (padded reference, scaled Intra_SAD per
-// block, failing-block count per wave, compacted failing-block lists), in bytes
-// from the start of one 256-byte aligned region.
+// Scratch layout of one ACBM frame (the call's arguments, padded reference,
+// scaled Intra_SAD per block, failing-block count per wave, compacted
+// failing-block lists), in bytes from the start of one 256-byte aligned region.
 struct AcbmScratch {
-  size_t off_pad, off_intra, off_cnt, off_list, total;
+  size_t off_args, off_pad, off_intra, off_cnt, off_list, total;
 };
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p);
 

@@ -74,15 +74,17 @@ def test_fsbm_small_all_shapes(me, orc, N, M, p):
             _eq(f"{N}x{M} p={p} {nm}", g, w)
 
 
-@pytest.mark.parametrize("p", [3, 11, 16, 20, 32])
-def test_fsbm_16x16_run_lengths(me, orc, p):
-    """Search ranges that exercise every instantiated run length and ragged runs."""
+@pytest.mark.parametrize("p,lam", [(3, 6595), (11, 6595), (16, 6595), (20, 6595), (32, 6595),
+                                   (32, 800000), (64, 2000), (64, 6595), (40, 1 << 20)])
+def test_fsbm_16x16_run_lengths(me, orc, p, lam):
+    """Search ranges that exercise every instantiated run length and ragged
+    runs, and lambdas on both sides of the 32-bit run-key limit."""
     rng = np.random.default_rng(p)
     ref = synth.texture(rng, 96, 64)
     cur = synth.shifted_copy(ref, 3, -2)
     cur = np.clip(cur.astype(int) + rng.integers(-3, 4, cur.shape), 0, 255).astype(np.uint8)
-    got = _fsbm_gpu(me, cur, ref, 16, 16, p, 6595)
-    want = orc.fsbm(cur, ref, 16, 16, p, 6595, nthreads=8)
+    got = _fsbm_gpu(me, cur, ref, 16, 16, p, lam)
+    want = orc.fsbm(cur, ref, 16, 16, p, lam, nthreads=8)
     for nm, g, w in zip(("mv", "J", "sad"), got, want):
         _eq(nm, g, w)
 
