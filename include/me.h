@@ -165,8 +165,9 @@ int me_batch_create(me_batch **out);
  * first me_batch_run. */
 int me_batch_add_stream(me_batch *b, int W, int H, int N, int M, int p, int *index);
 /* One step: items[k] belongs to stream k (all streams, in order).  Enqueued on
- * stream; returns ME_ERR_TIMEOUT (after the stream finished) if a bounded
- * device wait gave up, in which case the outputs are unspecified. */
+ * stream; me_batch_sync then reports ME_ERR_TIMEOUT if a bounded device wait
+ * gave up, in which case the outputs are unspecified.  Successive runs of one
+ * batch share its device tables: issue them on one stream (or order them). */
 int me_batch_run(me_batch *b, int mode, const me_batch_item *items, int n_items,
                  me_stream_t stream);
 /* Blocks until the last run on the given stream finished; reports its status

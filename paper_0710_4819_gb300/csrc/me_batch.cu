@@ -290,9 +290,11 @@ struct me_batch {
   me::BSegment* d_segs = nullptr;
   me::BFsEntry* d_fsent = nullptr;
   me::BCtrl* d_ctrl = nullptr;
-  me::BStream* h_streams = nullptr;     // pinned staging of the per-run arguments
+  static constexpr int kRing = 4;       // staging buffers in flight
+  me::BStream* h_streams = nullptr;     // pinned staging of the per-run arguments [kRing][n]
   me::BCtrl* h_ctrl = nullptr;          // pinned read-back of the control block
-  cudaEvent_t staged = nullptr;         // the staging copy of the last run is done
+  cudaEvent_t staged[kRing] = {};       // the staging copy from ring slot i is done
+  int ring = 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaGraph_t graph[2] = {nullptr, nullptr};
   long long timeout_ns = 1000000000ll;  // 1 s per wait
@@ -406,9 +408,10 @@ static int batch_finalize(me_batch* b) {
   c.skip_stream = b->skip_stream;
   c.skip_block = b->skip_block;
   ME_CUDA(cudaMemcpy(b->d_ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
-  ME_CUDA(cudaMallocHost(&b->h_streams, sizeof(BStream) * n));
+  ME_CUDA(cudaMallocHost(&b->h_streams, sizeof(BStream) * n * me_batch::kRing));
   ME_CUDA(cudaMallocHost(&b->h_ctrl, sizeof(BCtrl)));
-  ME_CUDA(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
+  for (int i = 0; i < me_batch::kRing; i++)
+    ME_CUDA(cudaEventCreateWithFlags(&b->staged[i], cudaEventDisableTiming));
   // persistent grids: as many CTAs as fit on the device at once
   int dev = 0, nsm = 0;
   ME_CUDA(cudaGetDevice(&dev));
@@ -521,20 +524,22 @@ int me_batch_run(me_batch* b, int mode, const me_batch_item* items, int n_items,
   int dev = 0;
   ME_CUDA(cudaGetDevice(&dev));
   if (dev != b->device) return ME_ERR_ARG;
-  // the previous run's staging copy must be done before the buffer is reused
-  ME_CUDA(cudaEventSynchronize(b->staged));
+  // a ring slot is reused only after the copy that last read it has run
+  const int slot = b->ring;
+  b->ring = (b->ring + 1) % me_batch::kRing;
+  ME_CUDA(cudaEventSynchronize(b->staged[slot]));
+  BStream* hs = b->h_streams + (size_t)slot * b->shapes.size();
   for (int i = 0; i < n_items; i++) {
     const me_batch_item& it = items[i];
-    BStream& a = b->h_streams[i];
+    BStream& a = hs[i];
     a.cur = it.cur; a.ref = it.ref; a.prev = it.prev_mv;
     a.mv = it.mv_out; a.J = it.J_out; a.mask = it.mask_out; a.sad = it.sad_out;
     a.load = it.load_out; a.lam = it.lambda_q8;
     a.alpha = it.prm.alpha; a.beta = it.prm.beta; a.gnum = it.prm.gamma_num;
     a.gden = it.prm.gamma_den; a.qp = it.prm.qp; a.refine = it.prm.refine;
   }
-  ME_CUDA(cudaMemcpyAsync(b->d_streams, b->h_streams, sizeof(BStream) * n_items,
-                          cudaMemcpyHostToDevice, s));
-  ME_CUDA(cudaEventRecord(b->staged, s));
+  ME_CUDA(cudaMemcpyAsync(b->d_streams, hs, sizeof(BStream) * n_items, cudaMemcpyHostToDevice, s));
+  ME_CUDA(cudaEventRecord(b->staged[slot], s));
   const int gi = mode == ME_MODE_ACBM ? 1 : 0;
   if (!b->exec[gi]) {
     // capture the step once on a private stream, then replay it
@@ -576,10 +581,11 @@ void me_batch_destroy(me_batch* b) {
     if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
     if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
   }
-  if (b->staged) {
-    cudaEventSynchronize(b->staged);
-    cudaEventDestroy(b->staged);
-  }
+  for (int i = 0; i < me_batch::kRing; i++)
+    if (b->staged[i]) {
+      cudaEventSynchronize(b->staged[i]);
+      cudaEventDestroy(b->staged[i]);
+    }
   if (b->dmem) {
     cudaDeviceSynchronize();
     cudaFree(b->dmem);
