@@ -181,6 +181,61 @@ int me_batch_sync(me_batch *b, me_stream_t stream);
 int me_batch_set_fault(me_batch *b, long long timeout_ns, int skip_stream, int skip_block);
 void me_batch_destroy(me_batch *b);
 
+/* ----------------------------------------------------------------- serving */
+
+/* A request server with continuous batching (an extension for serving many
+ * live streams; the paper has one sequence at a time).  Each stream submits
+ * its frames in order from host memory; the server keeps the stream's last
+ * frame (the reference) and last motion field resident in device memory, so a
+ * request is one new frame and its result is the motion field of the pair
+ * (previous frame, this frame).  A worker thread keeps up to max_inflight
+ * steps on the GPU; each step takes the oldest pending request of every
+ * stream not already on the GPU and runs them in one persistent launch, so
+ * requests that arrive while steps are running join the next step as soon as
+ * a slot frees.  Results are identical to me_acbm / me_fsbm on the same frames.
+ * Streams are admitted against device_budget_bytes (their resident state:
+ * two frames, two fields, the outputs and the padded reference). */
+typedef struct me_server me_server;
+
+typedef struct {
+    long long device_budget_bytes; /* admission budget for resident stream state */
+    int max_inflight;              /* steps on the GPU at once, 1..8              */
+    int mode;                      /* ME_MODE_ACBM or ME_MODE_FSBM                */
+    int N, M;                      /* block size of every stream                  */
+} me_server_config;
+
+typedef struct {
+    int has_result;      /* 0 for a stream's first frame (it only becomes the reference) */
+    int status;          /* ME_OK, or ME_ERR_TIMEOUT if a bounded device wait gave up   */
+    double latency_ms;   /* submit -> results in host memory                            */
+    /* host buffers the caller provides (each nullable), [BH][BW](x2 for mv) */
+    int16_t *mv;
+    uint32_t *J;
+    uint8_t *mask;       /* ACBM only */
+    uint32_t *sad;
+    uint32_t *load;      /* ACBM only */
+} me_server_result;
+
+int me_server_create(const me_server_config *cfg, me_server **out);
+/* Opens a stream of W x H frames with search range p; prm NULL = the paper's
+ * parameters for qp.  ME_ERR_NOMEM: the stream does not fit the budget now
+ * (retry after another stream closed). */
+int me_server_open_stream(me_server *s, int W, int H, int p, const me_acbm_params *prm,
+                          int32_t qp, int *stream_id);
+/* Queues one frame (W*H bytes of host memory, copied before returning). */
+int me_server_submit(me_server *s, int stream_id, const uint8_t *frame, long long *request_id);
+/* ME_ERR_BUSY while pending; on completion copies the results into res's
+ * buffers, returns the request's status and forgets the request. */
+int me_server_poll(me_server *s, long long request_id, me_server_result *res);
+/* As poll, waiting up to timeout_ms (ME_ERR_BUSY if still pending). */
+int me_server_wait(me_server *s, long long request_id, int timeout_ms, me_server_result *res);
+/* Closes a stream; its memory returns to the budget once its work is done. */
+int me_server_close_stream(me_server *s, int stream_id);
+/* Budget in use, open streams and pending requests; returns the server's
+ * status (ME_OK unless a CUDA error stopped it). */
+int me_server_stats(me_server *s, long long *used_bytes, int *open_streams, int *pending);
+void me_server_destroy(me_server *s);
+
 /* The same ACBM as me_acbm, for callers that cannot allocate device memory:
  * a host application or engine that owns every device allocation under a
  * fixed budget, a plugin loaded into another process's CUDA context, or code

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
-    "me_fsbm", "me_acbm", "me_sad_peak", "Batch", "STATUS",
+    "me_fsbm", "me_acbm", "me_sad_peak", "Batch", "Server", "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -51,6 +51,17 @@ class BatchItem(ctypes.Structure):
                 ("mask_out", ctypes.c_void_p), ("sad_out", ctypes.c_void_p),
                 ("load_out", ctypes.c_void_p), ("lambda_q8", ctypes.c_uint32),
                 ("prm", AcbmParams)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_longlong), ("max_inflight", ctypes.c_int),
+                ("mode", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("has_result", ctypes.c_int), ("status", ctypes.c_int),
+                ("latency_ms", ctypes.c_double), ("mv", ctypes.c_void_p), ("J", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("sad", ctypes.c_void_p), ("load", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -94,6 +105,16 @@ def load_library(build_if_missing: bool = True):
             "me_batch_sync": ([vp, vp], c_int),
             "me_batch_destroy": ([vp], None),
             "me_batch_set_fault": ([vp, ctypes.c_longlong, c_int, c_int], c_int),
+            "me_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], c_int),
+            "me_server_open_stream": ([vp, c_int, c_int, c_int, ctypes.POINTER(AcbmParams),
+                                       ctypes.c_int32, ctypes.POINTER(c_int)], c_int),
+            "me_server_submit": ([vp, c_int, vp, ctypes.POINTER(ctypes.c_longlong)], c_int),
+            "me_server_poll": ([vp, ctypes.c_longlong, ctypes.POINTER(ServerResult)], c_int),
+            "me_server_wait": ([vp, ctypes.c_longlong, c_int, ctypes.POINTER(ServerResult)], c_int),
+            "me_server_close_stream": ([vp, c_int], c_int),
+            "me_server_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_int)], c_int),
+            "me_server_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name, None)
@@ -286,3 +307,88 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """me_server: continuous-batching request server over many streams.
+
+    submit() takes one uint8 numpy frame [H, W] (host memory); results come
+    back as numpy arrays from poll()/wait().
+    """
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 2, mode: int = 1, N: int = 16,
+                 M: int = 16):
+        self._lib = load_library()
+        self.N, self.M, self.mode = N, M, mode
+        cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(mode), int(N), int(M))
+        h = ctypes.c_void_p()
+        _check(self._lib.me_server_create(ctypes.byref(cfg), ctypes.byref(h)), "me_server_create")
+        self._h = h
+        self.shapes = {}
+
+    def open_stream(self, W: int, H: int, p: int, qp: int = 28, prm: AcbmParams | None = None) -> int:
+        sid = ctypes.c_int()
+        _check(self._lib.me_server_open_stream(self._h, W, H, p,
+                                               None if prm is None else ctypes.byref(prm),
+                                               int(qp), ctypes.byref(sid)), "me_server_open_stream")
+        self.shapes[sid.value] = (W, H)
+        return sid.value
+
+    def submit(self, stream_id: int, frame) -> int:
+        import numpy as np
+        W, H = self.shapes[stream_id]
+        f = np.ascontiguousarray(frame, dtype=np.uint8)
+        if f.shape != (H, W):
+            raise ValueError(f"frame must be [{H}, {W}] uint8")
+        rid = ctypes.c_longlong()
+        _check(self._lib.me_server_submit(self._h, stream_id, f.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(rid)), "me_server_submit")
+        return rid.value
+
+    def _result(self, stream_id):
+        import numpy as np
+        W, H = self.shapes[stream_id]
+        BH, BW = H // self.M, W // self.N
+        out = dict(mv=np.zeros((BH, BW, 2), np.int16), J=np.zeros((BH, BW), np.uint32),
+                   mask=np.zeros((BH, BW), np.uint8), sad=np.zeros((BH, BW), np.uint32),
+                   load=np.zeros((BH, BW), np.uint32))
+        res = ServerResult(0, 0, 0.0, *(out[k].ctypes.data_as(ctypes.c_void_p).value
+                                        for k in ("mv", "J", "mask", "sad", "load")))
+        return res, out
+
+    def poll(self, request_id: int, stream_id: int):
+        """None while pending, else (has_result, latency_ms, arrays)."""
+        res, out = self._result(stream_id)
+        st = self._lib.me_server_poll(self._h, request_id, ctypes.byref(res))
+        if st == 6:
+            return None
+        _check(st, "me_server_poll")
+        return bool(res.has_result), res.latency_ms, out
+
+    def wait(self, request_id: int, stream_id: int, timeout_ms: int = 10000):
+        res, out = self._result(stream_id)
+        st = self._lib.me_server_wait(self._h, request_id, int(timeout_ms), ctypes.byref(res))
+        _check(st, "me_server_wait")
+        return bool(res.has_result), res.latency_ms, out
+
+    def close_stream(self, stream_id: int):
+        _check(self._lib.me_server_close_stream(self._h, stream_id), "me_server_close_stream")
+
+    def stats(self):
+        used, nstr, pend = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        st = self._lib.me_server_stats(self._h, ctypes.byref(used), ctypes.byref(nstr),
+                                       ctypes.byref(pend))
+        _check(st, "me_server_stats")
+        return used.value, nstr.value, pend.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.me_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

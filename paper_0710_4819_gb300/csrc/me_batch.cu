@@ -22,255 +22,8 @@
 #include <mutex>
 #include <vector>
 
-#include "me_device.cuh"
-#include "me_host.h"
-#include "me_search.cuh"
+#include "me_batch.cuh"
 
-namespace me {
-
-struct BStream {  // per-run arguments of one stream (copied to the device each run)
-  const uint8_t* cur;
-  const uint8_t* ref;
-  const int16_t* prev;
-  int16_t* mv;
-  uint32_t* J;
-  uint8_t* mask;
-  uint32_t* sad;
-  uint32_t* load;
-  uint32_t lam;
-  int32_t alpha, beta, gnum, gden, qp, refine;
-};
-
-struct BShape {  // fixed per stream
-  int W, H, p;
-  PadGeom pg;
-  uint8_t* refpad;
-  uint32_t* intra;
-  int* flags;
-  long long pad_base;  // first 16-byte chunk of this stream in the flat pad index
-  int blk_base;        // first block of this stream in the flat block index
-};
-
-struct BSegment {  // ACBM: the blocks of one wave of one stream
-  int stream, wave, ylo, count, item_base;
-};
-
-struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block
-  int stream, by, bx0, nb, G;
-};
-
-struct BCtrl {
-  int epoch;
-  int next;
-  int error;
-  int err_item;
-  long long timeout_ns;
-  int skip_stream, skip_block;  // fault injection: never publish this block
-};
-
-__device__ __forceinline__ long long global_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__global__ void k_batch_begin(BCtrl* c) {
-  c->epoch += 1;
-  c->next = 0;
-  c->error = 0;
-  c->err_item = -1;
-}
-
-__global__ void k_batch_pad(const BShape* __restrict__ shp, const BStream* __restrict__ st,
-                            int nstreams, long long total) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nstreams - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (shp[mid].pad_base <= i) lo = mid; else hi = mid - 1;
-    }
-    const BShape& s = shp[lo];
-    const long long k = i - s.pad_base;
-    const int chunks = s.pg.pitch / 16;
-    const int y = (int)(k / chunks), cx = (int)(k % chunks) * 16;
-    const uint8_t* src = st[lo].ref + (size_t)clampi(y - s.pg.P, 0, s.H - 1) * s.W;
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      uint32_t v = 0;
-#pragma unroll
-      for (int b = 0; b < 4; b++)
-        v |= (uint32_t)src[clampi(cx + 4 * q + b - s.pg.P, 0, s.W - 1)] << (8 * b);
-      w[q] = v;
-    }
-    *reinterpret_cast<uint4*>(s.refpad + (size_t)y * s.pg.pitch + cx) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-template <int N, int M>
-__global__ void __launch_bounds__(256) k_batch_intra(const BShape* __restrict__ shp,
-                                                     const BStream* __restrict__ st, int nstreams,
-                                                     int total_blocks) {
-  const int lane = threadIdx.x & 31;
-  for (int g = blockIdx.x * 8 + (threadIdx.x >> 5); g < total_blocks; g += gridDim.x * 8) {
-    int lo = 0, hi = nstreams - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (shp[mid].blk_base <= g) lo = mid; else hi = mid - 1;
-    }
-    const BShape& s = shp[lo];
-    const int b = g - s.blk_base, BW = s.W / N;
-    const uint32_t v = warp_intra_sad<N, M>(st[lo].cur, s.W, (b % BW) * N, (b / BW) * M);
-    if (lane == 0) s.intra[b] = v;
-  }
-}
-
-template <int N, int M, int T>
-__global__ void __launch_bounds__(256, 2) k_fsbm_persist(const BShape* __restrict__ shp,
-                                                      const BStream* __restrict__ st,
-                                                      const BFsEntry* __restrict__ ent, int nent,
-                                                      BCtrl* ctrl) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ unsigned long long keys[16];
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->next, 1);
-    __syncthreads();
-    const int i = s_item;
-    __syncthreads();
-    if (i >= nent) break;
-    const BFsEntry e = ent[i];
-    const BShape& s = shp[e.stream];
-    const BStream& a = st[e.stream];
-    const FsGeom g = fs_geom<N, M, T>(s.p, e.nb, e.G);
-    fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, e.bx0 * N, e.by * M, g, a.lam, smem, keys);
-    if ((int)threadIdx.x < e.nb) {
-      const Decoded d = decode_key(keys[threadIdx.x], s.p, a.lam);
-      const int b = e.by * (s.W / N) + e.bx0 + threadIdx.x;
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      if (a.sad) a.sad[b] = d.sad;
-    }
-  }
-}
-
-template <int N, int M, int T>
-__global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restrict__ shp,
-                                                      const BStream* __restrict__ st,
-                                                      const BSegment* __restrict__ seg, int nseg,
-                                                      int total, BCtrl* ctrl) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ unsigned long long keys[16];
-  __shared__ uint32_t curs[M * (N / 4)];
-  __shared__ int s_item, s_stream, s_b, s_pass, s_load;
-  __shared__ unsigned long long s_key;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
-  const long long timeout = ctrl->timeout_ns;
-  for (;;) {
-    if (tid == 0) {
-      const int i = atomicAdd(&ctrl->next, 1);
-      s_item = i;
-      if (i < total) {
-        int lo = 0, hi = nseg - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
-        }
-        const BSegment sg = seg[lo];
-        const int by = sg.ylo + (i - sg.item_base);
-        const int bx = sg.wave - 2 * by;
-        s_stream = sg.stream;
-        s_b = by * (shp[sg.stream].W / N) + bx;
-      }
-    }
-    __syncthreads();
-    if (s_item >= total) break;
-    const int si = s_stream, b = s_b;
-    const BShape& s = shp[si];
-    const BStream& a = st[si];
-    const int BW = s.W / N;
-    const int bx = b % BW, by = b / BW;
-    if (tid < 32) {
-      // wait until the spatial predictors are final (bounded)
-      if (lane < 4) {
-        const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
-        const int dy = (lane == 0) ? 0 : -1;
-        const int nx = bx + dx, ny = by + dy;
-        if (nx >= 0 && nx < BW && ny >= 0) {
-          const volatile int* f = s.flags + ny * BW + nx;
-          const volatile int* err = &ctrl->error;
-          const long long t0 = global_ns();
-          // after the first wait that gave up, no other wait starts: the step
-          // finishes quickly and reports the error
-          while (*f != epoch && *err == 0) {
-            if (global_ns() - t0 > timeout) {
-              atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
-              atomicExch(&ctrl->err_item, s_item);
-              break;
-            }
-            __nanosleep(64);
-          }
-        }
-      }
-      __syncwarp();
-      __threadfence();
-      const PbmResult r = warp_pbm<N, M>(a.cur, s.refpad, s.pg, s.W, s.H, s.p, a.lam, a.mv, a.prev,
-                                         bx, by, s.intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp,
-                                         a.refine, curs);
-      if (lane == 0) {
-        s_key = r.key;
-        s_pass = r.pass ? 1 : 0;
-        s_load = r.load;
-      }
-    }
-    __syncthreads();
-    const bool pass = s_pass != 0;
-    unsigned long long key = s_key;
-    if (!pass) {
-      const FsGeom g = fs_geom<N, M, T>(s.p, 1, blockDim.x);
-      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, bx * N, by * M, g, a.lam, smem, keys);
-      key = keys[0];
-    }
-    if (tid == 0) {
-      const Decoded d = decode_key(key, s.p, a.lam);
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      a.mask[b] = pass ? 0 : 1;
-      if (a.sad) a.sad[b] = d.sad;
-      if (a.load) a.load[b] = pass ? (uint32_t)s_load : (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
-      __threadfence();
-      if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
-    }
-    __syncthreads();
-  }
-}
-
-// ------------------------------------------------------------------ host side
-
-static const int kBatchThreads = 256;
-
-template <int N, int M, int T>
-static size_t smem_of(int p, int bpc) {
-  return fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, bpc, 32));
-}
-
-// Dispatch over the instantiated (N, M, T) of the persistent kernels.
-#define ME_BATCH_NMT(X)                                                             \
-  X(16, 16, 8) X(16, 16, 11) X(16, 16, 13) X(16, 16, 16) X(16, 8, 8) X(16, 4, 8)    \
-  X(8, 16, 8) X(8, 8, 8) X(8, 4, 8) X(4, 16, 8) X(4, 8, 8) X(4, 4, 8)
-
-static size_t batch_smem(int N, int M, int T, int p, int bpc) {
-#define X(n, m, t) if (N == n && M == m && T == t) return smem_of<n, m, t>(p, bpc);
-  ME_BATCH_NMT(X)
-#undef X
-  return 0;
-}
-
-}  // namespace me
 
 struct me_batch {
   int device = -1;
@@ -282,7 +35,6 @@ struct me_batch {
   int total_items = 0, total_blocks = 0;
   long long total_pad = 0;
   size_t smem_fs = 0, smem_acbm = 0;
-  int grid_fs = 0, grid_acbm = 0;
   // device memory
   void* dmem = nullptr;
   me::BShape* d_shapes = nullptr;
@@ -303,23 +55,108 @@ struct me_batch {
 
 namespace me {
 
-static int batch_finalize(me_batch* b) {
-  // T: the run length that wastes the fewest candidate rows, weighted by work
-  static const int kT16b[] = {8, 11, 13, 16};
-  if (b->N == 16 && b->M == 16) {
-    double best = 1e300;
-    for (int T : kT16b) {
-      double waste = 0;
-      for (const BShape& s : b->shapes) {
-        const int n = 2 * s.p + 1, nseg = (n + T - 1) / T;
-        const double blocks = (double)(s.W / b->N) * (s.H / b->M);
-        waste += blocks * n * (nseg * T + b->M - 1) * (1.0 + 4.0 / T);
-      }
-      if (waste < best * 0.999) { best = waste; b->T = T; }
+// Occupancy-sized persistent grids, cached per kernel and dynamic smem size.
+static std::mutex g_grid_mu;
+struct GridKey {
+  const void* fn;
+  size_t smem;
+  int dev, grid;
+};
+static std::vector<GridKey> g_grids;
+
+static int persistent_grid(const void* fn, size_t smem, int* grid) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_grid_mu);
+  for (const GridKey& k : g_grids)
+    if (k.fn == fn && k.smem == smem && k.dev == dev) {
+      *grid = k.grid;
+      return ME_OK;
     }
-  } else {
-    b->T = 8;
+  int nsm = 0, per_sm = 0;
+  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  ME_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem));
+  *grid = std::max(1, per_sm) * nsm;
+  g_grids.push_back(GridKey{fn, smem, dev, *grid});
+  return ME_OK;
+}
+
+int batch_choose_T(int N, int M, const std::vector<BShape>& shapes) {
+  static const int kT16b[] = {8, 11, 13, 16};
+  if (!(N == 16 && M == 16)) return 8;
+  int bestT = 13;
+  double best = 1e300;
+  for (int T : kT16b) {
+    double waste = 0;
+    for (const BShape& s : shapes) {
+      const int n = 2 * s.p + 1, nseg = (n + T - 1) / T;
+      const double blocks = (double)(s.W / N) * (s.H / M);
+      waste += blocks * n * (nseg * T + M - 1) * (1.0 + 4.0 / T);
+    }
+    if (waste < best * 0.999) { best = waste; bestT = T; }
   }
+  return bestT;
+}
+
+int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
+                     const BStream* streams, int nstreams, long long total_pad, int total_blocks,
+                     const BSegment* segs, int nseg, int total_items, size_t smem, cudaStream_t s) {
+  k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
+  ME_CUDA(cudaGetLastError());
+  const int gp = (int)std::max<long long>(1, std::min<long long>((total_pad + 255) / 256, 152 * 16));
+  k_batch_pad<<<gp, 256, 0, s>>>(shapes, streams, nstreams, total_pad);
+  ME_CUDA(cudaGetLastError());
+  const int gi = std::max(1, std::min((total_blocks + 7) / 8, 152 * 16));
+  int st = ME_ERR_ARG;
+#define X(n_, m_)                                                                              \
+  if (N == n_ && M == m_) {                                                                    \
+    k_batch_intra<n_, m_><<<gi, 256, 0, s>>>(shapes, streams, nstreams, total_blocks);         \
+    st = ME_OK;                                                                                \
+  }
+  X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && T == t_) {                                                         \
+    int grid = 0;                                                                              \
+    st = persistent_grid((const void*)k_acbm_persist<n_, m_, t_>, smem, &grid);                \
+    if (st == ME_OK)                                                                           \
+      k_acbm_persist<n_, m_, t_><<<grid, kBatchThreads, smem, s>>>(shapes, streams, segs, nseg, \
+                                                                   total_items, ctrl);         \
+  }
+  ME_BATCH_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
+                     const BStream* streams, const BFsEntry* ent, int nent, size_t smem,
+                     cudaStream_t s) {
+  k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
+  ME_CUDA(cudaGetLastError());
+  int st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && T == t_) {                                                         \
+    int grid = 0;                                                                              \
+    st = persistent_grid((const void*)k_fsbm_persist<n_, m_, t_>, smem, &grid);                \
+    if (st == ME_OK)                                                                           \
+      k_fsbm_persist<n_, m_, t_><<<grid, kBatchThreads, smem, s>>>(shapes, streams, ent, nent,  \
+                                                                   ctrl);                      \
+  }
+  ME_BATCH_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+static int batch_finalize(me_batch* b) {
+  b->T = batch_choose_T(b->N, b->M, b->shapes);
   // FSBM work entries: threads per block (and so blocks per CTA) per stream
   b->fsent.clear();
   size_t smem_fs = 0;
@@ -357,7 +194,9 @@ static int batch_finalize(me_batch* b) {
   }
   b->total_items = base;
   size_t smem_a = 0;
-  for (const BShape& s : b->shapes) smem_a = std::max(smem_a, batch_smem(b->N, b->M, b->T, s.p, 1));
+  for (const BShape& s : b->shapes)
+    smem_a = std::max({smem_a, batch_smem(b->N, b->M, b->T, s.p, 1),
+                       (size_t)4 * pbm_win_words(b->N, b->M, s.p)});
   b->smem_acbm = smem_a;
   // device memory: control, tables, per-stream scratch
   const size_t n = b->shapes.size();
@@ -412,24 +251,16 @@ static int batch_finalize(me_batch* b) {
   ME_CUDA(cudaMallocHost(&b->h_ctrl, sizeof(BCtrl)));
   for (int i = 0; i < me_batch::kRing; i++)
     ME_CUDA(cudaEventCreateWithFlags(&b->staged[i], cudaEventDisableTiming));
-  // persistent grids: as many CTAs as fit on the device at once
-  int dev = 0, nsm = 0;
+  int dev = 0;
   ME_CUDA(cudaGetDevice(&dev));
-  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   b->device = dev;
-  auto occ_grid = [&](const void* fn, size_t smem, int* grid) -> int {
-    ME_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem));
-    *grid = std::max(1, per_sm) * nsm;
-    return ME_OK;
-  };
-  int st = ME_ERR_ARG;
+  // size the persistent grids now, outside any capture
+  int st = ME_ERR_ARG, grid = 0;
 #define X(n_, m_, t_)                                                                          \
   if (b->N == n_ && b->M == m_ && b->T == t_) {                                                \
-    st = occ_grid((const void*)k_fsbm_persist<n_, m_, t_>, b->smem_fs, &b->grid_fs);           \
+    st = persistent_grid((const void*)k_fsbm_persist<n_, m_, t_>, b->smem_fs, &grid);          \
     if (st == ME_OK)                                                                           \
-      st = occ_grid((const void*)k_acbm_persist<n_, m_, t_>, b->smem_acbm, &b->grid_acbm);     \
+      st = persistent_grid((const void*)k_acbm_persist<n_, m_, t_>, b->smem_acbm, &grid);      \
   }
   ME_BATCH_NMT(X)
 #undef X
@@ -438,36 +269,12 @@ static int batch_finalize(me_batch* b) {
 
 // Enqueues one step of `mode` (no argument staging).
 static int batch_enqueue(me_batch* b, int mode, cudaStream_t s) {
-  const int ns = (int)b->shapes.size();
-  k_batch_begin<<<1, 1, 0, s>>>(b->d_ctrl);
-  ME_CUDA(cudaGetLastError());
-  if (mode == ME_MODE_ACBM) {
-    const long long chunks = b->total_pad;
-    const int grid = (int)std::min<long long>((chunks + 255) / 256, 152 * 16);
-    k_batch_pad<<<grid, 256, 0, s>>>(b->d_shapes, b->d_streams, ns, chunks);
-    ME_CUDA(cudaGetLastError());
-    const int gi = std::min((b->total_blocks + 7) / 8, 152 * 16);
-#define X(n_, m_)                                                                              \
-  if (b->N == n_ && b->M == m_)                                                                \
-    k_batch_intra<n_, m_><<<gi, 256, 0, s>>>(b->d_shapes, b->d_streams, ns, b->total_blocks);
-    X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
-#undef X
-    ME_CUDA(cudaGetLastError());
-  }
-#define X(n_, m_, t_)                                                                          \
-  if (b->N == n_ && b->M == m_ && b->T == t_) {                                                \
-    if (mode == ME_MODE_FSBM)                                                                  \
-      k_fsbm_persist<n_, m_, t_><<<b->grid_fs, kBatchThreads, b->smem_fs, s>>>(                \
-          b->d_shapes, b->d_streams, b->d_fsent, (int)b->fsent.size(), b->d_ctrl);             \
-    else                                                                                       \
-      k_acbm_persist<n_, m_, t_><<<b->grid_acbm, kBatchThreads, b->smem_acbm, s>>>(            \
-          b->d_shapes, b->d_streams, b->d_segs, (int)b->segs.size(), b->total_items,           \
-          b->d_ctrl);                                                                          \
-  }
-  ME_BATCH_NMT(X)
-#undef X
-  ME_CUDA(cudaGetLastError());
-  return ME_OK;
+  if (mode == ME_MODE_FSBM)
+    return launch_fsbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent,
+                            (int)b->fsent.size(), b->smem_fs, s);
+  return launch_acbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams,
+                          (int)b->shapes.size(), b->total_pad, b->total_blocks, b->d_segs,
+                          (int)b->segs.size(), b->total_items, b->smem_acbm, s);
 }
 
 }  // namespace me

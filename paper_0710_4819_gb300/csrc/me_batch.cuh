@@ -1,0 +1,274 @@
+// me_batch.cuh -- device structures and kernels of the multi-stream
+// persistent forms (the batch API and the server): stream tables, work
+// segments, the prologue kernels and the persistent FSBM / ACBM kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "me_device.cuh"
+#include "me_host.h"
+#include "me_search.cuh"
+
+namespace me {
+
+struct BStream {  // per-run arguments of one stream (copied to the device each run)
+  const uint8_t* cur;
+  const uint8_t* ref;
+  const int16_t* prev;
+  int16_t* mv;
+  uint32_t* J;
+  uint8_t* mask;
+  uint32_t* sad;
+  uint32_t* load;
+  uint32_t lam;
+  int32_t alpha, beta, gnum, gden, qp, refine;
+};
+
+struct BShape {  // fixed per stream
+  int W, H, p;
+  PadGeom pg;
+  uint8_t* refpad;
+  uint32_t* intra;
+  int* flags;
+  long long pad_base;  // first 16-byte chunk of this stream in the flat pad index
+  int blk_base;        // first block of this stream in the flat block index
+};
+
+struct BSegment {  // ACBM: the blocks of one wave of one stream
+  int stream, wave, ylo, count, item_base;
+};
+
+struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block
+  int stream, by, bx0, nb, G;
+};
+
+struct BCtrl {
+  int epoch;
+  int next;
+  int error;
+  int err_item;
+  long long timeout_ns;
+  int skip_stream, skip_block;  // fault injection: never publish this block
+};
+
+static __device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+static __global__ void k_batch_begin(BCtrl* c, int epoch) {
+  c->epoch = epoch > 0 ? epoch : c->epoch + 1;
+  c->next = 0;
+  c->error = 0;
+  c->err_item = -1;
+}
+
+static __global__ void k_batch_pad(const BShape* __restrict__ shp, const BStream* __restrict__ st,
+                            int nstreams, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nstreams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (shp[mid].pad_base <= i) lo = mid; else hi = mid - 1;
+    }
+    const BShape& s = shp[lo];
+    const long long k = i - s.pad_base;
+    const int chunks = s.pg.pitch / 16;
+    const int y = (int)(k / chunks), cx = (int)(k % chunks) * 16;
+    const uint8_t* src = st[lo].ref + (size_t)clampi(y - s.pg.P, 0, s.H - 1) * s.W;
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; b++)
+        v |= (uint32_t)src[clampi(cx + 4 * q + b - s.pg.P, 0, s.W - 1)] << (8 * b);
+      w[q] = v;
+    }
+    *reinterpret_cast<uint4*>(s.refpad + (size_t)y * s.pg.pitch + cx) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int N, int M>
+__global__ void __launch_bounds__(256) k_batch_intra(const BShape* __restrict__ shp,
+                                                     const BStream* __restrict__ st, int nstreams,
+                                                     int total_blocks) {
+  const int lane = threadIdx.x & 31;
+  for (int g = blockIdx.x * 8 + (threadIdx.x >> 5); g < total_blocks; g += gridDim.x * 8) {
+    int lo = 0, hi = nstreams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (shp[mid].blk_base <= g) lo = mid; else hi = mid - 1;
+    }
+    const BShape& s = shp[lo];
+    const int b = g - s.blk_base, BW = s.W / N;
+    const uint32_t v = warp_intra_sad<N, M>(st[lo].cur, s.W, (b % BW) * N, (b / BW) * M);
+    if (lane == 0) s.intra[b] = v;
+  }
+}
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(256, 2) k_fsbm_persist(const BShape* __restrict__ shp,
+                                                      const BStream* __restrict__ st,
+                                                      const BFsEntry* __restrict__ ent, int nent,
+                                                      BCtrl* ctrl) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->next, 1);
+    __syncthreads();
+    const int i = s_item;
+    __syncthreads();
+    if (i >= nent) break;
+    const BFsEntry e = ent[i];
+    const BShape& s = shp[e.stream];
+    const BStream& a = st[e.stream];
+    const FsGeom g = fs_geom<N, M, T>(s.p, e.nb, e.G);
+    fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, e.bx0 * N, e.by * M, g, a.lam, smem, keys);
+    if ((int)threadIdx.x < e.nb) {
+      const Decoded d = decode_key(keys[threadIdx.x], s.p, a.lam);
+      const int b = e.by * (s.W / N) + e.bx0 + threadIdx.x;
+      a.mv[2 * b] = (int16_t)d.mvx;
+      a.mv[2 * b + 1] = (int16_t)d.mvy;
+      a.J[b] = d.J;
+      if (a.sad) a.sad[b] = d.sad;
+    }
+  }
+}
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restrict__ shp,
+                                                      const BStream* __restrict__ st,
+                                                      const BSegment* __restrict__ seg, int nseg,
+                                                      int total, BCtrl* ctrl) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  __shared__ uint32_t curs[M * (N / 4)];
+  __shared__ int s_item, s_stream, s_b, s_pass, s_load;
+  __shared__ unsigned long long s_key;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
+  const long long timeout = ctrl->timeout_ns;
+  for (;;) {
+    if (tid == 0) {
+      const int i = atomicAdd(&ctrl->next, 1);
+      s_item = i;
+      if (i < total) {
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
+        }
+        const BSegment sg = seg[lo];
+        const int by = sg.ylo + (i - sg.item_base);
+        const int bx = sg.wave - 2 * by;
+        s_stream = sg.stream;
+        s_b = by * (shp[sg.stream].W / N) + bx;
+      }
+    }
+    __syncthreads();
+    if (s_item >= total) break;
+    const int si = s_stream, b = s_b;
+    const BShape& s = shp[si];
+    const BStream& a = st[si];
+    const int BW = s.W / N;
+    const int bx = b % BW, by = b / BW;
+    if (tid < 32) {
+      // wait until the spatial predictors are final (bounded)
+      if (lane < 4) {
+        const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
+        const int dy = (lane == 0) ? 0 : -1;
+        const int nx = bx + dx, ny = by + dy;
+        if (nx >= 0 && nx < BW && ny >= 0) {
+          const volatile int* f = s.flags + ny * BW + nx;
+          const volatile int* err = &ctrl->error;
+          const long long t0 = global_ns();
+          // after the first wait that gave up, no other wait starts: the step
+          // finishes quickly and reports the error
+          while (*f != epoch && *err == 0) {
+            if (global_ns() - t0 > timeout) {
+              atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+              atomicExch(&ctrl->err_item, s_item);
+              break;
+            }
+            __nanosleep(20);
+          }
+        }
+      }
+      __syncwarp();
+      __threadfence();
+      const PbmResult r = warp_pbm<N, M>(a.cur, s.refpad, s.pg, s.W, s.H, s.p, a.lam, a.mv, a.prev,
+                                         bx, by, s.intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp,
+                                         a.refine, curs, smem);
+      if (lane == 0) {
+        s_key = r.key;
+        s_pass = r.pass ? 1 : 0;
+        s_load = r.load;
+      }
+    }
+    __syncthreads();
+    const bool pass = s_pass != 0;
+    unsigned long long key = s_key;
+    if (!pass) {
+      const FsGeom g = fs_geom<N, M, T>(s.p, 1, blockDim.x);
+      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, bx * N, by * M, g, a.lam, smem, keys);
+      key = keys[0];
+    }
+    if (tid == 0) {
+      const Decoded d = decode_key(key, s.p, a.lam);
+      a.mv[2 * b] = (int16_t)d.mvx;
+      a.mv[2 * b + 1] = (int16_t)d.mvy;
+      a.J[b] = d.J;
+      a.mask[b] = pass ? 0 : 1;
+      if (a.sad) a.sad[b] = d.sad;
+      if (a.load) a.load[b] = pass ? (uint32_t)s_load : (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
+      __threadfence();
+      if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+constexpr int kBatchThreads = 256;
+
+template <int N, int M, int T>
+inline size_t smem_of(int p, int bpc) {
+  return fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, bpc, 32));
+}
+
+// Dispatch over the instantiated (N, M, T) of the persistent kernels.
+#define ME_BATCH_NMT(X)                                                             \
+  X(16, 16, 8) X(16, 16, 11) X(16, 16, 13) X(16, 16, 16) X(16, 8, 8) X(16, 4, 8)    \
+  X(8, 16, 8) X(8, 8, 8) X(8, 4, 8) X(4, 16, 8) X(4, 8, 8) X(4, 4, 8)
+
+inline size_t batch_smem(int N, int M, int T, int p, int bpc) {
+#define X(n, m, t) if (N == n && M == m && T == t) return smem_of<n, m, t>(p, bpc);
+  ME_BATCH_NMT(X)
+#undef X
+  return 0;
+}
+
+
+// Run length for a set of streams: fewest wasted candidate rows, weighted by
+// each stream's block count (16x16 blocks choose among 8, 11, 13, 16).
+int batch_choose_T(int N, int M, const std::vector<BShape>& shapes);
+
+// Enqueues one ACBM step over the streams in the device tables: the begin
+// kernel (epoch = `epoch`, or the previous epoch + 1 when epoch <= 0), the
+// padding and Intra_SAD prologue, and the persistent kernel.
+int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
+                     const BStream* streams, int nstreams, long long total_pad, int total_blocks,
+                     const BSegment* segs, int nseg, int total_items, size_t smem, cudaStream_t s);
+
+// Enqueues one FSBM step (begin kernel + persistent kernel).
+int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
+                     const BStream* streams, const BFsEntry* ent, int nent, size_t smem,
+                     cudaStream_t s);
+
+}  // namespace me

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
                                                   int* __restrict__ fail_count,
                                                   int* __restrict__ fail_list) {
   __shared__ uint32_t curs[4][M * (N / 4)];
+  extern __shared__ __align__(16) uint32_t wins[];   // 4 x pbm_win_words
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * 4 + warp;
   if (idx >= count) return;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
   const int BW = W / N, b = by * BW + bx;
   const PbmResult r = warp_pbm<N, M>(a.cur, refpad, pg, W, H, p, a.lam, a.mv, a.prev, bx, by,
                                      intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp, a.refine,
-                                     curs[warp]);
+                                     curs[warp], wins + warp * pbm_win_words(N, M, p));
   if (lane == 0) {
     if (r.pass) {
       const Decoded d = decode_key(r.key, p, a.lam);
@@ -413,8 +414,12 @@ template <int N, int M>
 static int launch_pbm_wave_t(const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
                              const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
                              int* cnt, int* list, cudaStream_t s) {
-  k_pbm_wave<N, M><<<(count + 3) / 4, 128, 0, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo, count,
-                                                   cnt, list);
+  const size_t smem = 4 * 4 * (size_t)pbm_win_words(N, M, p);
+  if (smem > 48 * 1024)
+    ME_CUDA(cudaFuncSetAttribute(k_pbm_wave<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  k_pbm_wave<N, M><<<(count + 3) / 4, 128, smem, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo,
+                                                      count, cnt, list);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }

@@ -70,24 +70,49 @@ __device__ __forceinline__ uint32_t warp_intra_sad(const uint8_t* __restrict__ c
 }
 
 // ---------------------------------------------------------------------------
-// One candidate's SAD computed by a single lane from the padded reference:
-// M rows of N/4 words, each row fetched as N/4+1 aligned words and shifted
-// into place with a funnel shift.  curs holds the current block (M x N/4).
+// The search window of one block, staged in shared memory by one warp so that
+// the PBM candidates are evaluated without further global-memory round trips.
+// The window covers padded-reference columns [A, A + 16*chunks) with A the
+// 16-byte boundary at or left of the block's column x0 + P - p, and rows
+// y0 + P - p .. y0 + P + p + M - 1.
 // ---------------------------------------------------------------------------
+struct PbmWin {
+  int s0;      // byte offset of column x0 - p inside the staged row
+  int chunks;  // 16-byte chunks per staged row
+  int wp;      // staged row pitch in words (4 * chunks)
+  int rows;    // M + 2p
+};
+
+__host__ __device__ inline PbmWin pbm_win(int N, int M, int p, int x0, int P) {
+  PbmWin w;
+  const int X = x0 + P - p;
+  w.s0 = X & 15;
+  w.chunks = (w.s0 + N + 2 * p + 4 + 15) / 16;  // + one spare word for the funnel shift
+  w.wp = 4 * w.chunks;
+  w.rows = M + 2 * p;
+  return w;
+}
+
+// Upper bound of the staged words for any block (for shared-memory sizing).
+__host__ __device__ inline int pbm_win_words(int N, int M, int p) {
+  return 4 * ((15 + N + 2 * p + 4 + 15) / 16) * (M + 2 * p);
+}
+
+// One candidate's SAD computed by a single lane from the staged window: M rows
+// of N/4 words, each row read as N/4+1 words and shifted into place.
 template <int N, int M>
-__device__ __forceinline__ uint32_t lane_sad(const uint32_t* curs, const uint8_t* __restrict__ refpad,
-                                             const PadGeom& pg, int x0, int y0, int mvx, int mvy) {
+__device__ __forceinline__ uint32_t lane_sad_win(const uint32_t* curs, const uint32_t* win,
+                                                 const PbmWin& wg, int p, int mvx, int mvy) {
   constexpr int NW = N / 4;
-  const int xs = x0 + pg.P + mvx, ys = y0 + pg.P + mvy;
-  const uint32_t* rowp = reinterpret_cast<const uint32_t*>(refpad + (size_t)ys * pg.pitch) + (xs >> 2);
-  const int stride = pg.pitch >> 2;
-  const unsigned sh = 8u * (unsigned)(xs & 3);
+  const int o = wg.s0 + p + mvx;
+  const uint32_t* rp = win + (p + mvy) * wg.wp + (o >> 2);
+  const unsigned sh = 8u * (unsigned)(o & 3);
   uint32_t acc = 0;
 #pragma unroll
   for (int j = 0; j < M; j++) {
     uint32_t wv[NW + 1];
 #pragma unroll
-    for (int w = 0; w <= NW; w++) wv[w] = __ldg(rowp + j * stride + w);
+    for (int w = 0; w <= NW; w++) wv[w] = rp[j * wg.wp + w];
 #pragma unroll
     for (int w = 0; w < NW; w++) acc = sad4(curs[j * NW + w], __funnelshift_r(wv[w], wv[w + 1], sh), acc);
   }
@@ -95,11 +120,11 @@ __device__ __forceinline__ uint32_t lane_sad(const uint32_t* curs, const uint8_t
 }
 
 template <int N, int M>
-__device__ __forceinline__ unsigned long long lane_key(const uint32_t* curs, const uint8_t* refpad,
-                                                       const PadGeom& pg, int x0, int y0, int mvx,
-                                                       int mvy, int p, uint32_t lam) {
-  uint32_t s = lane_sad<N, M>(curs, refpad, pg, x0, y0, mvx, mvy);
-  uint32_t J = 256u * s + lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy));
+__device__ __forceinline__ unsigned long long lane_key(const uint32_t* curs, const uint32_t* win,
+                                                       const PbmWin& wg, int mvx, int mvy, int p,
+                                                       uint32_t lam) {
+  const uint32_t s = lane_sad_win<N, M>(curs, win, wg, p, mvx, mvy);
+  const uint32_t J = 256u * s + lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy));
   return make_key(J, mvx, mvy, p);
 }
 
@@ -118,7 +143,8 @@ struct PbmResult {
 // 4-12 the 3x3 temporal ones, lane 13 the zero vector; each lane evaluates its
 // candidate unless a lower lane holds the same clipped position.  The ring
 // (lanes 0-7) skips positions already evaluated.  curs: this warp's staging
-// area for the current block (M*N/4 words of shared memory).
+// area for the current block (M*N/4 words of shared memory); win: this warp's
+// window area (pbm_win_words words).
 // ---------------------------------------------------------------------------
 template <int N, int M>
 __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ refpad,
@@ -126,7 +152,7 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
                               const int16_t* field, const int16_t* __restrict__ prev,
                               int bx, int by, uint32_t intra_x, int32_t alpha, int32_t beta,
                               int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
-                              uint32_t* curs) {
+                              uint32_t* curs, uint32_t* win) {
   constexpr int NW = N / 4;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -134,6 +160,20 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
   const int x0 = bx * N, y0 = by * M;
   for (int i = lane; i < M * NW; i += 32)
     curs[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
+  // stage the search window: each lane copies 16-byte chunks, several rows
+  // per pass, all loads of a pass in flight together
+  const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
+  {
+    const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
+    const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
+    const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
+    if (rl < rpp) {
+      for (int r = rl; r < wg.rows; r += rpp) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * pg.pitch) + cl);
+        *reinterpret_cast<uint4*>(win + r * wg.wp + 4 * cl) = v;
+      }
+    }
+  }
   __syncwarp();
 
   // step 1: predictors
@@ -175,7 +215,7 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
   }
   const bool eval = valid && !dup;
   // step 2: best predictor by J
-  unsigned long long key = eval ? lane_key<N, M>(curs, refpad, pg, x0, y0, cx, cy, p, lam) : kNoKey;
+  unsigned long long key = eval ? lane_key<N, M>(curs, win, wg, cx, cy, p, lam) : kNoKey;
   unsigned long long best = warp_min64(key);
   int load = __popc(__ballot_sync(FULL, eval));
   // step 3: +-1 integer ring around the best predictor
@@ -198,7 +238,7 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
       rdup |= (l < lane) && (v == rcode);
     }
     const bool reval = lane < 8 && !rdup;
-    unsigned long long k2 = reval ? lane_key<N, M>(curs, refpad, pg, x0, y0, rx, ry, p, lam) : kNoKey;
+    unsigned long long k2 = reval ? lane_key<N, M>(curs, win, wg, rx, ry, p, lam) : kNoKey;
     best = umin64(best, warp_min64(k2));
     load += __popc(__ballot_sync(FULL, reval));
   }
