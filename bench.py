@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve"],
+                    help="1080p: the default line; batch64 / serve: the multi-stream forms")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
+    ap.add_argument("--seconds", type=float, default=4.0, help="serve: arrival window")
     return ap.parse_args()
 
 
@@ -159,8 +163,162 @@ def cpu_threads():
 
 
 # ------------------------------------------------------------------ main
+def _item(me, cur, ref, prev, out, lam, prm):
+    it = me.BatchItem()
+    it.cur, it.ref = cur.data_ptr(), ref.data_ptr()
+    it.prev_mv = None if prev is None else prev.data_ptr()
+    it.mv_out, it.J_out, it.mask_out = out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr()
+    it.sad_out, it.load_out = out[3].data_ptr(), out[4].data_ptr()
+    it.lambda_q8 = lam
+    it.prm = prm
+    return it
+
+
+def run_batch64(args):
+    """The 64-stream mix (24 QCIF p16, 24 CIF p16, 12 720p p32, 4 2160p p64):
+    one persistent launch per step (captured graph) against the plain per-frame
+    ACBM/FSBM calls on the same frames; outputs compared."""
+    import torch
+    import synth
+    import paper_0710_4819_gb300 as me
+    specs = synth.batch_mix()
+    n_frames = 1 + max(2, args.steps)
+    seqs = [torch.from_numpy(synth.stream_frames(s, n_frames)).cuda() for s in specs]
+    lam = me.me_lambda_q8(QP)
+    prm = me.params(qp=QP)
+
+    def outs(s):
+        BH, BW = s.height // M, s.w // N
+        return [torch.empty((BH, BW, 2), dtype=torch.int16, device="cuda"),
+                torch.empty((BH, BW), dtype=torch.int32, device="cuda"),
+                torch.empty((BH, BW), dtype=torch.uint8, device="cuda"),
+                torch.empty((BH, BW), dtype=torch.int32, device="cuda"),
+                torch.empty((BH, BW), dtype=torch.int32, device="cuda")]
+
+    res = {}
+    stream = torch.cuda.current_stream()
+    for mode, name in ((0, "fsbm"), (1, "acbm")):
+        b = me.Batch()
+        for s in specs:
+            b.add_stream(s.w, s.height, N, M, s.p)
+        o_b = [[outs(s) for s in specs] for _ in range(n_frames)]
+        o_p = [[outs(s) for s in specs] for _ in range(n_frames)]
+
+        def batch_step(t):
+            items = [_item(me, seqs[i][t], seqs[i][t - 1],
+                           o_b[t - 1][i][0] if (mode == 1 and t >= 2) else None, o_b[t][i], lam, prm)
+                     for i in range(len(specs))]
+            b.run(mode, items)
+
+        def plain_step(t):
+            for i, s in enumerate(specs):
+                o = o_p[t][i]
+                if mode == 0:
+                    me.me_fsbm(seqs[i][t], seqs[i][t - 1], N, M, s.p, lam, out=(o[0], o[1], o[3]))
+                else:
+                    prev = o_p[t - 1][i][0] if t >= 2 else None
+                    me.me_acbm(seqs[i][t], seqs[i][t - 1], N, M, s.p, lam, prm, prev_mv=prev,
+                               out=tuple(o))
+        for fn in (batch_step, plain_step):       # warm-up (plans, graphs)
+            fn(1)
+        b.sync()
+        torch.cuda.synchronize()
+        timings = {}
+        for fn, key in ((batch_step, "batched"), (plain_step, "plain")):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for t in range(1, n_frames):
+                fn(t)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            timings[key] = e0.elapsed_time(e1) / (n_frames - 1)
+        b.sync()
+        same = all(torch.equal(x, y) for t in range(1, n_frames) for i in range(len(specs))
+                   for k, (x, y) in enumerate(zip(o_b[t][i], o_p[t][i])) if mode == 1 or k in (0, 1, 3))
+        b.close()
+        res[name] = {"batched_ms_per_step": timings["batched"], "plain_ms_per_step": timings["plain"],
+                     "batched_frames_per_s": len(specs) / (timings["batched"] * 1e-3),
+                     "plain_frames_per_s": len(specs) / (timings["plain"] * 1e-3),
+                     "speedup": timings["plain"] / timings["batched"], "outputs_identical": same}
+    absd = sum((s.w // N) * (s.height // M) * (2 * s.p + 1) ** 2 * N * M for s in specs)
+    line = {"metric": "64-stream mix frames/s (one persistent launch per step vs plain per-frame calls)",
+            "value": res["acbm"]["batched_frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "steps": n_frames - 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "batch64: 24 QCIF p16, 24 CIF p16, 12 720p p32, 4 2160p p64, 16x16, Qp 28"},
+            "fsbm": res["fsbm"], "acbm": res["acbm"],
+            "fsbm_absdiff_per_s_T": absd / (res["fsbm"]["batched_ms_per_step"] * 1e-3) / 1e12}
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """Continuous-batching server over 200 streams (CIF p16 : 720p p32 :
+    1080p p32 = 50 : 35 : 15), Poisson arrivals at --rate for --seconds."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_0710_4819_gb300 as me
+    specs = synth.serving_mix(200)
+    # a few distinct looping sequences per resolution, shared round-robin
+    pool = {}
+    for kind in ("cif", "720p", "1080p"):
+        ex = [s for s in specs if s.name == kind][:4]
+        pool[kind] = [synth.stream_frames(s, 6)[:, :s.height] for s in ex]
+    srv = me.Server(40 << 30, max_inflight=2, mode=1)
+    ids = [srv.open_stream(s.w, s.height, s.p, qp=QP) for s in specs]
+    seq_of = [pool[s.name][i % len(pool[s.name])] for i, s in enumerate(specs)]
+    frame_no = [0] * len(specs)
+    rng = np.random.default_rng(11)
+    # prime every stream with its first frame (no result), then the timed run
+    prime = [srv.submit(ids[i], seq_of[i][0]) for i in range(len(specs))]
+    for i, r in enumerate(prime):
+        srv.wait(r, ids[i], 60000)
+        frame_no[i] = 1
+    n_req = int(args.rate * args.seconds)
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    which = rng.integers(0, len(specs), size=n_req)
+    reqs = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for k in range(n_req):
+        t_next += gaps[k]
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            if t_next - now > 0.0005:
+                time.sleep(t_next - now - 0.0003)
+        i = int(which[k])
+        f = seq_of[i][frame_no[i] % seq_of[i].shape[0]]
+        frame_no[i] += 1
+        reqs.append((i, srv.submit(ids[i], f)))
+    lat = []
+    for i, r in reqs:
+        has, ms, _ = srv.wait(r, ids[i], 120000)
+        lat.append(ms)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    line = {"metric": "serving: frames/s and latency (continuous batching, 200 streams)",
+            "value": len(reqs) / wall, "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serve: 200 streams CIF p16 50% / 720p p32 35% / 1080p p32 15%, "
+                                   f"Poisson {args.rate:.0f} req/s for {args.seconds:.1f} s, budget 40 GB"},
+            "offered_rate": args.rate, "requests": len(reqs),
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "max_ms": lat[-1]}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.workload != "1080p" and args.impl == "native":
+        import torch
+        torch.cuda.set_device(0)
+        import paper_0710_4819_gb300 as me
+        me.load_library(build_if_missing=True)
+        (run_batch64 if args.workload == "batch64" else run_serve)(args)
+        return
     rank, world, local, pg = dist_setup(args.gpus)
     import numpy as np
     import synth

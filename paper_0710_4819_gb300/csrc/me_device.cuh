@@ -184,18 +184,32 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   const int A0 = (wx0 >> 2) << 2;        // floor to a multiple of 4
   const int s0 = wx0 - A0;
   const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
-  for (int r = warp; r < g.rows; r += nwarps) {
-    const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W;
-    uint32_t* dst = wb + r * g.wbw;
-    if (inside) {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(rowp + A0);
-      for (int q = lane; q < g.wbw; q += 32) dst[q] = src[q];
-    } else {
-      for (int q = lane; q < g.wbw; q += 32) {
-        uint32_t v = 0;
+  {
+    // eight independent loads per thread in flight before their stores, so
+    // the window costs about one global-memory round trip, not one per row
+    const int total = g.rows * g.wbw;
+    for (int base = tid; base < total; base += 8 * nthr) {
+      uint32_t v[8];
 #pragma unroll
-        for (int b = 0; b < 4; b++) v |= (uint32_t)rowp[clampi(A0 + 4 * q + b, 0, W - 1)] << (8 * b);
-        dst[q] = v;
+      for (int u = 0; u < 8; u++) {
+        const int i = base + u * nthr;
+        v[u] = 0;
+        if (i < total) {
+          const int r = i / g.wbw, q = i - r * g.wbw;
+          const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W;
+          if (inside) {
+            v[u] = *reinterpret_cast<const uint32_t*>(rowp + A0 + 4 * q);
+          } else {
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+              v[u] |= (uint32_t)rowp[clampi(A0 + 4 * q + b, 0, W - 1)] << (8 * b);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = base + u * nthr;
+        if (i < total) wb[i] = v[u];
       }
     }
   }

@@ -154,29 +154,14 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
                               int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
                               uint32_t* curs, uint32_t* win) {
   constexpr int NW = N / 4;
+  constexpr int CW = (M * NW + 31) / 32;   // current-block words per lane
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int BW = W / N, BH = H / M;
   const int x0 = bx * N, y0 = by * M;
-  for (int i = lane; i < M * NW; i += 32)
-    curs[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
-  // stage the search window: each lane copies 16-byte chunks, several rows
-  // per pass, all loads of a pass in flight together
-  const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
-  {
-    const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
-    const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
-    const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
-    if (rl < rpp) {
-      for (int r = rl; r < wg.rows; r += rpp) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * pg.pitch) + cl);
-        *reinterpret_cast<uint4*>(win + r * wg.wp + 4 * cl) = v;
-      }
-    }
-  }
-  __syncwarp();
 
-  // step 1: predictors
+  // step 1: predictors (their loads are issued first, with the block loads
+  // below, so the warp pays about one global-memory round trip in total)
   int cx = 0, cy = 0;
   bool valid = false;
   if (lane < 4) {
@@ -204,6 +189,41 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
   } else if (lane == 13) {
     valid = true;
   }
+  uint32_t cw[CW];
+#pragma unroll
+  for (int k = 0; k < CW; k++) {
+    const int i = lane + 32 * k;
+    if (i < M * NW)
+      cw[k] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
+  }
+  // the search window: eight 16-byte loads per lane in flight before their stores
+  const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
+  {
+    const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
+    const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
+    const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
+    if (rl < rpp) {
+      for (int r0 = rl; r0 < wg.rows; r0 += 8 * rpp) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const int r = r0 + u * rpp;
+          if (r < wg.rows) v[u] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * pg.pitch) + cl);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const int r = r0 + u * rpp;
+          if (r < wg.rows) *reinterpret_cast<uint4*>(win + r * wg.wp + 4 * cl) = v[u];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CW; k++) {
+    const int i = lane + 32 * k;
+    if (i < M * NW) curs[i] = cw[k];
+  }
+  __syncwarp();
   cx = clampi(cx, -p, p);
   cy = clampi(cy, -p, p);
   const int code = valid ? ((cy + p) << 8) + (cx + p) : -1 - lane;
