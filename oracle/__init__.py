@@ -12,6 +12,7 @@ sections each part follows).
 """
 from __future__ import annotations
 
+import contextvars
 import ctypes
 import os
 import subprocess
@@ -25,6 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libme_oracle.so")
 _lock = threading.Lock()
 _lib = None
+_override = contextvars.ContextVar("oracle_lib", default=None)
 
 
 class AcbmParams(ctypes.Structure):
@@ -54,39 +56,80 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    i16p = ctypes.POINTER(ctypes.c_int16)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    c_int, c_u32 = ctypes.c_int, ctypes.c_uint32
+    lib.oracle_lambda_q8.argtypes = [c_int]
+    lib.oracle_lambda_q8.restype = c_u32
+    lib.oracle_mv_bits.argtypes = [c_int]
+    lib.oracle_mv_bits.restype = c_int
+    lib.oracle_intra_sad.argtypes = [u8p, c_int, c_int, c_int, c_int, u32p]
+    lib.oracle_intra_sad.restype = c_int
+    lib.oracle_fsbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                i16p, u32p, u32p, c_int]
+    lib.oracle_fsbm.restype = c_int
+    lib.oracle_fsbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                       i32p, c_int, i16p, u32p, u32p, c_int]
+    lib.oracle_fsbm_blocks.restype = c_int
+    prm_p = ctypes.POINTER(AcbmParams)
+    lib.oracle_acbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                i16p, prm_p, i16p, u32p, u8p, u32p, u32p]
+    lib.oracle_acbm.restype = c_int
+    lib.oracle_acbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                       i16p, i16p, prm_p, i32p, c_int, i16p, u32p, u8p,
+                                       u32p, u32p]
+    lib.oracle_acbm_blocks.restype = c_int
+    return lib
+
+
 def _load():
     global _lib
+    ov = _override.get()
+    if ov is not None:
+        return ov
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        i16p = ctypes.POINTER(ctypes.c_int16)
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        i32p = ctypes.POINTER(ctypes.c_int32)
-        c_int, c_u32 = ctypes.c_int, ctypes.c_uint32
-        lib.oracle_lambda_q8.argtypes = [c_int]
-        lib.oracle_lambda_q8.restype = c_u32
-        lib.oracle_mv_bits.argtypes = [c_int]
-        lib.oracle_mv_bits.restype = c_int
-        lib.oracle_intra_sad.argtypes = [u8p, c_int, c_int, c_int, c_int, u32p]
-        lib.oracle_intra_sad.restype = c_int
-        lib.oracle_fsbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
-                                    i16p, u32p, u32p, c_int]
-        lib.oracle_fsbm.restype = c_int
-        lib.oracle_fsbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
-                                           i32p, c_int, i16p, u32p, u32p, c_int]
-        lib.oracle_fsbm_blocks.restype = c_int
-        prm_p = ctypes.POINTER(AcbmParams)
-        lib.oracle_acbm.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
-                                    i16p, prm_p, i16p, u32p, u8p, u32p, u32p]
-        lib.oracle_acbm.restype = c_int
-        lib.oracle_acbm_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
-                                           i16p, i16p, prm_p, i32p, c_int, i16p, u32p, u8p,
-                                           u32p, u32p]
-        lib.oracle_acbm_blocks.restype = c_int
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+
+
+def compile_variant(src_text: str, out_path: str) -> str:
+    """Compiles C source text with the oracle's flags into out_path (for tests
+    that check the pins against deliberately broken copies of the oracle)."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-w", "-o", out_path,
+                    c_path], check=True)
+    return out_path
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+class Variant:
+    """The oracle's Python interface bound to another compiled copy."""
+
+    def __init__(self, so_path: str):
+        self._lib = _bind(ctypes.CDLL(so_path))
+
+    def __getattr__(self, name):
+        fn = globals()[name]
+        if not callable(fn) or name.startswith("_") or isinstance(fn, type):
+            return fn
+
+        def call(*a, **k):
+            token = _override.set(self._lib)
+            try:
+                return fn(*a, **k)
+            finally:
+                _override.reset(token)
+        return call
 
 
 class OracleError(RuntimeError):

@@ -112,6 +112,15 @@ def test_fsbm_edge_cases(me, orc):
     want = orc.fsbm(cur, ref, 16, 16, 6, 0)
     for nm, g, w in zip(("mv", "J", "sad"), got, want):
         _eq(f"periodic {nm}", g, w)
+    # diagonal pattern: (1,0) and (0,1) tie in J and |mv|_1; raster order decides
+    g7 = np.array([13, 201, 77, 150, 30, 240, 99], np.uint8)
+    yy, xx = np.mgrid[0:64, 0:64]
+    refd, curd = g7[(xx + yy) % 7], g7[(xx + yy + 1) % 7]
+    for p in (3, 32):
+        got = _fsbm_gpu(me, curd, refd, 16, 16, p, 0)
+        want = orc.fsbm(curd, refd, 16, 16, p, 0)
+        for nm, g, w in zip(("mv", "J", "sad"), got, want):
+            _eq(f"diagonal p={p} {nm}", g, w)
 
 
 def test_fsbm_rejects_bad_arguments(me):

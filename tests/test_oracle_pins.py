@@ -210,6 +210,15 @@ def test_fsbm_tie_breaks(orc):
     # the same, (-2,0) still wins by raster; with lambda both beat (+-6,0)
     mv, J, sad = orc.fsbm(cur, ref, 16, 16, 6, 6595)
     assert tuple(mv[1, 1]) == (-2, 0)
+    # diagonal pattern g((x+y) mod 7), content moved so SAD is 0 exactly where
+    # mvx + mvy = 1: (1,0) and (0,1) tie in J and |mv|_1; the raster order
+    # (mvy before mvx) picks (1,0)
+    g = np.array([13, 201, 77, 150, 30, 240, 99], np.uint8)
+    yy, xx = np.mgrid[0:64, 0:64]
+    refd = g[(xx + yy) % 7]
+    curd = g[(xx + yy + 1) % 7]
+    mv, J, sad = orc.fsbm(curd, refd, 16, 16, 3, 0)
+    assert tuple(mv[1, 1]) == (1, 0) and tuple(mv[2, 2]) == (1, 0) and sad[1, 1] == 0
 
 
 def test_fsbm_rejects_bad_shapes(orc):
