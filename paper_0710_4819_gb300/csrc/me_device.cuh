@@ -95,6 +95,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // ---------------------------------------------------------------------------
 struct FsGeom {
   int p, n;          // search range, n = 2p+1 positions per axis
+  int c0, nc;        // the mvx columns searched: c0 .. c0+nc-1 (mvx = column - p)
   int rb;            // bits of the per-run tie rank (0: use 64-bit keys throughout)
   int nseg;          // runs per column: ceil(n / T)
   int bpc;           // blocks in this group (adjacent, same block row)
@@ -122,21 +123,25 @@ __host__ __device__ inline bool fast32_ok(int N, int M, int p, uint32_t lam) {
   return ((jmax << rb) | ((1ull << rb) - 1)) < (1ull << 32);
 }
 
+// Geometry of a search over columns c0 .. c0+nc-1 of the (2p+1)-wide window
+// (nc = 0: all columns); a slice lets several CTAs share one block's search.
 template <int N, int M, int T>
-__host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G) {
+__host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int nc = 0) {
   FsGeom g;
   g.p = p;
   g.rb = 0;
   g.n = 2 * p + 1;
+  g.c0 = c0;
+  g.nc = nc > 0 ? nc : g.n;
   g.nseg = (g.n + T - 1) / T;
   g.bpc = bpc;
   g.G = G;
   g.rows = g.nseg * T + M - 1;
-  // position o = blk*N + col (col < n) is read as words o .. o+N-4
-  g.pos = (bpc - 1) * N + g.n + N - 4;
+  // position o = blk*N + col (col < nc) is read as words o .. o+N-4
+  g.pos = (bpc - 1) * N + g.nc + N - 4;
   // raw row: up to 3 bytes of alignment slack, pos+3 bytes, one spare word
   g.wbw = (g.pos + 6) / 4 + 1;
-  g.tasks = g.n * g.nseg;
+  g.tasks = g.nc * g.nseg;
   return g;
 }
 
@@ -180,7 +185,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     curw[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w);
   }
   // 2. raw window rows, from the aligned word at or left of column x0 - p
-  const int wx0 = x0 - p;
+  const int wx0 = x0 - p + g.c0;
   const int A0 = (wx0 >> 2) << 2;        // floor to a multiple of 4
   const int s0 = wx0 - A0;
   const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
@@ -242,8 +247,9 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     for (int j = 0; j < M; j++)
 #pragma unroll
       for (int w = 0; w < NW; w++) c[j][w] = curw[(blk * M + j) * NW + w];
-    int seg = l / n, col = l - (l / n) * n;
-    const int dseg = g.G / n, dcol = g.G - (g.G / n) * n;
+    const int nc = g.nc;
+    int seg = l / nc, col = l - (l / nc) * nc;
+    const int dseg = g.G / nc, dcol = g.G - (g.G / nc) * nc;
     for (int t = l; t < g.tasks; t += g.G) {
       const int row0 = seg * T;
       const uint32_t* shp = sh + row0 * g.pos + blk * N + col;
@@ -265,8 +271,9 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
           }
         }
       }
-      // cost and key of each candidate of the run (mvx = col - p)
-      const int mvx = col - p;
+      // cost and key of each candidate of the run (mvx = c0 + col - p)
+      const int wcol = g.c0 + col;
+      const int mvx = wcol - p;
       const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
       const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
       if (fast) {
@@ -282,10 +289,10 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
         const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
         const int mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
         const uint32_t lo = ((amx + (uint32_t)(mvy < 0 ? -mvy : mvy)) << 17) +
-                            (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)col;
+                            (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)wcol;
         best = umin64(best, ((unsigned long long)J << 32) | lo);
       } else {
-        const uint32_t kx = (amx << 17) + (uint32_t)col;
+        const uint32_t kx = (amx << 17) + (uint32_t)wcol;
 #pragma unroll
         for (int k = 0; k < T; k++) {
           const int r = row0 + k;
@@ -297,7 +304,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       }
       seg += dseg;
       col += dcol;
-      if (col >= n) { col -= n; seg++; }
+      if (col >= nc) { col -= nc; seg++; }
     }
   }
   // 5. per-block minimum

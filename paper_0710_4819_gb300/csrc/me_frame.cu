@@ -87,11 +87,18 @@ __global__ void __launch_bounds__(256) k_acbm_prologue(AcbmArgs a, AcbmArgs* __r
                                                        PadGeom pg, int W, int H,
                                                        uint8_t* __restrict__ refpad,
                                                        uint32_t* __restrict__ intra,
-                                                       int* __restrict__ cnt, int nwaves) {
+                                                       int* __restrict__ cnt, int nwaves,
+                                                       unsigned long long* __restrict__ keys,
+                                                       int* __restrict__ done) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   if (gtid == 0) *slot = a;
   for (long long i = gtid; i < nwaves; i += nthr) cnt[i] = 0;
+  const int nblk = (W / N) * (H / M);
+  for (long long i = gtid; i < nblk; i += nthr) {
+    keys[i] = kNoKey;
+    done[i] = 0;
+  }
   const int chunks = pg.pitch / 16;
   for (long long i = gtid; i < (long long)pg.rows * chunks; i += nthr) {
     const int y = (int)(i / chunks), cx = (int)(i % chunks) * 16;
@@ -150,28 +157,49 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
   }
 }
 
-// ACBM full-search fallback of one wave: CTA i searches list entry i.
+// ACBM full-search fallback of one wave: list entry i is searched by S CTAs
+// (blockIdx = i*S + slice), each over a slice of the mvx columns; the slices'
+// winning keys meet in an atomic 64-bit minimum (the key order is total, so
+// the result does not depend on the order), and the last slice to finish
+// writes the block's outputs.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(kMaxThreads) k_fs_list(const AcbmArgs* __restrict__ ap, int W,
-                                                         int H, int p,
+                                                         int H, int p, int S,
                                                          const int* __restrict__ fail_count,
-                                                         const int* __restrict__ fail_list) {
+                                                         const int* __restrict__ fail_list,
+                                                         unsigned long long* __restrict__ bkeys,
+                                                         int* __restrict__ bdone) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  if ((int)blockIdx.x >= *fail_count) return;
+  const int item = blockIdx.x / S, sl = blockIdx.x - (blockIdx.x / S) * S;
+  if (item >= *fail_count) return;
   const AcbmArgs a = *ap;
-  const int BW = W / N;
-  const int b = fail_list[blockIdx.x];
-  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
+  const int BW = W / N, n = 2 * p + 1;
+  const int b = fail_list[item];
+  const int c0 = sl * n / S, c1 = (sl + 1) * n / S;
+  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x, c0, c1 - c0);
   fs_group<N, M, T>(a.cur, a.ref, W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
   if (threadIdx.x == 0) {
-    const Decoded d = decode_key(keys[0], p, a.lam);
-    a.mv[2 * b] = (int16_t)d.mvx;
-    a.mv[2 * b + 1] = (int16_t)d.mvy;
-    a.J[b] = d.J;
-    a.mask[b] = 1;
-    if (a.sad) a.sad[b] = d.sad;
-    if (a.load) a.load[b] = (uint32_t)((2 * p + 1) * (2 * p + 1));
+    unsigned long long key = keys[0];
+    bool last = true;
+    if (S > 1) {
+      atomicMin(bkeys + b, key);
+      __threadfence();
+      last = atomicAdd(bdone + b, 1) == S - 1;
+      if (last) {
+        __threadfence();
+        key = atomicMin(bkeys + b, kNoKey);   // reads the merged minimum
+      }
+    }
+    if (last) {
+      const Decoded d = decode_key(key, p, a.lam);
+      a.mv[2 * b] = (int16_t)d.mvx;
+      a.mv[2 * b + 1] = (int16_t)d.mvy;
+      a.J[b] = d.J;
+      a.mask[b] = 1;
+      if (a.sad) a.sad[b] = d.sad;
+      if (a.load) a.load[b] = (uint32_t)(n * n);
+    }
   }
 }
 
@@ -215,7 +243,7 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max) {
   const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
   const int nT = (N == 16 && M == 16) ? 4 : 1;
   // fallback (always valid): the first run length, one block of 128 threads
-  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1), 1};
   double best_cost = 1e300;
   static const int kG[] = {8, 16, 32, 64, 128, 256, 512};
   static const int kThr[] = {64, 128, 256, 512};
@@ -241,7 +269,7 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max) {
         const double cost = per_thread * thr / ((double)bpc * n * n) / occ;
         if (cost < best_cost * 0.999) {
           best_cost = cost;
-          best = FsPlan{T, G, thr, smem};
+          best = FsPlan{T, G, thr, smem, 1};
         }
       }
     }
@@ -254,7 +282,7 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max) {
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit) {
   const int n = 2 * p + 1;
   const int tasks = n * ((n + T - 1) / T);
-  FsPlan best{T, thr, thr, smem_dispatch(N, M, T, p, 1)};
+  FsPlan best{T, thr, thr, smem_dispatch(N, M, T, p, 1), 1};
   double best_cost = 1e300;
   static const int kG[] = {8, 16, 32, 64, 128, 256, 512};
   for (int G : kG) {
@@ -268,39 +296,46 @@ FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t sm
     const double cost = per_thread * thr / ((double)bpc * n * n);
     if (cost < best_cost * 0.999) {
       best_cost = cost;
-      best = FsPlan{T, G, thr, smem};
+      best = FsPlan{T, G, thr, smem, 1};
     }
   }
   return best;
 }
 
 // Plan for searching single blocks where latency matters (the ACBM fallback
-// sits on the wave chain): one block per CTA, all threads on it (G = threads),
-// the run length and thread count with the fewest instructions per thread.
+// sits on the wave chain): S CTAs per block, each over a slice of about n/S
+// mvx columns with one task per thread (at most 512 threads), choosing the run
+// length and S with the fewest instructions per thread, plus a per-slice
+// charge for the merge and for the SMs the extra CTAs take.
 FsPlan fs_plan_latency(int N, int M, int p) {
   const int n = 2 * p + 1;
   const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
   const int nT = (N == 16 && M == 16) ? 4 : 1;
-  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1)};
+  FsPlan best{Ts[0], 128, 128, smem_dispatch(N, M, Ts[0], p, 1), 1};
   double best_lat = 1e300;
   for (int ti = 0; ti < nT; ti++) {
     const int T = Ts[ti];
     const size_t smem = smem_dispatch(N, M, T, p, 1);
     if (smem > 200 * 1024) continue;
-    const int tasks = n * ((n + T - 1) / T);
-    for (int thr = 64; thr <= kMaxThreads; thr += 32) {
+    const int nseg = (n + T - 1) / T;
+    for (int S = 1; S <= 8 && S <= n; S++) {
+      const int nc = (n + S - 1) / S, tasks = nc * nseg;
+      const int thr = std::min(kMaxThreads, std::max(64, (tasks + 31) / 32 * 32));
       const int rounds = (tasks + thr - 1) / thr;
-      const double lat = rounds * task_cost(N, M, T) + stage_cost(N, M, T, p, 1) / thr;
+      // clocks: warps per SM sub-partition x (SAD steps at 2 clocks each, or
+      // the issue of all instructions), one global round trip for the window,
+      // and the merge of S > 1 slices
+      const int wps = (thr / 32 + 3) / 4;
+      const double lat = wps * rounds * std::max(2.0 * T * M * (N / 4), task_cost(N, M, T)) +
+                         1000.0 + (S > 1 ? 400.0 : 0.0) + 50.0 * S;
       if (lat < best_lat * 0.999) {
         best_lat = lat;
-        best = FsPlan{T, thr, thr, smem};
+        best = FsPlan{T, thr, thr, smem, S};
       }
     }
   }
   return best;
 }
-
-// ------------------------------------------------------------------ launch helpers
 
 // Optional plan override "T,G,threads" (for tile sweeps); ignored unless
 // the run length is one instantiated for the block shape.
@@ -315,7 +350,7 @@ static bool plan_override(int N, int M, FsPlan* pl, int p, int bpc_max) {
   const int bpc = thr / G;
   const size_t smem = smem_dispatch(N, M, T, p, bpc);
   if (smem == 0 || bpc > std::min(bpc_max, 16) || smem > 200 * 1024) return false;
-  *pl = FsPlan{T, G, thr, smem};
+  *pl = FsPlan{T, G, thr, smem, 1};
   return true;
 }
 
@@ -334,10 +369,11 @@ static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, i
 
 template <int N, int M, int T>
 static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* cnt,
-                            const int* list, int grid, const FsPlan& pl, cudaStream_t s) {
+                            const int* list, int grid, unsigned long long* bkeys, int* bdone,
+                            const FsPlan& pl, cudaStream_t s) {
   auto kern = k_fs_list<N, M, T>;
   ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-  kern<<<grid, pl.threads, pl.smem, s>>>(ap, W, H, p, cnt, list);
+  kern<<<grid * pl.S, pl.threads, pl.smem, s>>>(ap, W, H, p, pl.S, cnt, list, bkeys, bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
@@ -371,9 +407,10 @@ int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int
 }
 
 static int launch_fs_list(int N, int M, const AcbmArgs* ap, int W, int H, int p, const int* cnt,
-                          const int* list, int grid, cudaStream_t s) {
+                          const int* list, int grid, unsigned long long* bkeys, int* bdone,
+                          cudaStream_t s) {
   const FsPlan pl = fs_plan_latency(N, M, p);
-  ME_DISPATCH_FS(launch_fs_list_t, ap, W, H, p, cnt, list, grid, pl, s);
+  ME_DISPATCH_FS(launch_fs_list_t, ap, W, H, p, cnt, list, grid, bkeys, bdone, pl, s);
 }
 
 #define ME_DISPATCH_NM(FN, ...)                                  \
@@ -433,19 +470,20 @@ static int launch_pbm_wave(int N, int M, const AcbmArgs* ap, const uint8_t* refp
 template <int N, int M>
 static int launch_prologue_t(const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg, int W, int H,
                              uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
-                             cudaStream_t s) {
+                             unsigned long long* bkeys, int* bdone, cudaStream_t s) {
   const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16),
                                              32LL * (W / N) * (H / M));
   const int grid = (int)std::min<long long>((work + 255) / 256, 152 * 8);
-  k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, cnt, nwaves);
+  k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, cnt, nwaves, bkeys,
+                                             bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
 static int launch_prologue(int N, int M, const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg,
                            int W, int H, uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
-                           cudaStream_t s) {
-  ME_DISPATCH_NM(launch_prologue_t, a, slot, pg, W, H, refpad, intra, cnt, nwaves, s);
+                           unsigned long long* bkeys, int* bdone, cudaStream_t s) {
+  ME_DISPATCH_NM(launch_prologue_t, a, slot, pg, W, H, refpad, intra, cnt, nwaves, bkeys, bdone, s);
 }
 
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
@@ -458,7 +496,9 @@ AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
   l.off_intra = align_up(l.off_pad + (size_t)pg.pitch * pg.rows, 256);
   l.off_cnt = align_up(l.off_intra + 4 * (size_t)nb, 256);
   l.off_list = align_up(l.off_cnt + 4 * (size_t)wv.n, 256);
-  l.total = align_up(l.off_list + 4 * (size_t)nb, 256);
+  l.off_keys = align_up(l.off_list + 4 * (size_t)nb, 256);
+  l.off_done = align_up(l.off_keys + 8 * (size_t)nb, 256);
+  l.total = align_up(l.off_done + 4 * (size_t)nb, 256);
   return l;
 }
 
@@ -472,8 +512,10 @@ int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* 
   uint32_t* intra = reinterpret_cast<uint32_t*>(scratch + l.off_intra);
   int* cnt = reinterpret_cast<int*>(scratch + l.off_cnt);
   int* list = reinterpret_cast<int*>(scratch + l.off_list);
+  unsigned long long* bkeys = reinterpret_cast<unsigned long long*>(scratch + l.off_keys);
+  int* bdone = reinterpret_cast<int*>(scratch + l.off_done);
   const Waves wv = make_waves(W / N, H / M);
-  int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, cnt, wv.n, s);
+  int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, cnt, wv.n, bkeys, bdone, s);
   if (st) return st;
   int off = 0;
   for (int w = 0; w < wv.n; w++) {
@@ -482,7 +524,7 @@ int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* 
     st = launch_pbm_wave(N, M, slot, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w,
                          list + off, s);
     if (st) return st;
-    st = launch_fs_list(N, M, slot, W, H, p, cnt + w, list + off, c, s);
+    st = launch_fs_list(N, M, slot, W, H, p, cnt + w, list + off, c, bkeys, bdone, s);
     if (st) return st;
     off += c;
   }
@@ -561,7 +603,7 @@ static int launch_plan(AcbmPlan* pl, const AcbmArgs& a, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(pl->mu);
   // the prologue's first parameter is the AcbmArgs value; the rest stay
   void* argv[16];
-  for (int i = 0; i < 9; i++) argv[i] = pl->kp.kernelParams[i];
+  for (int i = 0; i < 11; i++) argv[i] = pl->kp.kernelParams[i];
   AcbmArgs val = a;
   argv[0] = &val;
   cudaKernelNodeParams kp = pl->kp;

@@ -280,6 +280,7 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
 struct FsPlan {
   int T, G, threads;   // run length, threads per block, threads per CTA
   size_t smem;
+  int S;               // CTAs sharing one block (column slices); 1 = whole block
 };
 
 // Chooses among the instantiated run lengths with a small cost model
@@ -291,9 +292,10 @@ FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t sm
 
 // Scratch layout of one ACBM frame (the call's arguments, padded reference,
 // scaled Intra_SAD per block, failing-block count per wave, compacted
-// failing-block lists), in bytes from the start of one 256-byte aligned region.
+// failing-block lists, per-block merge key and slice counter of the sliced
+// fallback search), in bytes from the start of one 256-byte aligned region.
 struct AcbmScratch {
-  size_t off_args, off_pad, off_intra, off_cnt, off_list, total;
+  size_t off_args, off_pad, off_intra, off_cnt, off_list, off_keys, off_done, total;
 };
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p);
 

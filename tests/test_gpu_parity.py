@@ -294,3 +294,22 @@ def test_acbm_invariants_vs_fsbm_on_gpu(me, orc):
     _eq("forced mv", forced[0], f[0])
     _eq("forced J", forced[1], f[1])
     assert np.all(forced[2] == 1) and np.all(forced[4] == 33 * 33)
+
+
+@pytest.mark.parametrize("p", [8, 20, 32, 40, 64])
+def test_acbm_forced_fallback_across_slice_counts(me, orc, p):
+    """Every block through the fallback search, whose CTAs split the mvx
+    columns into slices merged by an atomic minimum (the slice count grows
+    with p): equal to the oracle's FSBM for every block."""
+    rng = np.random.default_rng(p)
+    ref = synth.texture(rng, 96, 64)
+    cur = synth.shifted_copy(ref, 5, -3)
+    cur = np.clip(cur.astype(int) + rng.integers(-3, 4, cur.shape), 0, 255).astype(np.uint8)
+    lam = orc.lambda_q8(28)
+    got = _acbm_gpu(me, cur, ref, 16, 16, p, lam, me.params(alpha=0, beta=0, gamma_num=0, qp=28))
+    mv, J, sad = orc.fsbm(cur, ref, 16, 16, p, lam, nthreads=8)
+    _eq("mv", got[0], mv)
+    _eq("J", got[1], J)
+    _eq("sad", got[3], sad)
+    assert np.all(got[2] == 1) and np.all(got[4] == (2 * p + 1) ** 2)
+
