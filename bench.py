@@ -5,11 +5,13 @@ Workload: 1920x1080 luma padded to 1088 rows, 16x16 blocks, p = 32,
 Qp = 28 (lambda_q8 = 6595), a 60-frame synthetic sequence (panned textured
 background, 20 objects moving at up to 24 px/frame, noise sigma 2, 10% of
 block slots per frame overwritten with noise).  One step = every frame pair
-of the sequence through the whole hot path: FSBM (one launch per pair) and
-ACBM (padding, Intra_SAD, PBM waves with compaction and the sliced
-full-search fallback, replayed from a CUDA graph), the ACBM field of each pair
-feeding the next as temporal predictors.  The persistent one-launch ACBM form
-is timed beside it on the same pairs and its outputs compared.  Frames stay
+of the sequence through the whole hot path: FSBM of all pairs in one launch
+(me_fsbm_sequence) and ACBM of all pairs in one persistent launch
+(me_acbm_sequence: padding, Intra_SAD, PBM, the two conditions and the
+full-search fallback, the field of each pair feeding the next as temporal
+predictors, pairs overlapping on the GPU).  The per-pair calls (me_fsbm,
+me_acbm with its graph-replayed wave launches) are timed beside it for the
+per-pair latency, and their outputs compared with the step's.  Frames stay
 resident in device memory; L2 is flushed between timed steps (the flush
 itself is not timed).
 
@@ -373,49 +375,18 @@ def main():
     a_mask = torch.empty((pairs, BH, BW), dtype=torch.uint8, device=dev)
     a_load = torch.empty_like(f_J)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    f_out = (f_mv, f_J, f_sad)
+    a_out = (a_mv, a_J, a_mask, a_sad, a_load)
 
-    def run_fsbm(t):
-        me.me_fsbm(frames[t], frames[t - 1], N, M, P, lam, out=(f_mv[t - 1], f_J[t - 1], f_sad[t - 1]))
-
-    def run_acbm_plain(t):
-        prev = a_mv[t - 2] if t >= 2 else None
-        me.me_acbm(frames[t], frames[t - 1], N, M, P, lam, prm, prev_mv=prev,
-                   out=(a_mv[t - 1], a_J[t - 1], a_mask[t - 1], a_sad[t - 1], a_load[t - 1]))
-
-    # the persistent dataflow form of ACBM (one launch per frame pair)
-    batch = me.Batch()
-    batch.add_stream(W, H_PAD, N, M, P)
-
-    def acbm_item(cur, ref, prev, mv, J, mask, sad, load):
-        it = me.BatchItem()
-        it.cur, it.ref = cur.data_ptr(), ref.data_ptr()
-        it.prev_mv = None if prev is None else prev.data_ptr()
-        it.mv_out, it.J_out, it.mask_out = mv.data_ptr(), J.data_ptr(), mask.data_ptr()
-        it.sad_out, it.load_out = sad.data_ptr(), load.data_ptr()
-        it.lambda_q8 = lam
-        it.prm = prm
-        return it
-
-    def run_acbm(t):
-        prev = a_mv[t - 2] if t >= 2 else None
-        batch.run(1, [acbm_item(frames[t], frames[t - 1], prev, a_mv[t - 1], a_J[t - 1],
-                                a_mask[t - 1], a_sad[t - 1], a_load[t - 1])])
-
-    def step(ev_f=None, ev_a=None):
-        for t in range(1, pairs + 1):
-            if ev_f is not None:
-                ev_f[t - 1][0].record(stream)
-            run_fsbm(t)
-            if ev_f is not None:
-                ev_f[t - 1][1].record(stream)
-                ev_a[t - 1][0].record(stream)
-            run_acbm_plain(t)
-            if ev_a is not None:
-                ev_a[t - 1][1].record(stream)
+    def step():
+        # every pair of the sequence: FSBM in one launch, ACBM in one
+        # persistent launch with the pairs overlapping
+        me.me_fsbm_sequence(frames, N, M, P, lam, out=f_out)
+        me.me_acbm_sequence(frames, N, M, P, lam, prm, out=a_out)
 
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize()
+    me.me_acbm_sequence_status(W, H_PAD, N, M, P, pairs)
 
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
@@ -423,93 +394,86 @@ def main():
     clocks.start()
     for _ in range(args.steps):
         flush.fill_(1)
-        ev_f = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(pairs)]
-        ev_a = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(pairs)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         barrier(pg)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(ev_f, ev_a)
-        e1.record(stream)
+        ev[0].record(stream)
+        me.me_fsbm_sequence(frames, N, M, P, lam, out=f_out)
+        ev[1].record(stream)
+        me.me_acbm_sequence(frames, N, M, P, lam, prm, out=a_out)
+        ev[2].record(stream)
         torch.cuda.synchronize()
         barrier(pg)
-        step_ms.append(e0.elapsed_time(e1))
-        fsbm_ms.extend(a.elapsed_time(b) for a, b in ev_f)
-        acbm_ms.extend(a.elapsed_time(b) for a, b in ev_a)
+        step_ms.append(ev[0].elapsed_time(ev[2]))
+        fsbm_ms.append(ev[0].elapsed_time(ev[1]))
+        acbm_ms.append(ev[1].elapsed_time(ev[2]))
     clk = clocks.stop()
-
-    plain_out = [x.clone() for x in (a_mv, a_J, a_mask, a_sad, a_load)]
-    # the persistent dataflow form (one launch per pair), same outputs
-    for _ in range(2):
-        for t in range(1, pairs + 1):
-            run_acbm(t)
-    batch.sync()
-    torch.cuda.synchronize()
-    ep = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(pairs)]
-    for t in range(1, pairs + 1):
-        ep[t - 1][0].record(stream)
-        run_acbm(t)
-        ep[t - 1][1].record(stream)
-    batch.sync()
-    torch.cuda.synchronize()
-    persist_ms = [a.elapsed_time(b) for a, b in ep]
-    forms_identical = all(torch.equal(x, y) for x, y in
-                          zip(plain_out, (a_mv, a_J, a_mask, a_sad, a_load)))
+    me.me_acbm_sequence_status(W, H_PAD, N, M, P, pairs)
+    seq_out = [x.clone() for x in a_out + f_out]
+    acbm_load = int(a_load.to(torch.int64).sum().item())
+    fs_frac = float(a_mask.float().mean().item())
 
     total_ms = max_over_ranks(pg, sum(step_ms))
     frames_done = pairs * args.steps * world
     fps = frames_done / (total_ms * 1e-3)
 
-    # kernel-only FSBM timing (dominant kernel) for the roofline, same stream
+    # per-pair forms: plain ACBM (wave launches replayed from a graph) and
+    # single-pair FSBM, for latency per pair and to check identical outputs
+    def run_pair(t):
+        me.me_fsbm(frames[t], frames[t - 1], N, M, P, lam,
+                   out=(f_mv[t - 1], f_J[t - 1], f_sad[t - 1]))
+        prev = a_mv[t - 2] if t >= 2 else None
+        me.me_acbm(frames[t], frames[t - 1], N, M, P, lam, prm, prev_mv=prev,
+                   out=(a_mv[t - 1], a_J[t - 1], a_mask[t - 1], a_sad[t - 1], a_load[t - 1]))
+    for t in range(1, pairs + 1):
+        run_pair(t)
+    torch.cuda.synchronize()
+    ep = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(pairs)]
+    for t in range(1, pairs + 1):
+        ep[t - 1][0].record(stream)
+        me.me_fsbm(frames[t], frames[t - 1], N, M, P, lam,
+                   out=(f_mv[t - 1], f_J[t - 1], f_sad[t - 1]))
+        ep[t - 1][1].record(stream)
+        prev = a_mv[t - 2] if t >= 2 else None
+        me.me_acbm(frames[t], frames[t - 1], N, M, P, lam, prm, prev_mv=prev,
+                   out=(a_mv[t - 1], a_J[t - 1], a_mask[t - 1], a_sad[t - 1], a_load[t - 1]))
+        ep[t - 1][2].record(stream)
+    torch.cuda.synchronize()
+    pair_fsbm_ms = [e[0].elapsed_time(e[1]) for e in ep]
+    pair_acbm_ms = [e[1].elapsed_time(e[2]) for e in ep]
+    identical = all(torch.equal(x, y) for x, y in zip(seq_out, a_out + f_out))
+
+    # kernel-only FSBM timing (the SAD engine) for the roofline, same stream
     reps = 20
     ek0, ek1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ek0.record(stream)
     for i in range(reps):
-        run_fsbm(1 + i % pairs)
+        me.me_fsbm(frames[1 + i % pairs], frames[i % pairs], N, M, P, lam,
+                   out=(f_mv[0], f_J[0], f_sad[0]))
     ek1.record(stream)
     torch.cuda.synchronize()
     fsbm_kernel_ms = ek0.elapsed_time(ek1) / reps
     peak_absdiff = 152 * 256 * 2.07e9          # SMs x absdiff/clk/SM x max SM clock
-    achieved = ABSDIFF_PER_FRAME / (fsbm_kernel_ms * 1e-3)
+    seq_fsbm_ms = statistics.mean(fsbm_ms) / pairs
+    achieved = ABSDIFF_PER_FRAME / (seq_fsbm_ms * 1e-3)
 
-    acbm_load = int(a_load.to(torch.int64).sum().item())
-    fs_frac = float(a_mask.float().mean().item())
-
-    # end-to-end through the C ABI with host buffers
+    # end-to-end through the C ABI with host buffers: host frames copied in,
+    # the step's calls, results copied out, all inside the timed region
     host_frames = torch.from_numpy(frames_np).pin_memory()
-    h_out = {k: torch.empty(v.shape[1:], dtype=v.dtype).pin_memory()
-             for k, v in (("fmv", f_mv), ("fJ", f_J), ("amv", a_mv), ("aJ", a_J),
-                          ("amask", a_mask), ("aload", a_load))}
-    d_fr = [torch.empty((H_PAD, W), dtype=torch.uint8, device=dev) for _ in range(3)]
-    e2e_pairs = pairs
+    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in a_out + f_out]
+    d_frames = torch.empty_like(frames)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    d_fr[0].copy_(host_frames[0], non_blocking=True)
-    prev = None
-    for t in range(1, e2e_pairs + 1):
-        d_cur, d_ref = d_fr[t % 3], d_fr[(t - 1) % 3]
-        d_cur.copy_(host_frames[t], non_blocking=True)
-        me.me_fsbm(d_cur, d_ref, N, M, P, lam, out=(f_mv[0], f_J[0], f_sad[0]))
-        me.me_acbm(d_cur, d_ref, N, M, P, lam, prm, prev_mv=prev,
-                   out=(a_mv[t % 2], a_J[0], a_mask[0], a_sad[0], a_load[0]))
-        prev = a_mv[t % 2]
-        h_out["fmv"].copy_(f_mv[0], non_blocking=True)
-        h_out["fJ"].copy_(f_J[0], non_blocking=True)
-        h_out["amv"].copy_(a_mv[t % 2], non_blocking=True)
-        h_out["aJ"].copy_(a_J[0], non_blocking=True)
-        h_out["amask"].copy_(a_mask[0], non_blocking=True)
-        h_out["aload"].copy_(a_load[0], non_blocking=True)
-    batch.sync()
+    d_frames.copy_(host_frames, non_blocking=True)
+    me.me_fsbm_sequence(d_frames, N, M, P, lam, out=f_out)
+    me.me_acbm_sequence(d_frames, N, M, P, lam, prm, out=a_out)
+    for h, d in zip(h_out, a_out + f_out):
+        h.copy_(d, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(pg, e2e_s)
-    h2d = (e2e_pairs + 1) * H_PAD * W
-    d2h = e2e_pairs * sum(v.numel() * v.element_size() for v in h_out.values())
-    e2e_fps = e2e_pairs * world / e2e_s
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    h2d = host_frames.numel()
+    d2h = sum(x.numel() * x.element_size() for x in h_out)
+    e2e_fps = pairs * world / e2e_s
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -521,16 +485,14 @@ def main():
 
     if rank != 0:
         return
-    fsbm_mean = statistics.mean(fsbm_ms)
-    acbm_mean = statistics.mean(acbm_ms)
-    acbm_sorted = sorted(acbm_ms)
-    frame_ms = sorted(f + a for f, a in zip(fsbm_ms, acbm_ms))
+    fsbm_mean = statistics.mean(fsbm_ms) / pairs
+    acbm_mean = statistics.mean(acbm_ms) / pairs
 
     def pct(v, q):
+        v = sorted(v)
         return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
 
-    waves = (BW - 1) + 2 * (BH - 1) + 1
-    launches_per_pair = 1 + 1 + 2 * waves     # k_fsbm; ACBM prologue + two kernels per wave
+    pair_ms = [f + a for f, a in zip(pair_fsbm_ms, pair_acbm_ms)]
     line = {
         "metric": "1080p frames/s (FSBM + ACBM per frame pair), candidate-SADs/s, p99 ms",
         "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -539,28 +501,28 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step": pairs, "l2": "flushed between steps",
                    "parallelism": f"replicas x{world} (independent sequences, no collective)"},
-        "fsbm": {"frames_per_s": 1e3 / fsbm_mean, "cand_sads_per_s": NBLK * NCAND / (fsbm_mean * 1e-3),
-                 "ms_per_frame": fsbm_mean},
-        "acbm": {"form": "wave launches + compaction + sliced fallback, graph-replayed",
+        "fsbm": {"form": "me_fsbm_sequence (one launch for all pairs)",
+                 "frames_per_s": 1e3 / fsbm_mean, "cand_sads_per_s": NBLK * NCAND / (fsbm_mean * 1e-3),
+                 "ms_per_frame": fsbm_mean, "single_pair_kernel_ms": fsbm_kernel_ms},
+        "acbm": {"form": "me_acbm_sequence (one persistent launch, pairs overlapping)",
                  "frames_per_s": 1e3 / acbm_mean,
                  "cand_sads_per_s": acbm_load / pairs / (acbm_mean * 1e-3),
-                 "ms_per_frame": acbm_mean, "p50_ms": pct(acbm_sorted, 0.5),
-                 "p99_ms": pct(acbm_sorted, 0.99), "fullsearch_fraction": fs_frac,
+                 "ms_per_frame": acbm_mean, "fullsearch_fraction": fs_frac,
                  "avg_positions_per_block": acbm_load / (pairs * NBLK)},
-        "acbm_persistent": {"form": "persistent dataflow kernel (one launch per frame pair)",
-                            "frames_per_s": 1e3 / statistics.mean(persist_ms),
-                            "ms_per_frame": statistics.mean(persist_ms),
-                            "p99_ms": pct(sorted(persist_ms), 0.99),
-                            "outputs_identical_to_plain": forms_identical},
-        "p99_ms": pct(frame_ms, 0.99),
-        "roofline": {"bound": "alu", "kernel": "k_fsbm", "achieved": achieved / 1e12,
+        "per_pair": {"form": "me_fsbm + me_acbm (wave launches, graph-replayed) per pair",
+                     "frames_per_s": 1e3 / statistics.mean(pair_ms),
+                     "acbm_ms": statistics.mean(pair_acbm_ms), "fsbm_ms": statistics.mean(pair_fsbm_ms),
+                     "p50_ms": pct(pair_ms, 0.5), "p99_ms": pct(pair_ms, 0.99),
+                     "outputs_identical_to_sequence": identical},
+        "p99_ms": pct(pair_ms, 0.99),
+        "roofline": {"bound": "alu", "kernel": "k_fsbm_seq", "achieved": achieved / 1e12,
                      "peak": peak_absdiff / 1e12, "unit": "T absdiff/s",
                      "frac": achieved / peak_absdiff, "traffic": None,
                      "peak_source": "152 SMs x 64 packed-SAD lanes/clk x 4 bytes x 2070 MHz "
                                     "(lane rate measured by me_sad_peak)"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_pair * pairs * args.steps,
+        "gpu_launches": 4 * args.steps,   # k_fsbm_seq; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
     }

@@ -133,6 +133,34 @@ int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
             int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,
             uint32_t *load_out, me_stream_t stream);
 
+/* ----------------------------------------------------------------- sequences */
+
+/* FSBM over K consecutive frame pairs in one launch (1 <= K <= 64).
+ * frames is a HOST array of K+1 device frame pointers: pair k has reference
+ * frames[k] and current frame frames[k+1].  Outputs are [K][BH][BW] (x2 for
+ * mv), pair k at offset k*BW*BH.  No scratch memory. */
+int me_fsbm_sequence(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
+                     me_stream_t stream);
+
+/* ACBM over K consecutive frame pairs in one persistent launch: pair k's
+ * previous field is pair k-1's output (prev_mv_field for pair 0, NULL =
+ * zeros), exactly as K chained me_acbm calls, with identical outputs.  The
+ * method's causal order (Sec. 2.2) lets the pairs overlap: a block of pair k
+ * needs only its spatial neighbours of pair k and its 3x3 neighbourhood of
+ * pair k-1, so blocks are claimed in order of (wave + 4k) and each waits
+ * (bounded) for those predecessors; many pairs are in flight at once.
+ * Scratch: one cached plan per (device, W, H, N, M, p, K) with K padded
+ * references, Intra_SAD and ready flags (allocated at the first call, kept
+ * until exit); runs with the same plan are ordered on the GPU.
+ * me_acbm_sequence_status waits for the stream and reports ME_ERR_TIMEOUT if
+ * a bounded wait of the last run gave up. */
+int me_acbm_sequence(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, const int16_t *prev_mv_field, const me_acbm_params *prm,
+                     int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out,
+                     uint32_t *sad_out, uint32_t *load_out, me_stream_t stream);
+int me_acbm_sequence_status(int W, int H, int N, int M, int p, int K, me_stream_t stream);
+
 /* ----------------------------------------------------------------- batches */
 
 /* Many independent streams of uneven size in one launch per step (an

@@ -96,6 +96,12 @@ def load_library(build_if_missing: bool = True):
                          ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
             "me_acbm_noalloc": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp,
                                  ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
+            "me_fsbm_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
+                                  u32, vp, vp, vp, vp], c_int),
+            "me_acbm_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
+                                  u32, vp, ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp],
+                                 c_int),
+            "me_acbm_sequence_status": ([c_int, c_int, c_int, c_int, c_int, c_int, vp], c_int),
             "me_sad_peak": ([c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), vp], c_int),
             "me_batch_create": ([ctypes.POINTER(vp)], c_int),
@@ -258,6 +264,63 @@ def me_acbm(cur, ref, N: int, M: int, p: int, lambda_q8: int, prm: AcbmParams, p
                                   _ptr(prev_mv), ctypes.byref(prm), _ptr(mv), _ptr(J), _ptr(mask),
                                   _ptr(sad), _ptr(load), _stream_ptr(stream)), "me_acbm")
     return AcbmResult(mv, J, mask, sad, load)
+
+
+def _frame_ptrs(frames):
+    """frames: uint8 CUDA tensor [K+1, H, W] (contiguous) or a list of [H, W] tensors."""
+    torch = _torch()
+    if isinstance(frames, torch.Tensor):
+        if not (frames.is_cuda and frames.dtype == torch.uint8 and frames.dim() == 3):
+            raise ValueError("frames must be a uint8 CUDA tensor [K+1, H, W]")
+        frames = [frames[i] for i in range(frames.shape[0])]
+    for f in frames:
+        if not (f.is_cuda and f.dtype == torch.uint8 and f.dim() == 2 and f.is_contiguous()):
+            raise ValueError("each frame must be a contiguous uint8 CUDA tensor [H, W]")
+    H, W = frames[0].shape
+    arr = (ctypes.c_void_p * len(frames))(*[f.data_ptr() for f in frames])
+    return arr, len(frames) - 1, int(W), int(H)
+
+
+def me_fsbm_sequence(frames, N: int, M: int, p: int, lambda_q8: int, out=None, stream=None):
+    """FSBM of K consecutive pairs in one launch; outputs [K, BH, BW, ...]."""
+    torch = _torch()
+    arr, K, W, H = _frame_ptrs(frames)
+    dev = frames[0].device
+    if out is None:
+        BH, BW = H // M, W // N
+        out = (torch.empty((K, BH, BW, 2), dtype=torch.int16, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev))
+    mv, J, sad = out
+    _check(load_library().me_fsbm_sequence(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(mv), _ptr(J),
+                                           _ptr(sad), _stream_ptr(stream)), "me_fsbm_sequence")
+    return FsbmResult(mv, J, sad)
+
+
+def me_acbm_sequence(frames, N: int, M: int, p: int, lambda_q8: int, prm: AcbmParams,
+                     prev_mv=None, out=None, stream=None) -> AcbmResult:
+    """ACBM of K consecutive pairs in one persistent launch (pairs overlap)."""
+    torch = _torch()
+    arr, K, W, H = _frame_ptrs(frames)
+    dev = frames[0].device
+    if out is None:
+        BH, BW = H // M, W // N
+        out = (torch.empty((K, BH, BW, 2), dtype=torch.int16, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.uint8, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev))
+    mv, J, mask, sad, load = out
+    _check(load_library().me_acbm_sequence(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(prev_mv),
+                                           ctypes.byref(prm), _ptr(mv), _ptr(J), _ptr(mask),
+                                           _ptr(sad), _ptr(load), _stream_ptr(stream)),
+           "me_acbm_sequence")
+    return AcbmResult(mv, J, mask, sad, load)
+
+
+def me_acbm_sequence_status(W: int, H: int, N: int, M: int, p: int, K: int, stream=None):
+    _check(load_library().me_acbm_sequence_status(W, H, N, M, p, K, _stream_ptr(stream)),
+           "me_acbm_sequence")
 
 
 def me_sad_peak(variant: int = 0, stream=None):

@@ -149,7 +149,7 @@ struct PbmResult {
 template <int N, int M>
 __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ refpad,
                               const PadGeom& pg, int W, int H, int p, uint32_t lam,
-                              const int16_t* field, const int16_t* __restrict__ prev,
+                              const int16_t* field, const int16_t* prev,
                               int bx, int by, uint32_t intra_x, int32_t alpha, int32_t beta,
                               int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
                               uint32_t* curs, uint32_t* win) {
@@ -181,8 +181,11 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
     const int nx = bx + dx, ny = by + dy;
     if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
       if (prev) {
-        cx = prev[2 * (ny * BW + nx)];
-        cy = prev[2 * (ny * BW + nx) + 1];
+        // volatile: in a sequence run the previous field is written by
+        // other CTAs of the same launch
+        const volatile int16_t* f = prev + 2 * (ny * BW + nx);
+        cx = f[0];
+        cy = f[1];
       }
       valid = true;
     }

@@ -1,0 +1,470 @@
+// me_sequence.cu -- FSBM and ACBM over K consecutive frame pairs of one
+// sequence in one launch each.
+//
+// FSBM: the frame kernel with one grid row per pair (no dependencies between
+// pairs; the long grid also removes the last-wave tail of a single frame).
+//
+// ACBM: the causal order of the method (Sec. 2.2: spatial predictors must be
+// final in the current frame; temporal predictors come from the previous
+// frame's field) allows pairs to overlap: block (x, y) of pair k needs the
+// final vectors of its left, up-left, up and up-right neighbours in pair k
+// (anti-diagonal waves w-1 .. w-3, with w = x + 2y) and of its 3x3
+// neighbourhood in pair k-1 (waves up to w+3).  Ordering all blocks of all
+// pairs by w + 4k therefore puts every dependency first, and one persistent
+// launch walks the whole sequence with about 4 waves between consecutive
+// pairs instead of a full frame: the GPU sees many pairs in flight at once.
+// Each block waits (bounded in time) for its 4 + 9 predecessors' ready flags.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "me_device.cuh"
+#include "me_host.h"
+#include "me_search.cuh"
+
+namespace me {
+
+constexpr int kSeqMax = 64;     // frame pairs per call
+constexpr int kSeqThreads = 256;
+constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
+
+struct SeqFrames {
+  const uint8_t* f[kSeqMax + 1];  // f[k] = reference of pair k, f[k+1] = its current frame
+};
+
+struct SeqArgs {
+  const int16_t* prev0;  // field before pair 0 (nullable)
+  int16_t* mv;           // [K][BH][BW][2]
+  uint32_t* J;           // [K][BH][BW]
+  uint8_t* mask;
+  uint32_t* sad;         // nullable
+  uint32_t* load;        // nullable
+  uint32_t lam;
+  int32_t alpha, beta, gnum, gden, qp, refine;
+};
+
+struct SeqSeg {  // the blocks of wave w of pair k, claimed as one run of items
+  int k, wave, ylo, count, item_base;
+};
+
+struct SeqCtrl {
+  int epoch, next, error, err_item;
+  long long timeout_ns;
+};
+
+// ------------------------------------------------------------------ FSBM
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, int H, int p, int G,
+                                                          uint32_t lam, int16_t* __restrict__ mv_out,
+                                                          uint32_t* __restrict__ J_out,
+                                                          uint32_t* __restrict__ sad_out) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  const int k = blockIdx.y;
+  const int BW = W / N, nbf = BW * (H / M);
+  const int bpc = blockDim.x / G;
+  const int gpr = (BW + bpc - 1) / bpc;
+  const int by = blockIdx.x / gpr, bx0 = (blockIdx.x % gpr) * bpc;
+  const int nb = min(bpc, BW - bx0);
+  const FsGeom g = fs_geom<N, M, T>(p, nb, G);
+  fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, bx0 * N, by * M, g, lam, smem, keys);
+  if ((int)threadIdx.x < nb) {
+    const Decoded d = decode_key(keys[threadIdx.x], p, lam);
+    const size_t b = (size_t)k * nbf + by * BW + bx0 + threadIdx.x;
+    mv_out[2 * b] = (int16_t)d.mvx;
+    mv_out[2 * b + 1] = (int16_t)d.mvy;
+    J_out[b] = d.J;
+    if (sad_out) sad_out[b] = d.sad;
+  }
+}
+
+// ------------------------------------------------------------------ ACBM
+
+static __device__ __forceinline__ long long seq_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void k_seq_begin(SeqCtrl* c) {
+  c->epoch += 1;
+  c->next = 0;
+  c->error = 0;
+  c->err_item = -1;
+}
+
+// Padded references and scaled Intra_SAD of all K pairs.
+template <int N, int M>
+__global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGeom pg, int W, int H,
+                                                      uint8_t* __restrict__ refpad,
+                                                      uint32_t* __restrict__ intra) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const int chunks = pg.pitch / 16;
+  const long long per = (long long)pg.rows * chunks;
+  for (long long i = gtid; i < per * K; i += nthr) {
+    const int k = (int)(i / per);
+    const long long j = i - (long long)k * per;
+    const int y = (int)(j / chunks), cx = (int)(j % chunks) * 16;
+    const uint8_t* src = fr.f[k] + (size_t)clampi(y - pg.P, 0, H - 1) * W;
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; b++) v |= (uint32_t)src[clampi(cx + 4 * q + b - pg.P, 0, W - 1)] << (8 * b);
+      w[q] = v;
+    }
+    *reinterpret_cast<uint4*>(refpad + (size_t)k * pg.pitch * pg.rows + (size_t)y * pg.pitch + cx) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  const int BW = W / N, nbf = BW * (H / M);
+  const long long warps = nthr / 32;
+  for (long long g = gtid / 32; g < (long long)nbf * K; g += warps) {
+    const int k = (int)(g / nbf), b = (int)(g - (long long)k * nbf);
+    const uint32_t v = warp_intra_sad<N, M>(fr.f[k + 1], W, (b % BW) * N, (b / BW) * M);
+    if ((threadIdx.x & 31) == 0) intra[g] = v;
+  }
+}
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
+                                                             int p, PadGeom pg,
+                                                             const uint8_t* __restrict__ refpad,
+                                                             const uint32_t* __restrict__ intra,
+                                                             int* __restrict__ flags,
+                                                             const SeqSeg* __restrict__ seg, int nseg,
+                                                             int total, SeqCtrl* ctrl) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  __shared__ uint32_t curs[M * (N / 4)];
+  __shared__ int s_item, s_k, s_b, s_pass, s_load;
+  __shared__ unsigned long long s_key;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int BW = W / N, BH = H / M, nbf = BW * BH;
+  const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
+  const long long timeout = ctrl->timeout_ns;
+  const size_t padsz = (size_t)pg.pitch * pg.rows;
+  for (;;) {
+    if (tid == 0) {
+      const int i = atomicAdd(&ctrl->next, 1);
+      s_item = i;
+      if (i < total) {
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
+        }
+        const SeqSeg sg = seg[lo];
+        const int by = sg.ylo + (i - sg.item_base);
+        s_k = sg.k;
+        s_b = by * BW + (sg.wave - 2 * by);
+      }
+    }
+    __syncthreads();
+    if (s_item >= total) break;
+    const int k = s_k, b = s_b;
+    const int bx = b % BW, by = b / BW;
+    int16_t* field = a.mv + (size_t)k * nbf * 2;
+    const int16_t* prev = k > 0 ? a.mv + (size_t)(k - 1) * nbf * 2 : a.prev0;
+    if (tid < 32) {
+      // lanes 0-3: spatial predecessors in pair k; lanes 4-12: the 3x3 in pair k-1
+      int nidx = -1;
+      if (lane < 4) {
+        const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
+        const int dy = (lane == 0) ? 0 : -1;
+        const int nx = bx + dx, ny = by + dy;
+        if (nx >= 0 && nx < BW && ny >= 0) nidx = k * nbf + ny * BW + nx;
+      } else if (lane < 13 && k > 0) {
+        const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
+        if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) nidx = (k - 1) * nbf + ny * BW + nx;
+      }
+      if (nidx >= 0) {
+        const volatile int* f = flags + nidx;
+        const volatile int* err = &ctrl->error;
+        const long long t0 = seq_ns();
+        while (*f != epoch && *err == 0) {
+          if (seq_ns() - t0 > timeout) {
+            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+            atomicExch(&ctrl->err_item, s_item);
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __syncwarp();
+      __threadfence();
+      const PbmResult r = warp_pbm<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, H, p, a.lam,
+                                         field, prev, bx, by, intra[(size_t)k * nbf + b], a.alpha,
+                                         a.beta, a.gnum, a.gden, a.qp, a.refine, curs, smem);
+      if (lane == 0) {
+        s_key = r.key;
+        s_pass = r.pass ? 1 : 0;
+        s_load = r.load;
+      }
+    }
+    __syncthreads();
+    const bool pass = s_pass != 0;
+    unsigned long long key = s_key;
+    if (!pass) {
+      const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
+      fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, bx * N, by * M, g, a.lam, smem, keys);
+      key = keys[0];
+    }
+    if (tid == 0) {
+      const Decoded d = decode_key(key, p, a.lam);
+      const size_t o = (size_t)k * nbf + b;
+      field[2 * b] = (int16_t)d.mvx;
+      field[2 * b + 1] = (int16_t)d.mvy;
+      a.J[o] = d.J;
+      a.mask[o] = pass ? 0 : 1;
+      if (a.sad) a.sad[o] = d.sad;
+      if (a.load) a.load[o] = pass ? (uint32_t)s_load : (uint32_t)((2 * p + 1) * (2 * p + 1));
+      __threadfence();
+      atomicExch(flags + (size_t)k * nbf + b, epoch);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ plans
+
+struct SeqPlan {
+  int dev, W, H, N, M, p, K, T;
+  void* mem = nullptr;
+  uint8_t* refpad = nullptr;
+  uint32_t* intra = nullptr;
+  int* flags = nullptr;
+  SeqSeg* segs = nullptr;
+  SeqCtrl* ctrl = nullptr;
+  int nseg = 0, total = 0;
+  size_t smem = 0;
+  int grid = 0;
+  cudaEvent_t last = nullptr;   // end of the previous run (runs of one plan never overlap)
+  bool ran = false;
+  std::mutex mu;
+};
+
+static std::mutex g_seq_mu;
+static std::vector<SeqPlan*> g_seq_plans;
+
+template <int N, int M, int T>
+static size_t seq_smem(int p) {
+  return std::max(fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads)),
+                  (size_t)4 * pbm_win_words(N, M, p));
+}
+
+#define ME_SEQ_NMT(X)                                                                          \
+  X(16, 16, 8) X(16, 16, 11) X(16, 16, 13) X(16, 16, 16) X(16, 8, 8) X(16, 4, 8) X(8, 16, 8)   \
+  X(8, 8, 8) X(8, 4, 8) X(4, 16, 8) X(4, 8, 8) X(4, 4, 8)
+
+static int seq_T(int N, int M, int p) {
+  if (!(N == 16 && M == 16)) return 8;
+  static const int Ts[] = {8, 11, 13, 16};
+  int bestT = 13;
+  double best = 1e300;
+  for (int T : Ts) {
+    const int n = 2 * p + 1, nseg = (n + T - 1) / T;
+    const double waste = (double)(nseg * T + M - 1) * (1.0 + 4.0 / T);
+    if (waste < best * 0.999) { best = waste; bestT = T; }
+  }
+  return bestT;
+}
+
+static int build_seq_plan(SeqPlan* pl) {
+  const int N = pl->N, M = pl->M, BW = pl->W / N, BH = pl->H / M, nbf = BW * BH;
+  const Waves wv = make_waves(BW, BH);
+  std::vector<SeqSeg> segs;
+  int base = 0;
+  const int maxkey = wv.n - 1 + kSeqLag * (pl->K - 1);
+  for (int key = 0; key <= maxkey; key++)
+    for (int k = 0; k < pl->K; k++) {
+      const int w = key - kSeqLag * k;
+      if (w < 0 || w >= wv.n || wv.count(w) == 0) continue;
+      segs.push_back(SeqSeg{k, w, wv.ylo(w), wv.count(w), base});
+      base += wv.count(w);
+    }
+  pl->nseg = (int)segs.size();
+  pl->total = base;
+  const PadGeom pg = pad_geom(pl->W, pl->H, pl->p);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_ctrl = take(sizeof(SeqCtrl));
+  const size_t o_segs = take(sizeof(SeqSeg) * segs.size());
+  const size_t o_pad = take((size_t)pg.pitch * pg.rows * pl->K);
+  const size_t o_intra = take(4 * (size_t)nbf * pl->K);
+  const size_t o_flags = take(4 * (size_t)nbf * pl->K);
+  ME_CUDA(cudaMalloc(&pl->mem, off));
+  ME_CUDA(cudaMemset(pl->mem, 0, off));
+  uint8_t* m = static_cast<uint8_t*>(pl->mem);
+  pl->ctrl = reinterpret_cast<SeqCtrl*>(m + o_ctrl);
+  pl->segs = reinterpret_cast<SeqSeg*>(m + o_segs);
+  pl->refpad = m + o_pad;
+  pl->intra = reinterpret_cast<uint32_t*>(m + o_intra);
+  pl->flags = reinterpret_cast<int*>(m + o_flags);
+  ME_CUDA(cudaMemcpy(pl->segs, segs.data(), sizeof(SeqSeg) * segs.size(), cudaMemcpyHostToDevice));
+  SeqCtrl c;
+  std::memset(&c, 0, sizeof(c));
+  c.timeout_ns = 1000000000ll;
+  ME_CUDA(cudaMemcpy(pl->ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
+  pl->T = seq_T(N, M, pl->p);
+  int nsm = 0, per_sm = 0, st = ME_ERR_ARG;
+  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->dev));
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && pl->T == t_) {                                                     \
+    pl->smem = seq_smem<n_, m_, t_>(pl->p);                                                    \
+    ME_CUDA(cudaFuncSetAttribute(k_acbm_seq<n_, m_, t_>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem)); \
+    ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<n_, m_, t_>,     \
+                                                          kSeqThreads, pl->smem));             \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ_NMT(X)
+#undef X
+  pl->grid = std::max(1, per_sm) * nsm;
+  ME_CUDA(cudaEventCreateWithFlags(&pl->last, cudaEventDisableTiming));
+  return st;
+}
+
+static int get_seq_plan(int W, int H, int N, int M, int p, int K, SeqPlan** out) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_seq_mu);
+  for (SeqPlan* pl : g_seq_plans)
+    if (pl->dev == dev && pl->W == W && pl->H == H && pl->N == N && pl->M == M && pl->p == p &&
+        pl->K == K) {
+      *out = pl;
+      return ME_OK;
+    }
+  SeqPlan* pl = new SeqPlan();
+  pl->dev = dev; pl->W = W; pl->H = H; pl->N = N; pl->M = M; pl->p = p; pl->K = K;
+  const int st = build_seq_plan(pl);
+  if (st) {
+    if (pl->mem) cudaFree(pl->mem);
+    delete pl;
+    return st;
+  }
+  g_seq_plans.push_back(pl);
+  *out = pl;
+  return ME_OK;
+}
+
+static int check_seq_frames(const uint8_t* const* frames, int K) {
+  if (!frames || K < 1 || K > kSeqMax) return ME_ERR_ARG;
+  for (int k = 0; k <= K; k++)
+    if (!frames[k] || !aligned4(frames[k])) return ME_ERR_ARG;
+  return ME_OK;
+}
+
+}  // namespace me
+
+using namespace me;
+
+extern "C" {
+
+int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out,
+                     me_stream_t stream) {
+  int st = check_seq_frames(frames, K);
+  if (st) return st;
+  if (!mv_out || !J_out) return ME_ERR_ARG;
+  st = check_frame_args(W, H, N, M, p, lambda_q8);
+  if (st) return st;
+  SeqFrames fr;
+  std::memset(&fr, 0, sizeof(fr));
+  for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
+  FsPlan pl = fs_plan(N, M, p, W / N);
+  const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
+  const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && pl.T == t_) {                                                      \
+    ME_CUDA(cudaFuncSetAttribute(k_fsbm_seq<n_, m_, t_>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));  \
+    k_fsbm_seq<n_, m_, t_><<<grid, pl.threads, pl.smem, s>>>(fr, W, H, p, pl.G, lambda_q8,     \
+                                                            mv_out, J_out, sad_out);           \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, const int16_t* prev_mv_field, const me_acbm_params* prm,
+                     int16_t* mv_out, uint32_t* J_out, uint8_t* fullsearch_mask_out,
+                     uint32_t* sad_out, uint32_t* load_out, me_stream_t stream) {
+  int st = check_seq_frames(frames, K);
+  if (st) return st;
+  if (!mv_out || !J_out || !fullsearch_mask_out) return ME_ERR_ARG;
+  st = check_frame_args(W, H, N, M, p, lambda_q8);
+  if (st) return st;
+  st = check_acbm_params(prm);
+  if (st) return st;
+  SeqPlan* pl = nullptr;
+  st = get_seq_plan(W, H, N, M, p, K, &pl);
+  if (st) return st;
+  SeqFrames fr;
+  std::memset(&fr, 0, sizeof(fr));
+  for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
+  SeqArgs a;
+  a.prev0 = prev_mv_field;
+  a.mv = mv_out; a.J = J_out; a.mask = fullsearch_mask_out; a.sad = sad_out; a.load = load_out;
+  a.lam = lambda_q8;
+  a.alpha = prm->alpha; a.beta = prm->beta; a.gnum = prm->gamma_num; a.gden = prm->gamma_den;
+  a.qp = prm->qp; a.refine = prm->refine;
+  const PadGeom pg = pad_geom(W, H, p);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // runs that share a plan's scratch are ordered on the GPU, whatever their streams
+  std::lock_guard<std::mutex> lk(pl->mu);
+  if (pl->ran) ME_CUDA(cudaStreamWaitEvent(s, pl->last, 0));
+  k_seq_begin<<<1, 1, 0, s>>>(pl->ctrl);
+  ME_CUDA(cudaGetLastError());
+  const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16) * K,
+                                             32LL * (W / N) * (H / M) * K);
+  const int gp = (int)std::min<long long>((work + 255) / 256, 152 * 8);
+  st = ME_ERR_ARG;
+#define X(n_, m_)                                                                              \
+  if (N == n_ && M == m_) {                                                                    \
+    k_seq_prologue<n_, m_><<<gp, 256, 0, s>>>(fr, K, pg, W, H, pl->refpad, pl->intra);         \
+    st = ME_OK;                                                                                \
+  }
+  X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && pl->T == t_) {                                                     \
+    k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
+        fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->segs, pl->nseg, pl->total,   \
+        pl->ctrl);                                                                             \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  ME_CUDA(cudaEventRecord(pl->last, s));
+  pl->ran = true;
+  return ME_OK;
+}
+
+int me_acbm_sequence_status(int W, int H, int N, int M, int p, int K, me_stream_t stream) {
+  SeqPlan* pl = nullptr;
+  int st = get_seq_plan(W, H, N, M, p, K, &pl);
+  if (st) return st;
+  ME_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  SeqCtrl c;
+  ME_CUDA(cudaMemcpy(&c, pl->ctrl, sizeof(c), cudaMemcpyDeviceToHost));
+  return c.error ? c.error : ME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""Sequence calls: FSBM / ACBM over K consecutive frame pairs in one launch.
+
+ACBM pairs overlap on the GPU (a block of pair k waits only for its spatial
+neighbours in pair k and its 3x3 neighbourhood in pair k-1), so these tests
+check that the result is exactly that of K chained single-pair runs: against
+the oracle chained frame by frame and against chained me_acbm calls."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def me():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_0710_4819_gb300 as me
+    me.load_library(build_if_missing=True)
+    return me
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_fsbm_sequence_matches_oracle(me, orc):
+    import torch
+    seq = synth.config_sequence("qcif", seed=41)
+    lam = orc.lambda_q8(28)
+    r = me.me_fsbm_sequence(torch.from_numpy(seq).cuda(), 16, 16, 16, lam)
+    torch.cuda.synchronize()
+    for k in range(seq.shape[0] - 1):
+        mv, J, sad = orc.fsbm(seq[k + 1], seq[k], 16, 16, 16, lam, nthreads=8)
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), k
+        assert np.array_equal(_u32(r.J[k]), J), k
+        assert np.array_equal(_u32(r.sad[k]), sad), k
+
+
+@pytest.mark.parametrize("name,n,p,qp", [("qcif", 10, 16, 28), ("cif", 5, 16, 40),
+                                         ("1080p", 3, 32, 28)])
+def test_acbm_sequence_matches_chained_oracle(me, orc, name, n, p, qp):
+    import torch
+    seq = synth.config_sequence(name, seed=42, n_frames=n)
+    lam = orc.lambda_q8(qp)
+    frames = torch.from_numpy(seq).cuda()
+    r = me.me_acbm_sequence(frames, 16, 16, p, lam, me.params(qp=qp))
+    me.me_acbm_sequence_status(seq.shape[2], seq.shape[1], 16, 16, p, n - 1)
+    prev = None
+    fs = 0
+    for k in range(n - 1):
+        mv, J, mask, sad, load = orc.acbm(seq[k + 1], seq[k], 16, 16, p, lam, orc.params(qp=qp), prev)
+        prev = mv
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), (name, k, "mv")
+        assert np.array_equal(_u32(r.J[k]), J), (name, k, "J")
+        assert np.array_equal(r.mask[k].cpu().numpy(), mask), (name, k, "mask")
+        assert np.array_equal(_u32(r.sad[k]), sad), (name, k, "sad")
+        assert np.array_equal(_u32(r.load[k]), load), (name, k, "load")
+        fs += int(mask.sum())
+    assert fs > 0
+
+
+@pytest.mark.parametrize("N,M", [(8, 8), (16, 8), (4, 4)])
+def test_acbm_sequence_equals_chained_calls(me, N, M):
+    import torch
+    seq = synth.scene_sequence(43, 12 * N, 9 * M, 6, n_objects=3, vmax=3)
+    frames = torch.from_numpy(seq).cuda()
+    lam = me.me_lambda_q8(28)
+    for kw in (dict(qp=28), dict(qp=28, refine=0), dict(alpha=0, beta=0, gamma_num=0, qp=28)):
+        prm = me.params(**kw)
+        r = me.me_acbm_sequence(frames, N, M, 5, lam, prm)
+        prev = None
+        for k in range(5):
+            a = me.me_acbm(frames[k + 1], frames[k], N, M, 5, lam, prm, prev_mv=prev)
+            torch.cuda.synchronize()
+            for x, y in ((r.mv[k], a.mv), (r.J[k], a.J), (r.mask[k], a.mask), (r.sad[k], a.sad),
+                         (r.load[k], a.load)):
+                assert torch.equal(x, y), (N, M, kw, k)
+            prev = a.mv
+
+
+def test_sequence_with_given_prev_field_and_repeat_runs(me, orc):
+    """A sequence continuing from a given field; the same plan run twice."""
+    import torch
+    seq = synth.config_sequence("qcif", seed=44)
+    lam = orc.lambda_q8(28)
+    frames = torch.from_numpy(seq).cuda()
+    first = me.me_acbm_sequence(frames[:4], 16, 16, 16, lam, me.params(qp=28))
+    prev = first.mv[2].contiguous()
+    for _ in range(2):
+        r = me.me_acbm_sequence(frames[3:7], 16, 16, 16, lam, me.params(qp=28), prev_mv=prev)
+        torch.cuda.synchronize()
+        p_o = prev.cpu().numpy()
+        for k in range(3):
+            mv, J, mask, sad, load = orc.acbm(seq[4 + k], seq[3 + k], 16, 16, 16, lam,
+                                              orc.params(qp=28), p_o)
+            p_o = mv
+            assert np.array_equal(r.mv[k].cpu().numpy(), mv)
+            assert np.array_equal(r.mask[k].cpu().numpy(), mask)
+
+
+def test_sequence_argument_errors(me):
+    import torch
+    f = torch.zeros((70, 32, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(me.MeError) as e:
+        me.me_fsbm_sequence(f, 16, 16, 4, 0)          # K = 69 > 64
+    assert e.value.status == 1
+    with pytest.raises(me.MeError) as e:
+        me.me_acbm_sequence(f[:3, :, :30].contiguous(), 16, 16, 4, 0, me.params())
+    assert e.value.status == 2
