@@ -44,7 +44,7 @@ WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=SEQ_FRAMES)
