@@ -53,6 +53,7 @@ struct SeqSeg {  // the blocks of wave w of pair k, claimed as one run of items
 struct SeqCtrl {
   int epoch, next, error, err_item;
   long long timeout_ns;
+  int fs_head, fs_tail, pbm_done, pad;
 };
 
 // ------------------------------------------------------------------ FSBM
@@ -95,6 +96,9 @@ __global__ void k_seq_begin(SeqCtrl* c) {
   c->next = 0;
   c->error = 0;
   c->err_item = -1;
+  c->fs_head = 0;
+  c->fs_tail = 0;
+  c->pbm_done = 0;
 }
 
 // Padded references and scaled Intra_SAD of all K pairs.
@@ -131,6 +135,31 @@ __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGe
   }
 }
 
+// Bounded wait until *f == want; gives up (and flags the error for everyone)
+// after the timeout or as soon as another wait has given up.
+static __device__ __forceinline__ void seq_wait(const int* f, int want, SeqCtrl* ctrl,
+                                                long long timeout, int item) {
+  const volatile int* vf = f;
+  const volatile int* err = &ctrl->error;
+  const long long t0 = seq_ns();
+  while (*vf != want && *err == 0) {
+    if (seq_ns() - t0 > timeout) {
+      atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+      atomicExch(&ctrl->err_item, item);
+      break;
+    }
+    __nanosleep(32);
+  }
+}
+
+// Two roles in one launch.  The first half of the CTAs (one per SM) run PBM:
+// each warp claims blocks on its own in the (wave + 4*pair) order, waits for
+// the block's predecessors, runs PBM and the two conditions, and either
+// publishes the block or appends it to the full-search queue.  The second half
+// take queued blocks in order and search each with the whole CTA.  A PBM warp
+// only waits for blocks claimed before its own, and a search CTA only for a
+// queue entry that a running PBM warp will write (or for the end of the run),
+// so every wait ends.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
                                                              int p, PadGeom pg,
@@ -138,22 +167,33 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              const uint32_t* __restrict__ intra,
                                                              int* __restrict__ flags,
                                                              const SeqSeg* __restrict__ seg, int nseg,
-                                                             int total, SeqCtrl* ctrl) {
+                                                             int total, SeqCtrl* ctrl,
+                                                             int* __restrict__ q_item,
+                                                             int* __restrict__ q_ready,
+                                                             int pbm_warps) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ uint32_t curs[M * (N / 4)];
-  __shared__ int s_item, s_k, s_b, s_pass, s_load;
-  __shared__ unsigned long long s_key;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int s_slot, s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int BW = W / N, BH = H / M, nbf = BW * BH;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
-  for (;;) {
-    if (tid == 0) {
-      const int i = atomicAdd(&ctrl->next, 1);
-      s_item = i;
-      if (i < total) {
+  const int n = 2 * p + 1;
+
+  if (blockIdx.x < gridDim.x / 2) {
+    // ---------------------------------------------------------------- PBM warps
+    if (warp >= pbm_warps) return;   // shared memory holds pbm_warps windows
+    const int wwords = pbm_win_words(N, M, p) + M * (N / 4);
+    uint32_t* win = smem + warp * wwords;
+    uint32_t* curs = win + pbm_win_words(N, M, p);
+    for (;;) {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&ctrl->next, 1);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i >= total) break;
+      int k = 0, b = 0;
+      if (lane == 0) {
         int lo = 0, hi = nseg - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) / 2;
@@ -161,17 +201,14 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         }
         const SeqSeg sg = seg[lo];
         const int by = sg.ylo + (i - sg.item_base);
-        s_k = sg.k;
-        s_b = by * BW + (sg.wave - 2 * by);
+        k = sg.k;
+        b = by * BW + (sg.wave - 2 * by);
       }
-    }
-    __syncthreads();
-    if (s_item >= total) break;
-    const int k = s_k, b = s_b;
-    const int bx = b % BW, by = b / BW;
-    int16_t* field = a.mv + (size_t)k * nbf * 2;
-    const int16_t* prev = k > 0 ? a.mv + (size_t)(k - 1) * nbf * 2 : a.prev0;
-    if (tid < 32) {
+      k = __shfl_sync(0xffffffffu, k, 0);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      const int bx = b % BW, by = b / BW;
+      int16_t* field = a.mv + (size_t)k * nbf * 2;
+      const int16_t* prev = k > 0 ? a.mv + (size_t)(k - 1) * nbf * 2 : a.prev0;
       // lanes 0-3: spatial predecessors in pair k; lanes 4-12: the 3x3 in pair k-1
       int nidx = -1;
       if (lane < 4) {
@@ -183,51 +220,82 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
         if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) nidx = (k - 1) * nbf + ny * BW + nx;
       }
-      if (nidx >= 0) {
-        const volatile int* f = flags + nidx;
-        const volatile int* err = &ctrl->error;
-        const long long t0 = seq_ns();
-        while (*f != epoch && *err == 0) {
-          if (seq_ns() - t0 > timeout) {
-            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
-            atomicExch(&ctrl->err_item, s_item);
-            break;
-          }
-          __nanosleep(20);
-        }
-      }
+      if (nidx >= 0) seq_wait(flags + nidx, epoch, ctrl, timeout, i);
       __syncwarp();
       __threadfence();
       const PbmResult r = warp_pbm<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, H, p, a.lam,
                                          field, prev, bx, by, intra[(size_t)k * nbf + b], a.alpha,
-                                         a.beta, a.gnum, a.gden, a.qp, a.refine, curs, smem);
+                                         a.beta, a.gnum, a.gden, a.qp, a.refine, curs, win);
       if (lane == 0) {
-        s_key = r.key;
-        s_pass = r.pass ? 1 : 0;
-        s_load = r.load;
+        const size_t o = (size_t)k * nbf + b;
+        if (r.pass) {
+          const Decoded d = decode_key(r.key, p, a.lam);
+          field[2 * b] = (int16_t)d.mvx;
+          field[2 * b + 1] = (int16_t)d.mvy;
+          a.J[o] = d.J;
+          a.mask[o] = 0;
+          if (a.sad) a.sad[o] = d.sad;
+          if (a.load) a.load[o] = (uint32_t)r.load;
+          __threadfence();
+          atomicExch(flags + o, epoch);
+        } else {
+          const int slot = atomicAdd(&ctrl->fs_tail, 1);
+          q_item[slot] = (int)o;
+          __threadfence();
+          atomicExch(q_ready + slot, epoch);
+        }
+        __threadfence();
+        atomicAdd(&ctrl->pbm_done, 1);
       }
+      __syncwarp();
     }
-    __syncthreads();
-    const bool pass = s_pass != 0;
-    unsigned long long key = s_key;
-    if (!pass) {
+  } else {
+    // ---------------------------------------------------------------- search CTAs
+    for (;;) {
+      if (tid == 0) {
+        const int slot = atomicAdd(&ctrl->fs_head, 1);
+        const volatile int* rd = q_ready + slot;
+        const volatile int* done = &ctrl->pbm_done;
+        const volatile int* tail = &ctrl->fs_tail;
+        const volatile int* err = &ctrl->error;
+        const long long t0 = seq_ns();
+        int got = -1;
+        for (;;) {
+          if (*rd == epoch) { got = slot; break; }
+          if (*done == total && *tail <= slot) break;     // no more blocks will come
+          if (*err != 0) break;
+          if (seq_ns() - t0 > timeout) {
+            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (got >= 0) {
+          __threadfence();
+          s_item = *reinterpret_cast<volatile int*>(q_item + slot);
+        }
+        s_slot = got;
+      }
+      __syncthreads();
+      if (s_slot < 0) break;
+      const int o = s_item;
+      const int k = o / nbf, b = o - k * nbf;
       const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
-      fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, bx * N, by * M, g, a.lam, smem, keys);
-      key = keys[0];
+      fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
+      if (tid == 0) {
+        const Decoded d = decode_key(keys[0], p, a.lam);
+        int16_t* field = a.mv + (size_t)k * nbf * 2;
+        field[2 * b] = (int16_t)d.mvx;
+        field[2 * b + 1] = (int16_t)d.mvy;
+        a.J[o] = d.J;
+        a.mask[o] = 1;
+        if (a.sad) a.sad[o] = d.sad;
+        if (a.load) a.load[o] = (uint32_t)(n * n);
+        __threadfence();
+        atomicExch(flags + o, epoch);
+      }
+      __syncthreads();
     }
-    if (tid == 0) {
-      const Decoded d = decode_key(key, p, a.lam);
-      const size_t o = (size_t)k * nbf + b;
-      field[2 * b] = (int16_t)d.mvx;
-      field[2 * b + 1] = (int16_t)d.mvy;
-      a.J[o] = d.J;
-      a.mask[o] = pass ? 0 : 1;
-      if (a.sad) a.sad[o] = d.sad;
-      if (a.load) a.load[o] = pass ? (uint32_t)s_load : (uint32_t)((2 * p + 1) * (2 * p + 1));
-      __threadfence();
-      atomicExch(flags + (size_t)k * nbf + b, epoch);
-    }
-    __syncthreads();
   }
 }
 
@@ -239,6 +307,8 @@ struct SeqPlan {
   uint8_t* refpad = nullptr;
   uint32_t* intra = nullptr;
   int* flags = nullptr;
+  int* q_item = nullptr;
+  int* q_ready = nullptr;
   SeqSeg* segs = nullptr;
   SeqCtrl* ctrl = nullptr;
   int nseg = 0, total = 0;
@@ -252,10 +322,16 @@ struct SeqPlan {
 static std::mutex g_seq_mu;
 static std::vector<SeqPlan*> g_seq_plans;
 
+// PBM warps per CTA: as many windows as fit in about 100 KB (8 at p = 32).
+static int seq_pbm_warps(int N, int M, int p) {
+  const size_t per = (size_t)4 * (pbm_win_words(N, M, p) + M * (N / 4));
+  return (int)std::max<size_t>(1, std::min<size_t>(kSeqThreads / 32, (100 * 1024) / per));
+}
+
 template <int N, int M, int T>
 static size_t seq_smem(int p) {
-  return std::max(fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads)),
-                  (size_t)4 * pbm_win_words(N, M, p));
+  const size_t pbm = (size_t)4 * seq_pbm_warps(N, M, p) * (pbm_win_words(N, M, p) + M * (N / 4));
+  return std::max(fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads)), pbm);
 }
 
 #define ME_SEQ_NMT(X)                                                                          \
@@ -298,6 +374,8 @@ static int build_seq_plan(SeqPlan* pl) {
   const size_t o_pad = take((size_t)pg.pitch * pg.rows * pl->K);
   const size_t o_intra = take(4 * (size_t)nbf * pl->K);
   const size_t o_flags = take(4 * (size_t)nbf * pl->K);
+  const size_t o_qitem = take(4 * (size_t)nbf * pl->K);
+  const size_t o_qready = take(4 * (size_t)nbf * pl->K);
   ME_CUDA(cudaMalloc(&pl->mem, off));
   ME_CUDA(cudaMemset(pl->mem, 0, off));
   uint8_t* m = static_cast<uint8_t*>(pl->mem);
@@ -306,6 +384,8 @@ static int build_seq_plan(SeqPlan* pl) {
   pl->refpad = m + o_pad;
   pl->intra = reinterpret_cast<uint32_t*>(m + o_intra);
   pl->flags = reinterpret_cast<int*>(m + o_flags);
+  pl->q_item = reinterpret_cast<int*>(m + o_qitem);
+  pl->q_ready = reinterpret_cast<int*>(m + o_qready);
   ME_CUDA(cudaMemcpy(pl->segs, segs.data(), sizeof(SeqSeg) * segs.size(), cudaMemcpyHostToDevice));
   SeqCtrl c;
   std::memset(&c, 0, sizeof(c));
@@ -325,7 +405,9 @@ static int build_seq_plan(SeqPlan* pl) {
   }
   ME_SEQ_NMT(X)
 #undef X
-  pl->grid = std::max(1, per_sm) * nsm;
+  // half the CTAs run PBM warps, half the full searches: two per SM
+  pl->grid = 2 * nsm;
+  if (per_sm < 2) st = ME_ERR_CUDA;
   ME_CUDA(cudaEventCreateWithFlags(&pl->last, cudaEventDisableTiming));
   return st;
 }
@@ -445,7 +527,7 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   if (N == n_ && M == m_ && pl->T == t_) {                                                     \
     k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
         fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->segs, pl->nseg, pl->total,   \
-        pl->ctrl);                                                                             \
+        pl->ctrl, pl->q_item, pl->q_ready, seq_pbm_warps(N, M, p));                            \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)
