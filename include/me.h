@@ -290,9 +290,11 @@ int me_acbm_noalloc(const uint8_t *cur, const uint8_t *ref, int W, int H, int N,
 
 /* Measures the integer-pipe rate of a packed-SAD instruction form on the
  * current device with no memory traffic (the roofline denominator of the SAD
- * kernels).  variant 0: vabsdiff4 with accumulate; 1: per-byte absolute
- * difference + dp4a byte sum.  Writes absolute differences per second, and
- * lane-operations per SM clock (from the SM cycle counter).  Synchronous. */
+ * kernels).  variant 0: vabsdiff4 with accumulate (the form the kernels
+ * use); 1: per-byte absolute difference + dp4a byte sum; 2: __vsadu4 + add;
+ * 3: per-byte max - min + dp4a; 4: vabsdiff2 with accumulate (16-bit lanes).
+ * Writes absolute differences per second, and operations per SM clock per
+ * SM (from the SM cycle counter).  Synchronous. */
 int me_sad_peak(int variant, double *absdiff_per_s, double *lane_ops_per_clk_per_sm,
                 me_stream_t stream);
 

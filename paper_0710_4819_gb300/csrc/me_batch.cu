@@ -42,6 +42,9 @@ struct me_batch {
   me::BSegment* d_segs = nullptr;
   me::BFsEntry* d_fsent = nullptr;
   me::BCtrl* d_ctrl = nullptr;
+  unsigned long long* d_qitem = nullptr;   // full-search queue of the ACBM step
+  int* d_qready = nullptr;
+  int p_max = 1;
   static constexpr int kRing = 4;       // staging buffers in flight
   me::BStream* h_streams = nullptr;     // pinned staging of the per-run arguments [kRing][n]
   me::BCtrl* h_ctrl = nullptr;          // pinned read-back of the control block
@@ -99,9 +102,16 @@ int batch_choose_T(int N, int M, const std::vector<BShape>& shapes) {
   return bestT;
 }
 
+size_t acbm_step_smem(int N, int M, int T, int p_max) {
+  const size_t pbm =
+      (size_t)4 * batch_pbm_warps(N, M, p_max) * (pbm_win_words(N, M, p_max) + M * (N / 4));
+  return std::max(batch_smem(N, M, T, p_max, 1), pbm);
+}
+
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
-                     const BSegment* segs, int nseg, int total_items, size_t smem, cudaStream_t s) {
+                     const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
+                     unsigned long long* q_item, int* q_ready, cudaStream_t s) {
   k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
   const int gp = (int)std::max<long long>(1, std::min<long long>((total_pad + 255) / 256, 152 * 16));
@@ -118,14 +128,21 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
 #undef X
   if (st) return st;
   ME_CUDA(cudaGetLastError());
+  // half the CTAs run PBM warps, half the full searches: two per SM
+  int dev = 0, nsm = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int pw = batch_pbm_warps(N, M, p_max);
+  const int ww = pbm_win_words(N, M, p_max);
   st = ME_ERR_ARG;
 #define X(n_, m_, t_)                                                                          \
   if (N == n_ && M == m_ && T == t_) {                                                         \
     int grid = 0;                                                                              \
     st = persistent_grid((const void*)k_acbm_persist<n_, m_, t_>, smem, &grid);                \
+    if (st == ME_OK && grid < 2 * nsm) st = ME_ERR_CUDA;  /* needs two CTAs per SM */         \
     if (st == ME_OK)                                                                           \
-      k_acbm_persist<n_, m_, t_><<<grid, kBatchThreads, smem, s>>>(shapes, streams, segs, nseg, \
-                                                                   total_items, ctrl);         \
+      k_acbm_persist<n_, m_, t_><<<2 * nsm, kBatchThreads, smem, s>>>(                         \
+          shapes, streams, segs, nseg, total_items, ctrl, q_item, q_ready, pw, ww);            \
   }
   ME_BATCH_NMT(X)
 #undef X
@@ -193,11 +210,9 @@ static int batch_finalize(me_batch* b) {
     }
   }
   b->total_items = base;
-  size_t smem_a = 0;
-  for (const BShape& s : b->shapes)
-    smem_a = std::max({smem_a, batch_smem(b->N, b->M, b->T, s.p, 1),
-                       (size_t)4 * pbm_win_words(b->N, b->M, s.p)});
-  b->smem_acbm = smem_a;
+  b->p_max = 1;
+  for (const BShape& s : b->shapes) b->p_max = std::max(b->p_max, s.p);
+  b->smem_acbm = acbm_step_smem(b->N, b->M, b->T, b->p_max);
   // device memory: control, tables, per-stream scratch
   const size_t n = b->shapes.size();
   size_t off = 0;
@@ -207,6 +222,8 @@ static int batch_finalize(me_batch* b) {
   const size_t o_streams = take(sizeof(BStream) * n);
   const size_t o_segs = take(sizeof(BSegment) * b->segs.size());
   const size_t o_fsent = take(sizeof(BFsEntry) * b->fsent.size());
+  const size_t o_qitem = take(8 * (size_t)std::max(1, b->total_items));
+  const size_t o_qready = take(4 * (size_t)std::max(1, b->total_items));
   std::vector<size_t> o_pad(n), o_intra(n), o_flags(n);
   b->total_pad = 0;
   b->total_blocks = 0;
@@ -234,6 +251,8 @@ static int batch_finalize(me_batch* b) {
   b->d_streams = reinterpret_cast<BStream*>(base8 + o_streams);
   b->d_segs = reinterpret_cast<BSegment*>(base8 + o_segs);
   b->d_fsent = reinterpret_cast<BFsEntry*>(base8 + o_fsent);
+  b->d_qitem = reinterpret_cast<unsigned long long*>(base8 + o_qitem);
+  b->d_qready = reinterpret_cast<int*>(base8 + o_qready);
   ME_CUDA(cudaMemcpy(b->d_shapes, b->shapes.data(), sizeof(BShape) * n, cudaMemcpyHostToDevice));
   if (!b->segs.empty())
     ME_CUDA(cudaMemcpy(b->d_segs, b->segs.data(), sizeof(BSegment) * b->segs.size(),
@@ -274,7 +293,8 @@ static int batch_enqueue(me_batch* b, int mode, cudaStream_t s) {
                             (int)b->fsent.size(), b->smem_fs, s);
   return launch_acbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams,
                           (int)b->shapes.size(), b->total_pad, b->total_blocks, b->d_segs,
-                          (int)b->segs.size(), b->total_items, b->smem_acbm, s);
+                          (int)b->segs.size(), b->total_items, b->smem_acbm, b->p_max,
+                          b->d_qitem, b->d_qready, s);
 }
 
 }  // namespace me

@@ -12,6 +12,8 @@
 
 namespace me {
 
+constexpr int kBatchThreads = 256;
+
 struct BStream {  // per-run arguments of one stream (copied to the device each run)
   const uint8_t* cur;
   const uint8_t* ref;
@@ -50,6 +52,7 @@ struct BCtrl {
   int err_item;
   long long timeout_ns;
   int skip_stream, skip_block;  // fault injection: never publish this block
+  int fs_head, fs_tail, pbm_done, pad;  // full-search queue of the ACBM step
 };
 
 static __device__ __forceinline__ long long global_ns() {
@@ -60,6 +63,9 @@ static __device__ __forceinline__ long long global_ns() {
 
 static __global__ void k_batch_begin(BCtrl* c, int epoch) {
   c->epoch = epoch > 0 ? epoch : c->epoch + 1;
+  c->fs_head = 0;
+  c->fs_tail = 0;
+  c->pbm_done = 0;
   c->next = 0;
   c->error = 0;
   c->err_item = -1;
@@ -140,24 +146,67 @@ __global__ void __launch_bounds__(256, 2) k_fsbm_persist(const BShape* __restric
   }
 }
 
+// Bounded wait until *f == want (gives up after the timeout, or at once after
+// any other wait has given up, and then reports ME_ERR_TIMEOUT).
+static __device__ __forceinline__ void batch_wait(const int* f, int want, BCtrl* ctrl,
+                                                  long long timeout, int item) {
+  const volatile int* vf = f;
+  const volatile int* err = &ctrl->error;
+  const long long t0 = global_ns();
+  while (*vf != want && *err == 0) {
+    if (global_ns() - t0 > timeout) {
+      atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+      atomicExch(&ctrl->err_item, item);
+      break;
+    }
+    __nanosleep(32);
+  }
+}
+
+// PBM warps per CTA for a search range: as many windows as fit in about 100 KB.
+__host__ __device__ inline int batch_pbm_warps(int N, int M, int p) {
+  const int per = 4 * (pbm_win_words(N, M, p) + M * (N / 4));
+  const int w = (100 * 1024) / per;
+  return w < 1 ? 1 : (w > kBatchThreads / 32 ? kBatchThreads / 32 : w);
+}
+
+// ACBM step over many streams, two roles in one launch.  The first half of the
+// CTAs run PBM: every warp claims blocks on its own, in wave order across
+// streams, waits for the block's left / up-left / up / up-right neighbours,
+// runs PBM and the two conditions, and publishes the block or appends it to
+// the full-search queue.  The second half take queued blocks in order and
+// search each with the whole CTA.  PBM warps only wait for blocks claimed
+// before their own, search CTAs only for queue entries a running PBM warp
+// will write (or the end of the step): every wait ends, and each is also
+// bounded in time.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restrict__ shp,
-                                                      const BStream* __restrict__ st,
-                                                      const BSegment* __restrict__ seg, int nseg,
-                                                      int total, BCtrl* ctrl) {
+                                                         const BStream* __restrict__ st,
+                                                         const BSegment* __restrict__ seg, int nseg,
+                                                         int total, BCtrl* ctrl,
+                                                         unsigned long long* __restrict__ q_item,
+                                                         int* __restrict__ q_ready, int pbm_warps,
+                                                         int win_words) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ uint32_t curs[M * (N / 4)];
-  __shared__ int s_item, s_stream, s_b, s_pass, s_load;
-  __shared__ unsigned long long s_key;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int s_slot;
+  __shared__ unsigned long long s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
-  for (;;) {
-    if (tid == 0) {
-      const int i = atomicAdd(&ctrl->next, 1);
-      s_item = i;
-      if (i < total) {
+
+  if (blockIdx.x < gridDim.x / 2) {
+    // ---------------------------------------------------------------- PBM warps
+    if (warp >= pbm_warps) return;
+    uint32_t* win = smem + warp * (win_words + M * (N / 4));
+    uint32_t* curs = win + win_words;
+    for (;;) {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&ctrl->next, 1);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i >= total) break;
+      int si = 0, b = 0;
+      if (lane == 0) {
         int lo = 0, hi = nseg - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) / 2;
@@ -165,77 +214,101 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         }
         const BSegment sg = seg[lo];
         const int by = sg.ylo + (i - sg.item_base);
-        const int bx = sg.wave - 2 * by;
-        s_stream = sg.stream;
-        s_b = by * (shp[sg.stream].W / N) + bx;
+        si = sg.stream;
+        b = by * (shp[sg.stream].W / N) + (sg.wave - 2 * by);
       }
-    }
-    __syncthreads();
-    if (s_item >= total) break;
-    const int si = s_stream, b = s_b;
-    const BShape& s = shp[si];
-    const BStream& a = st[si];
-    const int BW = s.W / N;
-    const int bx = b % BW, by = b / BW;
-    if (tid < 32) {
-      // wait until the spatial predictors are final (bounded)
+      si = __shfl_sync(0xffffffffu, si, 0);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      const BShape& s = shp[si];
+      const BStream& a = st[si];
+      const int BW = s.W / N;
+      const int bx = b % BW, by = b / BW;
       if (lane < 4) {
         const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
         const int dy = (lane == 0) ? 0 : -1;
         const int nx = bx + dx, ny = by + dy;
-        if (nx >= 0 && nx < BW && ny >= 0) {
-          const volatile int* f = s.flags + ny * BW + nx;
-          const volatile int* err = &ctrl->error;
-          const long long t0 = global_ns();
-          // after the first wait that gave up, no other wait starts: the step
-          // finishes quickly and reports the error
-          while (*f != epoch && *err == 0) {
-            if (global_ns() - t0 > timeout) {
-              atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
-              atomicExch(&ctrl->err_item, s_item);
-              break;
-            }
-            __nanosleep(20);
-          }
-        }
+        if (nx >= 0 && nx < BW && ny >= 0) batch_wait(s.flags + ny * BW + nx, epoch, ctrl, timeout, i);
       }
       __syncwarp();
       __threadfence();
       const PbmResult r = warp_pbm<N, M>(a.cur, s.refpad, s.pg, s.W, s.H, s.p, a.lam, a.mv, a.prev,
                                          bx, by, s.intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp,
-                                         a.refine, curs, smem);
+                                         a.refine, curs, win);
       if (lane == 0) {
-        s_key = r.key;
-        s_pass = r.pass ? 1 : 0;
-        s_load = r.load;
+        if (r.pass) {
+          const Decoded d = decode_key(r.key, s.p, a.lam);
+          a.mv[2 * b] = (int16_t)d.mvx;
+          a.mv[2 * b + 1] = (int16_t)d.mvy;
+          a.J[b] = d.J;
+          a.mask[b] = 0;
+          if (a.sad) a.sad[b] = d.sad;
+          if (a.load) a.load[b] = (uint32_t)r.load;
+          __threadfence();
+          if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
+        } else {
+          const int slot = atomicAdd(&ctrl->fs_tail, 1);
+          q_item[slot] = ((unsigned long long)si << 32) | (unsigned)b;
+          __threadfence();
+          atomicExch(q_ready + slot, epoch);
+        }
+        __threadfence();
+        atomicAdd(&ctrl->pbm_done, 1);
       }
+      __syncwarp();
     }
-    __syncthreads();
-    const bool pass = s_pass != 0;
-    unsigned long long key = s_key;
-    if (!pass) {
+  } else {
+    // ---------------------------------------------------------------- search CTAs
+    for (;;) {
+      if (tid == 0) {
+        const int slot = atomicAdd(&ctrl->fs_head, 1);
+        const volatile int* rd = q_ready + slot;
+        const volatile int* done = &ctrl->pbm_done;
+        const volatile int* tail = &ctrl->fs_tail;
+        const volatile int* err = &ctrl->error;
+        const long long t0 = global_ns();
+        int got = -1;
+        for (;;) {
+          if (*rd == epoch) { got = slot; break; }
+          if (*done == total && *tail <= slot) break;     // no more blocks will come
+          if (*err != 0) break;
+          if (global_ns() - t0 > timeout) {
+            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (got >= 0) {
+          __threadfence();
+          s_item = *reinterpret_cast<volatile unsigned long long*>(q_item + slot);
+        }
+        s_slot = got;
+      }
+      __syncthreads();
+      if (s_slot < 0) break;
+      const int si = (int)(s_item >> 32), b = (int)(s_item & 0xffffffffu);
+      const BShape& s = shp[si];
+      const BStream& a = st[si];
+      const int BW = s.W / N;
       const FsGeom g = fs_geom<N, M, T>(s.p, 1, blockDim.x);
-      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, bx * N, by * M, g, a.lam, smem, keys);
-      key = keys[0];
+      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
+      if (tid == 0) {
+        const Decoded d = decode_key(keys[0], s.p, a.lam);
+        a.mv[2 * b] = (int16_t)d.mvx;
+        a.mv[2 * b + 1] = (int16_t)d.mvy;
+        a.J[b] = d.J;
+        a.mask[b] = 1;
+        if (a.sad) a.sad[b] = d.sad;
+        if (a.load) a.load[b] = (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
+        __threadfence();
+        if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
+      }
+      __syncthreads();
     }
-    if (tid == 0) {
-      const Decoded d = decode_key(key, s.p, a.lam);
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      a.mask[b] = pass ? 0 : 1;
-      if (a.sad) a.sad[b] = d.sad;
-      if (a.load) a.load[b] = pass ? (uint32_t)s_load : (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
-      __threadfence();
-      if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
-    }
-    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ host side
 
-constexpr int kBatchThreads = 256;
 
 template <int N, int M, int T>
 inline size_t smem_of(int p, int bpc) {
@@ -261,10 +334,16 @@ int batch_choose_T(int N, int M, const std::vector<BShape>& shapes);
 
 // Enqueues one ACBM step over the streams in the device tables: the begin
 // kernel (epoch = `epoch`, or the previous epoch + 1 when epoch <= 0), the
-// padding and Intra_SAD prologue, and the persistent kernel.
+// padding and Intra_SAD prologue, and the persistent kernel.  q_item and
+// q_ready hold at least total_items entries; smem and the PBM warp count
+// come from acbm_step_smem for the largest search range p_max.
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
-                     const BSegment* segs, int nseg, int total_items, size_t smem, cudaStream_t s);
+                     const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
+                     unsigned long long* q_item, int* q_ready, cudaStream_t s);
+
+// Dynamic shared memory of the ACBM step kernel for search ranges up to p_max.
+size_t acbm_step_smem(int N, int M, int T, int p_max);
 
 // Enqueues one FSBM step (begin kernel + persistent kernel).
 int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,

@@ -10,17 +10,27 @@
 
 namespace me {
 
+// Packed-SAD forms, each returning c + sum of |a.byte[k] - b.byte[k]|
+// (variant 4 works on two 16-bit lanes and counts two differences).
 template <int V>
 __device__ __forceinline__ uint32_t peak_op(uint32_t a, uint32_t b, uint32_t c) {
-  if (V == 0) {
-    uint32_t d;
-    asm volatile("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-  } else {
-    uint32_t t, d;
-    asm volatile("vabsdiff4.u32.u32.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(a), "r"(b), "r"(0u));
-    asm volatile("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(t), "r"(0x01010101u), "r"(c));
-    return d;
+  uint32_t t, d;
+  switch (V) {
+    case 0:  // one packed SAD-with-accumulate instruction
+      asm volatile("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+      return d;
+    case 1:  // per-byte absolute differences, then a byte dot product with ones
+      asm volatile("vabsdiff4.u32.u32.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(a), "r"(b), "r"(0u));
+      asm volatile("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(t), "r"(0x01010101u), "r"(c));
+      return d;
+    case 2:  // CUDA's SAD intrinsic plus an add
+      asm volatile("" ::: "memory");
+      return __vsadu4(a, b) + c;
+    case 3:  // per-byte max minus min, then the byte dot product
+      return __dp4a(__vmaxu4(a, b) - __vminu4(a, b), 0x01010101u, c);
+    default:  // two 16-bit lanes with accumulate
+      asm volatile("vabsdiff2.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+      return d;
   }
 }
 
@@ -83,7 +93,7 @@ static int run_peak(cudaStream_t s, double* per_s, double* per_clk) {
   scratch_free(mem, s);
   const long long mx = *std::max_element(h.begin(), h.end());
   const double ops = (double)grid * 256 * iters * 16 * 8;  // SAD steps of 4 pixels each
-  if (per_s) *per_s = 4.0 * ops / (ms * 1e-3);
+  if (per_s) *per_s = (V == 4 ? 2.0 : 4.0) * ops / (ms * 1e-3);
   if (per_clk) *per_clk = ops / nsm / (double)(mx > 0 ? mx : 1);
   return ME_OK;
 }
@@ -93,7 +103,12 @@ static int run_peak(cudaStream_t s, double* per_s, double* per_clk) {
 extern "C" int me_sad_peak(int variant, double* absdiff_per_s, double* lane_ops_per_clk_per_sm,
                            me_stream_t stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (variant == 0) return me::run_peak<0>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
-  if (variant == 1) return me::run_peak<1>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+  switch (variant) {
+    case 0: return me::run_peak<0>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+    case 1: return me::run_peak<1>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+    case 2: return me::run_peak<2>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+    case 3: return me::run_peak<3>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+    case 4: return me::run_peak<4>(s, absdiff_per_s, lane_ops_per_clk_per_sm);
+  }
   return ME_ERR_ARG;
 }

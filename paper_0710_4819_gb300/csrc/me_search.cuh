@@ -199,33 +199,28 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
     if (i < M * NW)
       cw[k] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
   }
-  // the search window: eight 16-byte loads per lane in flight before their stores
+  // the search window: every lane queues its 16-byte chunks as asynchronous
+  // global-to-shared copies, so the whole window costs one round trip
   const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
   {
     const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
     const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
     const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
     if (rl < rpp) {
-      for (int r0 = rl; r0 < wg.rows; r0 += 8 * rpp) {
-        uint4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const int r = r0 + u * rpp;
-          if (r < wg.rows) v[u] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * pg.pitch) + cl);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const int r = r0 + u * rpp;
-          if (r < wg.rows) *reinterpret_cast<uint4*>(win + r * wg.wp + 4 * cl) = v[u];
-        }
+      for (int r = rl; r < wg.rows; r += rpp) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(win + r * wg.wp + 4 * cl);
+        const void* g = src + (size_t)r * pg.pitch + 16 * cl;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g) : "memory");
       }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
 #pragma unroll
   for (int k = 0; k < CW; k++) {
     const int i = lane + 32 * k;
     if (i < M * NW) curs[i] = cw[k];
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
   cx = clampi(cx, -p, p);
   cy = clampi(cy, -p, p);

@@ -211,7 +211,7 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     std::vector<BSegment> segs;
     std::vector<BFsEntry> ent;
     size_t smem = 0;
-    int total_items = 0;
+    int total_items = 0, p_max = 1;
     if (acbm) {
       int maxw = 0;
       for (const BShape& sh : shapes) maxw = std::max(maxw, make_waves(sh.W / N, sh.H / M).n);
@@ -222,8 +222,8 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
           segs.push_back(BSegment{si, w, wv.ylo(w), wv.count(w), total_items});
           total_items += wv.count(w);
         }
-      for (const BShape& sh : shapes)
-        smem = std::max({smem, batch_smem(N, M, T, sh.p, 1), (size_t)4 * pbm_win_words(N, M, sh.p)});
+      for (const BShape& sh : shapes) p_max = std::max(p_max, sh.p);
+      smem = acbm_step_smem(N, M, T, p_max);
     } else {
       for (int si = 0; si < ns; si++) {
         const BShape& sh = shapes[si];
@@ -240,7 +240,10 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     const size_t o_st = align_up(o_sh + sizeof(BShape) * ns, 256);
     const size_t o_tab = align_up(o_st + sizeof(BStream) * ns, 256);
     const size_t tab = acbm ? sizeof(BSegment) * segs.size() : sizeof(BFsEntry) * ent.size();
-    int st = slot_reserve(sl, o_tab + tab + 256);
+    // full-search queue (ACBM): 8 + 4 bytes per block of the step
+    const size_t o_q = align_up(o_tab + tab, 256);
+    const size_t o_qr = align_up(o_q + 8 * (size_t)std::max(1, total_items), 256);
+    int st = slot_reserve(sl, o_qr + 4 * (size_t)std::max(1, total_items) + 256);
     if (st) return st;
     uint8_t* h = static_cast<uint8_t*>(sl.h_tab);
     uint8_t* d = static_cast<uint8_t*>(sl.d_tab);
@@ -254,7 +257,8 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
       st = launch_acbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
                             reinterpret_cast<BStream*>(d + o_st), ns, total_pad, total_blocks,
                             reinterpret_cast<BSegment*>(d + o_tab), (int)segs.size(), total_items,
-                            smem, sl.cs);
+                            smem, p_max, reinterpret_cast<unsigned long long*>(d + o_q),
+                            reinterpret_cast<int*>(d + o_qr), sl.cs);
     else
       st = launch_fsbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
                             reinterpret_cast<BStream*>(d + o_st),
