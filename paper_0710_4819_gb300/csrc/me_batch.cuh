@@ -52,7 +52,7 @@ struct BCtrl {
   int err_item;
   long long timeout_ns;
   int skip_stream, skip_block;  // fault injection: never publish this block
-  int fs_head, fs_tail, pbm_done, pad;  // full-search queue of the ACBM step
+  int fs_head, fs_tail, pbm_done, started;  // full-search queue of the ACBM step
 };
 
 static __device__ __forceinline__ long long global_ns() {
@@ -66,6 +66,7 @@ static __global__ void k_batch_begin(BCtrl* c, int epoch) {
   c->fs_head = 0;
   c->fs_tail = 0;
   c->pbm_done = 0;
+  c->started = 0;
   c->next = 0;
   c->error = 0;
   c->err_item = -1;
@@ -186,16 +187,24 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
                                                          int total, BCtrl* ctrl,
                                                          unsigned long long* __restrict__ q_item,
                                                          int* __restrict__ q_ready, int pbm_warps,
-                                                         int win_words) {
+                                                         int win_words, int nsm) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_slot;
+  __shared__ int s_slot, s_role;
   __shared__ unsigned long long s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
+  // role by arrival, alternating and shifted by one every nsm arrivals, so the
+  // two CTAs an SM receives differ and any three resident CTAs of this launch
+  // include both roles (another launch may hold the rest of the SMs)
+  if (tid == 0) {
+    const int arr = atomicAdd(&ctrl->started, 1);
+    s_role = (arr + arr / nsm) & 1;
+  }
+  __syncthreads();
 
-  if (blockIdx.x < gridDim.x / 2) {
+  if (s_role == 0) {
     // ---------------------------------------------------------------- PBM warps
     if (warp >= pbm_warps) return;
     uint32_t* win = smem + warp * (win_words + M * (N / 4));

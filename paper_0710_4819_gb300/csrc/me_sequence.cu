@@ -53,7 +53,7 @@ struct SeqSeg {  // the blocks of wave w of pair k, claimed as one run of items
 struct SeqCtrl {
   int epoch, next, error, err_item;
   long long timeout_ns;
-  int fs_head, fs_tail, pbm_done, pad;
+  int fs_head, fs_tail, pbm_done, started;
 };
 
 // ------------------------------------------------------------------ FSBM
@@ -99,6 +99,7 @@ __global__ void k_seq_begin(SeqCtrl* c) {
   c->fs_head = 0;
   c->fs_tail = 0;
   c->pbm_done = 0;
+  c->started = 0;
 }
 
 // Padded references and scaled Intra_SAD of all K pairs.
@@ -170,18 +171,26 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              int total, SeqCtrl* ctrl,
                                                              int* __restrict__ q_item,
                                                              int* __restrict__ q_ready,
-                                                             int pbm_warps) {
+                                                             int pbm_warps, int nsm) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_slot, s_item;
+  __shared__ int s_slot, s_item, s_role;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int BW = W / N, BH = H / M, nbf = BW * BH;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
   const int n = 2 * p + 1;
+  // role by arrival, alternating and shifted by one every nsm arrivals, so the
+  // two CTAs an SM receives differ and any three resident CTAs of this launch
+  // include both roles (another launch may hold the rest of the SMs)
+  if (tid == 0) {
+    const int arr = atomicAdd(&ctrl->started, 1);
+    s_role = (arr + arr / nsm) & 1;
+  }
+  __syncthreads();
 
-  if (blockIdx.x < gridDim.x / 2) {
+  if (s_role == 0) {
     // ---------------------------------------------------------------- PBM warps
     if (warp >= pbm_warps) return;   // shared memory holds pbm_warps windows
     const int wwords = pbm_win_words(N, M, p) + M * (N / 4);
@@ -527,7 +536,7 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   if (N == n_ && M == m_ && pl->T == t_) {                                                     \
     k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
         fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->segs, pl->nseg, pl->total,   \
-        pl->ctrl, pl->q_item, pl->q_ready, seq_pbm_warps(N, M, p));                            \
+        pl->ctrl, pl->q_item, pl->q_ready, seq_pbm_warps(N, M, p), pl->grid / 2);              \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)

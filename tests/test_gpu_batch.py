@@ -161,3 +161,37 @@ def test_batch_bounded_wait_reports_timeout(me):
     r = me.me_fsbm(seqs[0][1], seqs[0][0], 16, 16, 8, lam)
     torch.cuda.synchronize()
     assert r.mv.shape == (9, 11, 2)
+
+
+def test_two_batches_on_concurrent_streams(me):
+    """Two ACBM steps in flight at once on different CUDA streams (their
+    persistent launches share the SMs) both finish with their solo results."""
+    import torch
+    specs_a = [synth.StreamSpec("cif", 352, 288, 16, 7201 + i) for i in range(3)]
+    specs_b = [synth.StreamSpec("720p", 1280, 720, 32, 7301 + i) for i in range(2)]
+    lam = me.me_lambda_q8(28)
+    prm = me.params(qp=28)
+    runs = []
+    for specs in (specs_a, specs_b):
+        b = me.Batch()
+        for s in specs:
+            b.add_stream(s.w, s.height, 16, 16, s.p)
+        seqs = [torch.from_numpy(synth.stream_frames(s, 2)).cuda() for s in specs]
+        outs = [_alloc(me, s.height, s.w) for s in specs]
+        items = [_item(me, seqs[i][1], seqs[i][0], outs[i], lam, prm) for i in range(len(specs))]
+        runs.append((b, specs, seqs, outs, items))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for (b, specs, seqs, outs, items), st in zip(runs, streams):
+            b.run(1, items, stream=st)
+        for (b, *_), st in zip(runs, streams):
+            b.sync(stream=st)
+    for b, specs, seqs, outs, items in runs:
+        for i, s in enumerate(specs):
+            alone = me.me_acbm(seqs[i][1], seqs[i][0], 16, 16, s.p, lam, prm)
+            torch.cuda.synchronize()
+            for k, v in (("mv", alone.mv), ("J", alone.J), ("mask", alone.mask), ("load", alone.load)):
+                assert torch.equal(outs[i][k], v), (s.name, k)
+        b.close()
+
