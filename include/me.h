@@ -59,7 +59,8 @@ typedef enum {
 
 /* Text for a status code (static storage). */
 const char *me_status_string(int status);
-/* Text of the last CUDA error seen by this host thread ("" if none). */
+/* Text of the last CUDA error seen by this host thread ("" if none); a server
+ * call that reports its worker thread's error passes that text on. */
 const char *me_last_error(void);
 
 /* ----------------------------------------------------------------- cost */

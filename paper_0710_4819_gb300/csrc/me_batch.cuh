@@ -270,13 +270,16 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
     for (;;) {
       if (tid == 0) {
         const int slot = atomicAdd(&ctrl->fs_head, 1);
-        const volatile int* rd = q_ready + slot;
+        // the queue holds at most `total` entries: a slot beyond can never be
+        // filled, so the CTA is done without touching it
+        const volatile int* rd = q_ready + (slot < total ? slot : 0);
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
         const long long t0 = global_ns();
         int got = -1;
         for (;;) {
+          if (slot >= total) break;
           if (*rd == epoch) { got = slot; break; }
           if (*done == total && *tail <= slot) break;     // no more blocks will come
           if (*err != 0) break;

@@ -38,6 +38,10 @@ int check_acbm_params(const me_acbm_params* prm) {
   return ME_OK;
 }
 
+void set_last_error_text(const char* text) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", text ? text : "");
+}
+
 bool aligned4(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0; }
 
 // One pool per device, created on first use, that keeps freed blocks cached

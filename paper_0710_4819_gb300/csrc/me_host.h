@@ -12,6 +12,9 @@ namespace me {
 
 // Records the CUDA error text for me_last_error() and maps it to a status.
 int cuda_status(cudaError_t e);
+// Sets this thread's me_last_error() text (to hand a worker thread's error to
+// the caller that observes it).
+void set_last_error_text(const char* text);
 
 #define ME_CUDA(call)                                   \
   do {                                                  \

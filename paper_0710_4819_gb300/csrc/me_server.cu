@@ -14,6 +14,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -100,6 +101,7 @@ struct me_server {
   std::vector<me::SrvSlot> slots;
   std::multimap<size_t, uint8_t*> pinned_free;  // reusable pinned frame buffers by size
   int fatal = ME_OK;
+  char fatal_text[256] = "";                     // the worker's error text, for callers
 };
 
 namespace me {
@@ -340,7 +342,11 @@ static void worker_main(me_server* sv) {
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaSuccess) complete_step(sv, sl);
       else if (q == cudaErrorNotReady) any_busy = true;
-      else { sv->fatal = cuda_status(q); sl.busy = false; }
+      else {
+        sv->fatal = cuda_status(q);
+        std::snprintf(sv->fatal_text, sizeof(sv->fatal_text), "%s", me_last_error());
+        sl.busy = false;
+      }
     }
     SrvSlot* free_slot = nullptr;
     for (SrvSlot& sl : sv->slots)
@@ -351,7 +357,10 @@ static void worker_main(me_server* sv) {
         if (!kv.second->inflight && !kv.second->queue.empty()) ready.push_back(kv.second);
     if (free_slot && !ready.empty() && sv->fatal == ME_OK) {
       const int st = launch_step(sv, *free_slot, ready);
-      if (st) sv->fatal = st;
+      if (st) {
+        sv->fatal = st;
+        std::snprintf(sv->fatal_text, sizeof(sv->fatal_text), "%s", me_last_error());
+      }
       continue;
     }
     if (any_busy) sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
@@ -432,7 +441,10 @@ int me_server_submit(me_server* sv, int stream_id, const uint8_t* frame, long lo
   size_t bytes = 0;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (sv->fatal) return sv->fatal;
+    if (sv->fatal) {
+      set_last_error_text(sv->fatal_text);
+      return sv->fatal;
+    }
     auto it = sv->streams.find(stream_id);
     if (it == sv->streams.end() || it->second->closing) return ME_ERR_NOTFOUND;
     bytes = (size_t)it->second->W * it->second->H;
@@ -496,7 +508,10 @@ int me_server_poll(me_server* sv, long long request_id, me_server_result* res) {
   std::lock_guard<std::mutex> lk(sv->mu);
   auto it = sv->reqs.find(request_id);
   if (it == sv->reqs.end()) return ME_ERR_NOTFOUND;
-  if (!it->second->done) return sv->fatal ? sv->fatal : ME_ERR_BUSY;
+  if (!it->second->done) {
+    if (sv->fatal) set_last_error_text(sv->fatal_text);
+    return sv->fatal ? sv->fatal : ME_ERR_BUSY;
+  }
   return take_result(sv, it->second, res);
 }
 
@@ -508,7 +523,10 @@ int me_server_wait(me_server* sv, long long request_id, int timeout_ms, me_serve
   SrvRequest* r = it->second;
   const bool ok = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
                                        [&] { return r->done || sv->fatal != ME_OK; });
-  if (!r->done) return ok ? sv->fatal : ME_ERR_BUSY;
+  if (!r->done) {
+    if (sv->fatal) set_last_error_text(sv->fatal_text);
+    return ok ? sv->fatal : ME_ERR_BUSY;
+  }
   return take_result(sv, r, res);
 }
 
