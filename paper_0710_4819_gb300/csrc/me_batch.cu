@@ -70,6 +70,8 @@ static std::vector<GridKey> g_grids;
 static int persistent_grid(const void* fn, size_t smem, int* grid) {
   int dev = 0;
   ME_CUDA(cudaGetDevice(&dev));
+  int st = ensure_dynamic_smem(fn, smem);   // every launch path raises, never lowers
+  if (st) return st;
   std::lock_guard<std::mutex> lk(g_grid_mu);
   for (const GridKey& k : g_grids)
     if (k.fn == fn && k.smem == smem && k.dev == dev) {
@@ -78,7 +80,6 @@ static int persistent_grid(const void* fn, size_t smem, int* grid) {
     }
   int nsm = 0, per_sm = 0;
   ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  ME_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem));
   *grid = std::max(1, per_sm) * nsm;
   g_grids.push_back(GridKey{fn, smem, dev, *grid});

@@ -358,7 +358,10 @@ template <int N, int M, int T>
 static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, int p, uint32_t lam,
                          int16_t* mv, uint32_t* J, uint32_t* sad, const FsPlan& pl, cudaStream_t s) {
   auto kern = k_fsbm<N, M, T>;
-  ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  {
+    const int st = ensure_dynamic_smem((const void*)kern, pl.smem);
+    if (st) return st;
+  }
   const int BW = W / N, BH = H / M;
   const int bpc = pl.threads / pl.G;
   const int grid = ((BW + bpc - 1) / bpc) * BH;
@@ -372,7 +375,10 @@ static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* 
                             const int* list, int grid, unsigned long long* bkeys, int* bdone,
                             const FsPlan& pl, cudaStream_t s) {
   auto kern = k_fs_list<N, M, T>;
-  ME_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  {
+    const int st = ensure_dynamic_smem((const void*)kern, pl.smem);
+    if (st) return st;
+  }
   kern<<<grid * pl.S, pl.threads, pl.smem, s>>>(ap, W, H, p, pl.S, cnt, list, bkeys, bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
@@ -452,9 +458,10 @@ static int launch_pbm_wave_t(const AcbmArgs* ap, const uint8_t* refpad, const Pa
                              const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
                              int* cnt, int* list, cudaStream_t s) {
   const size_t smem = 4 * 4 * (size_t)pbm_win_words(N, M, p);
-  if (smem > 48 * 1024)
-    ME_CUDA(cudaFuncSetAttribute(k_pbm_wave<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  {
+    const int st = ensure_dynamic_smem((const void*)k_pbm_wave<N, M>, smem);
+    if (st) return st;
+  }
   k_pbm_wave<N, M><<<(count + 3) / 4, 128, smem, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo,
                                                       count, cnt, list);
   ME_CUDA(cudaGetLastError());

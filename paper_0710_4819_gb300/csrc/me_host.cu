@@ -42,6 +42,32 @@ void set_last_error_text(const char* text) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s", text ? text : "");
 }
 
+static std::mutex g_smem_mu;
+struct SmemAttr {
+  const void* fn;
+  int dev;
+  size_t bytes;
+};
+static std::vector<SmemAttr> g_smem;
+
+int ensure_dynamic_smem(const void* kernel, size_t bytes) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  for (SmemAttr& a : g_smem)
+    if (a.fn == kernel && a.dev == dev) {
+      if (bytes > a.bytes) {
+        ME_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        a.bytes = bytes;
+      }
+      return ME_OK;
+    }
+  if (bytes > 48 * 1024)
+    ME_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  g_smem.push_back(SmemAttr{kernel, dev, bytes > 48 * 1024 ? bytes : 48 * 1024});
+  return ME_OK;
+}
+
 bool aligned4(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0; }
 
 // One pool per device, created on first use, that keeps freed blocks cached

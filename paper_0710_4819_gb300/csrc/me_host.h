@@ -22,6 +22,11 @@ void set_last_error_text(const char* text);
     if (e_ != cudaSuccess) return ::me::cuda_status(e_); \
   } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device; the limit only ever grows, so concurrent callers asking for
+// different sizes never lower it under one another's launch.
+int ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 // Frame/shape validation shared by the frame calls (see me.h conventions).
 int check_frame_args(int W, int H, int N, int M, int p, uint32_t lambda_q8);
 int check_acbm_params(const me_acbm_params* prm);

@@ -409,8 +409,8 @@ static int build_seq_plan(SeqPlan* pl) {
 #define X(n_, m_, t_)                                                                          \
   if (N == n_ && M == m_ && pl->T == t_) {                                                     \
     pl->smem = seq_smem<n_, m_, t_>(pl->p);                                                    \
-    ME_CUDA(cudaFuncSetAttribute(k_acbm_seq<n_, m_, t_>,                                       \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem)); \
+    { const int e_ = ensure_dynamic_smem((const void*)k_acbm_seq<n_, m_, t_>, pl->smem);        \
+      if (e_) return e_; }                                                                     \
     ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<n_, m_, t_>,     \
                                                           kSeqThreads, pl->smem));             \
     st = ME_OK;                                                                                \
@@ -478,8 +478,8 @@ int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   st = ME_ERR_ARG;
 #define X(n_, m_, t_)                                                                          \
   if (N == n_ && M == m_ && pl.T == t_) {                                                      \
-    ME_CUDA(cudaFuncSetAttribute(k_fsbm_seq<n_, m_, t_>,                                       \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));  \
+    { const int e_ = ensure_dynamic_smem((const void*)k_fsbm_seq<n_, m_, t_>, pl.smem);         \
+      if (e_) return e_; }                                                                     \
     k_fsbm_seq<n_, m_, t_><<<grid, pl.threads, pl.smem, s>>>(fr, W, H, p, pl.G, lambda_q8,     \
                                                             mv_out, J_out, sad_out);           \
     st = ME_OK;                                                                                \
