@@ -263,6 +263,9 @@ int me_server_close_stream(me_server *s, int stream_id);
 /* Budget in use, open streams and pending requests; returns the server's
  * status (ME_OK unless a CUDA error stopped it). */
 int me_server_stats(me_server *s, long long *used_bytes, int *open_streams, int *pending);
+/* Text describing the last step whose bounded device wait gave up (its
+ * control block: claimed blocks, queue head and tail), "" if none. */
+const char *me_server_diagnostics(me_server *s);
 void me_server_destroy(me_server *s);
 
 /* The same ACBM as me_acbm, for callers that cannot allocate device memory:

@@ -121,6 +121,7 @@ def load_library(build_if_missing: bool = True):
             "me_server_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_int)], c_int),
             "me_server_destroy": ([vp], None),
+            "me_server_diagnostics": ([vp], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name, None)
@@ -433,6 +434,9 @@ class Server:
         st = self._lib.me_server_wait(self._h, request_id, int(timeout_ms), ctypes.byref(res))
         _check(st, "me_server_wait")
         return bool(res.has_result), res.latency_ms, out
+
+    def diagnostics(self) -> str:
+        return self._lib.me_server_diagnostics(self._h).decode()
 
     def close_stream(self, stream_id: int):
         _check(self._lib.me_server_close_stream(self._h, stream_id), "me_server_close_stream")

@@ -95,13 +95,13 @@ struct me_server {
   size_t used = 0;
   int next_stream = 0;
   long long next_req = 1;
-  int epoch = 0;
   std::map<int, me::SrvStream*> streams;
   std::unordered_map<long long, me::SrvRequest*> reqs;
   std::vector<me::SrvSlot> slots;
   std::multimap<size_t, uint8_t*> pinned_free;  // reusable pinned frame buffers by size
   int fatal = ME_OK;
   char fatal_text[256] = "";                     // the worker's error text, for callers
+  char diag[256] = "";                           // control block of the last step that timed out
 };
 
 namespace me {
@@ -160,10 +160,16 @@ static int slot_reserve(SrvSlot& sl, size_t bytes) {
     sl.d_tab = sl.h_tab = nullptr;
   }
   ME_CUDA(cudaMalloc(&sl.d_tab, nb));
+  // a fresh buffer may hold an earlier owner's queue flags: clear it
+  ME_CUDA(cudaMemsetAsync(sl.d_tab, 0, nb, sl.cs));
   ME_CUDA(cudaMallocHost(&sl.h_tab, nb));
   sl.tab_bytes = nb;
   return ME_OK;
 }
+
+// Step epochs are unique within the process, so ready flags and queue flags
+// left in reused memory by another server can never match a current step.
+static std::atomic<int> g_epoch{0};
 
 // Launches one step on slot `sl` with the head request of every ready stream.
 // Called with sv->mu held.
@@ -254,7 +260,7 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     if (acbm) std::memcpy(h + o_tab, segs.data(), tab);
     else std::memcpy(h + o_tab, ent.data(), tab);
     ME_CUDA(cudaMemcpyAsync(d, h, o_tab + tab, cudaMemcpyHostToDevice, sl.cs));
-    const int epoch = ++sv->epoch;
+    const int epoch = ++g_epoch;
     if (acbm)
       st = launch_acbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
                             reinterpret_cast<BStream*>(d + o_st), ns, total_pad, total_blocks,
@@ -291,6 +297,14 @@ static void complete_step(me_server* sv, SrvSlot& sl) {
   const bool acbm = sv->cfg.mode == ME_MODE_ACBM;
   const int err = sl.h_ctrl->error;
   const double t = now_ms();
+  if (err) {
+    const BCtrl& c = *sl.h_ctrl;
+    std::snprintf(sv->diag, sizeof(sv->diag),
+                  "step epoch %d: error %d at item %d; next %d, pbm_done %d, queue head %d tail %d; "
+                  "%d requests in the step",
+                  c.epoch, c.error, c.err_item, c.next, c.pbm_done, c.fs_head, c.fs_tail,
+                  (int)sl.work.size());
+  }
   for (auto& wr : sl.work) {
     SrvStream* s = sv->streams[wr.first];
     SrvRequest* r = wr.second;
@@ -556,6 +570,14 @@ int me_server_stats(me_server* sv, long long* used_bytes, int* open_streams, int
     *pending = n;
   }
   return sv->fatal;
+}
+
+const char* me_server_diagnostics(me_server* sv) {
+  if (!sv) return "";
+  std::lock_guard<std::mutex> lk(sv->mu);
+  static thread_local char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s", sv->diag);
+  return buf;
 }
 
 void me_server_destroy(me_server* sv) {
