@@ -143,7 +143,8 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
     if (st == ME_OK && grid < 2 * nsm) st = ME_ERR_CUDA;  /* needs two CTAs per SM */         \
     if (st == ME_OK)                                                                           \
       k_acbm_persist<n_, m_, t_><<<2 * nsm, kBatchThreads, smem, s>>>(                         \
-          shapes, streams, segs, nseg, total_items, ctrl, q_item, q_ready, pw, ww, nsm);       \
+          shapes, streams, segs, nseg, total_items, ctrl, q_item, q_ready, pw, ww, nsm,        \
+          nstreams);                                                                           \
   }
   ME_BATCH_NMT(X)
 #undef X

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
                                                          int total, BCtrl* ctrl,
                                                          unsigned long long* __restrict__ q_item,
                                                          int* __restrict__ q_ready, int pbm_warps,
-                                                         int win_words, int nsm) {
+                                                         int win_words, int nsm, int nstreams) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_slot, s_role;
@@ -298,6 +298,12 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       __syncthreads();
       if (s_slot < 0) break;
       const int si = (int)(s_item >> 32), b = (int)(s_item & 0xffffffffu);
+      if (si < 0 || si >= nstreams || b < 0 || b >= (shp[si].W / N) * (shp[si].H / M)) {
+        // not a block of this step: report it instead of touching memory
+        if (tid == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
+        __syncthreads();
+        continue;
+      }
       const BShape& s = shp[si];
       const BStream& a = st[si];
       const int BW = s.W / N;

@@ -291,6 +291,12 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       __syncthreads();
       if (s_slot < 0) break;
       const int o = s_item;
+      if (o < 0 || o >= total) {
+        // not a block of this run: report it instead of touching memory
+        if (tid == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
+        __syncthreads();
+        continue;
+      }
       const int k = o / nbf, b = o - k * nbf;
       const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
       fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);

@@ -260,6 +260,8 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     if (acbm) std::memcpy(h + o_tab, segs.data(), tab);
     else std::memcpy(h + o_tab, ent.data(), tab);
     ME_CUDA(cudaMemcpyAsync(d, h, o_tab + tab, cudaMemcpyHostToDevice, sl.cs));
+    // the queue sits where earlier steps kept their tables: clear its flags
+    if (acbm) ME_CUDA(cudaMemsetAsync(d + o_qr, 0, 4 * (size_t)std::max(1, total_items), sl.cs));
     const int epoch = ++g_epoch;
     if (acbm)
       st = launch_acbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
