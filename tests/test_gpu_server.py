@@ -117,3 +117,44 @@ def test_server_admits_work_while_busy(me):
     used, n, pending = srv.stats()
     assert pending == 0 and n == 6
     srv.close()
+
+
+def test_server_random_arrivals_mixed_sizes(me):
+    """Many steps of changing composition (random arrival order, uneven frame
+    sizes and search ranges, two steps in flight): every stream's results
+    equal its frames run through chained me_acbm calls."""
+    import torch
+    rng = np.random.default_rng(5)
+    kinds = [("qcif", 176, 144, 16), ("cif", 352, 288, 16), ("cif", 352, 288, 24),
+             ("720p", 1280, 720, 32)]
+    specs = [synth.StreamSpec(k[0], k[1], k[2], k[3], 8301 + i) for i, k in
+             enumerate([kinds[j] for j in rng.integers(0, len(kinds), size=10)])]
+    n = 5
+    seqs = [synth.stream_frames(s, n) for s in specs]
+    srv = me.Server(8 << 30, max_inflight=2, mode=1)
+    ids = [srv.open_stream(s.w, s.height, s.p, qp=28) for s in specs]
+    order = [i for i in range(len(specs)) for _ in range(n)]
+    rng.shuffle(order)
+    nxt = [0] * len(specs)
+    reqs = []
+    for i in order:
+        reqs.append((i, nxt[i], srv.submit(ids[i], seqs[i][nxt[i]])))
+        nxt[i] += 1
+    got = {}
+    for i, t, r in reqs:
+        has, lat, res = srv.wait(r, ids[i], timeout_ms=60000)
+        if has:
+            got[(i, t)] = res
+    srv.close()
+    lam = me.me_lambda_q8(28)
+    for i, s in enumerate(specs):
+        frames = torch.from_numpy(seqs[i]).cuda()
+        prev = None
+        for t in range(1, n):
+            a = me.me_acbm(frames[t], frames[t - 1], 16, 16, s.p, lam, me.params(qp=28), prev_mv=prev)
+            torch.cuda.synchronize()
+            prev = a.mv
+            assert np.array_equal(got[(i, t)]["mv"], a.mv.cpu().numpy()), (i, t)
+            assert np.array_equal(got[(i, t)]["mask"], a.mask.cpu().numpy()), (i, t)
+            assert np.array_equal(got[(i, t)]["J"], a.J.cpu().numpy().view(np.uint32)), (i, t)
+
