@@ -42,8 +42,8 @@ struct me_batch {
   me::BSegment* d_segs = nullptr;
   me::BFsEntry* d_fsent = nullptr;
   me::BCtrl* d_ctrl = nullptr;
-  unsigned long long* d_qitem = nullptr;   // full-search queue of the ACBM step
-  int* d_qready = nullptr;
+  unsigned long long* d_items = nullptr;   // claim order of the ACBM step
+  unsigned long long* d_q = nullptr;       // full-search queue of the ACBM step
   int p_max = 1;
   static constexpr int kRing = 4;       // staging buffers in flight
   me::BStream* h_streams = nullptr;     // pinned staging of the per-run arguments [kRing][n]
@@ -112,9 +112,14 @@ size_t acbm_step_smem(int N, int M, int T, int p_max) {
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
-                     unsigned long long* q_item, int* q_ready, cudaStream_t s) {
+                     unsigned long long* items, unsigned long long* q, cudaStream_t s) {
   k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
+  if (total_items > 0) {
+    const int gt = std::max(1, std::min((total_items + 255) / 256, 152 * 8));
+    k_batch_items<<<gt, 256, 0, s>>>(segs, nseg, total_items, shapes, N, items);
+    ME_CUDA(cudaGetLastError());
+  }
   const int gp = (int)std::max<long long>(1, std::min<long long>((total_pad + 255) / 256, 152 * 16));
   k_batch_pad<<<gp, 256, 0, s>>>(shapes, streams, nstreams, total_pad);
   ME_CUDA(cudaGetLastError());
@@ -143,8 +148,7 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
     if (st == ME_OK && grid < 2 * nsm) st = ME_ERR_CUDA;  /* needs two CTAs per SM */         \
     if (st == ME_OK)                                                                           \
       k_acbm_persist<n_, m_, t_><<<2 * nsm, kBatchThreads, smem, s>>>(                         \
-          shapes, streams, segs, nseg, total_items, ctrl, q_item, q_ready, pw, ww, nsm,        \
-          nstreams);                                                                           \
+          shapes, streams, items, total_items, ctrl, q, pw, ww, nsm, nstreams);                \
   }
   ME_BATCH_NMT(X)
 #undef X
@@ -224,8 +228,8 @@ static int batch_finalize(me_batch* b) {
   const size_t o_streams = take(sizeof(BStream) * n);
   const size_t o_segs = take(sizeof(BSegment) * b->segs.size());
   const size_t o_fsent = take(sizeof(BFsEntry) * b->fsent.size());
-  const size_t o_qitem = take(8 * (size_t)std::max(1, b->total_items));
-  const size_t o_qready = take(4 * (size_t)std::max(1, b->total_items));
+  const size_t o_items = take(8 * (size_t)std::max(1, b->total_items));
+  const size_t o_q = take(8 * (size_t)std::max(1, b->total_items));
   std::vector<size_t> o_pad(n), o_intra(n), o_flags(n);
   b->total_pad = 0;
   b->total_blocks = 0;
@@ -234,7 +238,7 @@ static int batch_finalize(me_batch* b) {
     const int nb = (s.W / b->N) * (s.H / b->M);
     o_pad[i] = take((size_t)s.pg.pitch * s.pg.rows);
     o_intra[i] = take(4 * (size_t)nb);
-    o_flags[i] = take(4 * (size_t)nb);
+    o_flags[i] = take(8 * (size_t)nb);
     s.pad_base = b->total_pad;
     s.blk_base = b->total_blocks;
     b->total_pad += (long long)s.pg.rows * (s.pg.pitch / 16);
@@ -246,15 +250,15 @@ static int batch_finalize(me_batch* b) {
   for (size_t i = 0; i < n; i++) {
     b->shapes[i].refpad = base8 + o_pad[i];
     b->shapes[i].intra = reinterpret_cast<uint32_t*>(base8 + o_intra[i]);
-    b->shapes[i].flags = reinterpret_cast<int*>(base8 + o_flags[i]);
+    b->shapes[i].flags = reinterpret_cast<unsigned long long*>(base8 + o_flags[i]);
   }
   b->d_ctrl = reinterpret_cast<BCtrl*>(base8 + o_ctrl);
   b->d_shapes = reinterpret_cast<BShape*>(base8 + o_shapes);
   b->d_streams = reinterpret_cast<BStream*>(base8 + o_streams);
   b->d_segs = reinterpret_cast<BSegment*>(base8 + o_segs);
   b->d_fsent = reinterpret_cast<BFsEntry*>(base8 + o_fsent);
-  b->d_qitem = reinterpret_cast<unsigned long long*>(base8 + o_qitem);
-  b->d_qready = reinterpret_cast<int*>(base8 + o_qready);
+  b->d_items = reinterpret_cast<unsigned long long*>(base8 + o_items);
+  b->d_q = reinterpret_cast<unsigned long long*>(base8 + o_q);
   ME_CUDA(cudaMemcpy(b->d_shapes, b->shapes.data(), sizeof(BShape) * n, cudaMemcpyHostToDevice));
   if (!b->segs.empty())
     ME_CUDA(cudaMemcpy(b->d_segs, b->segs.data(), sizeof(BSegment) * b->segs.size(),
@@ -296,7 +300,7 @@ static int batch_enqueue(me_batch* b, int mode, cudaStream_t s) {
   return launch_acbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams,
                           (int)b->shapes.size(), b->total_pad, b->total_blocks, b->d_segs,
                           (int)b->segs.size(), b->total_items, b->smem_acbm, b->p_max,
-                          b->d_qitem, b->d_qready, s);
+                          b->d_items, b->d_q, s);
 }
 
 }  // namespace me

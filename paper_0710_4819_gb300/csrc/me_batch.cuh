@@ -32,7 +32,7 @@ struct BShape {  // fixed per stream
   PadGeom pg;
   uint8_t* refpad;
   uint32_t* intra;
-  int* flags;
+  unsigned long long* flags;  // per block: epoch + final vector (pub_word)
   long long pad_base;  // first 16-byte chunk of this stream in the flat pad index
   int blk_base;        // first block of this stream in the flat block index
 };
@@ -147,20 +147,45 @@ __global__ void __launch_bounds__(256, 2) k_fsbm_persist(const BShape* __restric
   }
 }
 
-// Bounded wait until *f == want (gives up after the timeout, or at once after
-// any other wait has given up, and then reports ME_ERR_TIMEOUT).
-static __device__ __forceinline__ void batch_wait(const int* f, int want, BCtrl* ctrl,
-                                                  long long timeout, int item) {
-  const volatile int* vf = f;
+// Bounded wait until the flag word carries epoch `want` (gives up after the
+// timeout, or at once after any other wait has given up, and then reports
+// ME_ERR_TIMEOUT); returns the word, whose low half is the block's vector.
+static __device__ __forceinline__ unsigned long long batch_wait(const unsigned long long* f, int want,
+                                                                BCtrl* ctrl, long long timeout,
+                                                                int item) {
+  const volatile unsigned long long* vf = f;
   const volatile int* err = &ctrl->error;
+  unsigned long long w = *vf;
+  if (pub_epoch(w) == want) return w;
   const long long t0 = global_ns();
-  while (*vf != want && *err == 0) {
+  while (*err == 0) {
+    __nanosleep(32);
+    w = *vf;
+    if (pub_epoch(w) == want) break;
     if (global_ns() - t0 > timeout) {
       atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
       atomicExch(&ctrl->err_item, item);
       break;
     }
-    __nanosleep(32);
+  }
+  return w;
+}
+
+// Claim order of an ACBM step as a table: item i -> (stream << 32) | block,
+// expanded from the wave segments by one thread per item.
+static __global__ void k_batch_items(const BSegment* __restrict__ seg, int nseg, int total,
+                                     const BShape* __restrict__ shp, int N,
+                                     unsigned long long* __restrict__ items) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
+    }
+    const BSegment sg = seg[lo];
+    const int by = sg.ylo + (i - sg.item_base);
+    const int b = by * (shp[sg.stream].W / N) + (sg.wave - 2 * by);
+    items[i] = ((unsigned long long)(uint32_t)sg.stream << 32) | (uint32_t)b;
   }
 }
 
@@ -171,27 +196,31 @@ __host__ __device__ inline int batch_pbm_warps(int N, int M, int p) {
   return w < 1 ? 1 : (w > kBatchThreads / 32 ? kBatchThreads / 32 : w);
 }
 
-// ACBM step over many streams, two roles in one launch.  The first half of the
-// CTAs run PBM: every warp claims blocks on its own, in wave order across
-// streams, waits for the block's left / up-left / up / up-right neighbours,
-// runs PBM and the two conditions, and publishes the block or appends it to
-// the full-search queue.  The second half take queued blocks in order and
-// search each with the whole CTA.  PBM warps only wait for blocks claimed
-// before their own, search CTAs only for queue entries a running PBM warp
-// will write (or the end of the step): every wait ends, and each is also
-// bounded in time.
+// ACBM step over many streams, two roles in one launch.  PBM CTAs: every warp
+// claims blocks on its own, in wave order across streams (the item table maps
+// a claim to its stream and block), queues the block's current pixels and
+// search window as asynchronous copies, waits for the block's left / up-left /
+// up / up-right neighbours (whose flag words carry their final vectors), runs
+// PBM and the two conditions, and publishes the block or appends its claim to
+// the full-search queue.  A warp claims its next block before working on the
+// current one.  Search CTAs take queued blocks in order and search each with
+// the whole CTA.  The smallest unfinished block is always some warp's current
+// block with all its predecessors finished, and search CTAs only wait for
+// queue entries a running PBM warp will write (or the end of the step): every
+// wait ends, and each is also bounded in time.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restrict__ shp,
                                                          const BStream* __restrict__ st,
-                                                         const BSegment* __restrict__ seg, int nseg,
+                                                         const unsigned long long* __restrict__ items,
                                                          int total, BCtrl* ctrl,
-                                                         unsigned long long* __restrict__ q_item,
-                                                         int* __restrict__ q_ready, int pbm_warps,
-                                                         int win_words, int nsm, int nstreams) {
+                                                         unsigned long long* __restrict__ q,
+                                                         int pbm_warps, int win_words, int nsm,
+                                                         int nstreams) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_slot, s_role;
+  __shared__ int s_role;
   __shared__ unsigned long long s_item;
+  const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
@@ -209,58 +238,74 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
     if (warp >= pbm_warps) return;
     uint32_t* win = smem + warp * (win_words + M * (N / 4));
     uint32_t* curs = win + win_words;
+    // lane 0 holds the next claim (item index and its stream/block)
+    int nxt = 0;
+    unsigned long long inxt = 0;
+    if (lane == 0) {
+      nxt = atomicAdd(&ctrl->next, 1);
+      if (nxt < total) inxt = items[nxt];
+    }
     for (;;) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&ctrl->next, 1);
-      i = __shfl_sync(0xffffffffu, i, 0);
+      const int i = __shfl_sync(FULL, nxt, 0);
       if (i >= total) break;
-      int si = 0, b = 0;
-      if (lane == 0) {
-        int lo = 0, hi = nseg - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
-        }
-        const BSegment sg = seg[lo];
-        const int by = sg.ylo + (i - sg.item_base);
-        si = sg.stream;
-        b = by * (shp[sg.stream].W / N) + (sg.wave - 2 * by);
-      }
-      si = __shfl_sync(0xffffffffu, si, 0);
-      b = __shfl_sync(0xffffffffu, b, 0);
+      const unsigned long long it = __shfl_sync(FULL, inxt, 0);
+      const int si = (int)(it >> 32), b = (int)(uint32_t)it;
       const BShape& s = shp[si];
       const BStream& a = st[si];
-      const int BW = s.W / N;
+      const int BW = s.W / N, BH = s.H / M;
       const int bx = b % BW, by = b / BW;
+      const PbmWin wg = pbm_stage<N, M>(a.cur, s.refpad, s.pg, s.W, s.p, bx * N, by * M, curs, win);
+      const uint32_t ix = s.intra[b];
+      if (lane == 0) nxt = atomicAdd(&ctrl->next, 1);
+      // predictors: lanes 0-3 the spatial ones (final vectors of this step,
+      // carried by their flags), lanes 4-12 the previous field's 3x3, lane 13
+      // the zero vector
+      int cx = 0, cy = 0;
+      bool valid = false;
       if (lane < 4) {
         const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
         const int dy = (lane == 0) ? 0 : -1;
         const int nx = bx + dx, ny = by + dy;
-        if (nx >= 0 && nx < BW && ny >= 0) batch_wait(s.flags + ny * BW + nx, epoch, ctrl, timeout, i);
+        if (nx >= 0 && nx < BW && ny >= 0) {
+          const unsigned long long w = batch_wait(s.flags + ny * BW + nx, epoch, ctrl, timeout, i);
+          cx = pub_mvx(w);
+          cy = pub_mvy(w);
+          valid = true;
+        }
+      } else if (lane < 13) {
+        const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
+        if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+          if (a.prev) {
+            cx = a.prev[2 * (ny * BW + nx)];
+            cy = a.prev[2 * (ny * BW + nx) + 1];
+          }
+          valid = true;
+        }
+      } else if (lane == 13) {
+        valid = true;
       }
-      __syncwarp();
-      __threadfence();
-      const PbmResult r = warp_pbm<N, M>(a.cur, s.refpad, s.pg, s.W, s.H, s.p, a.lam, a.mv, a.prev,
-                                         bx, by, s.intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp,
-                                         a.refine, curs, win);
+      if (lane == 0 && nxt < total) inxt = items[nxt];
+      const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, s.p, a.lam, ix, a.alpha, a.beta, a.gnum,
+                                         a.gden, a.qp, a.refine, curs, win);
       if (lane == 0) {
         if (r.pass) {
+          // the flag word carries the vector: publish first, outputs after
           const Decoded d = decode_key(r.key, s.p, a.lam);
+          if (!(si == ctrl->skip_stream && b == ctrl->skip_block))
+            atomicExch(s.flags + b, pub_word(epoch, d.mvx, d.mvy));
           a.mv[2 * b] = (int16_t)d.mvx;
           a.mv[2 * b + 1] = (int16_t)d.mvy;
           a.J[b] = d.J;
           a.mask[b] = 0;
           if (a.sad) a.sad[b] = d.sad;
           if (a.load) a.load[b] = (uint32_t)r.load;
-          __threadfence();
-          if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
         } else {
+          // queue entry = epoch and claim index in one word; the tail count is
+          // ordered before this warp's pbm_done increment
           const int slot = atomicAdd(&ctrl->fs_tail, 1);
-          q_item[slot] = ((unsigned long long)si << 32) | (unsigned)b;
+          atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)i);
           __threadfence();
-          atomicExch(q_ready + slot, epoch);
         }
-        __threadfence();
         atomicAdd(&ctrl->pbm_done, 1);
       }
       __syncwarp();
@@ -272,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         const int slot = atomicAdd(&ctrl->fs_head, 1);
         // the queue holds at most `total` entries: a slot beyond can never be
         // filled, so the CTA is done without touching it
-        const volatile int* rd = q_ready + (slot < total ? slot : 0);
+        const volatile unsigned long long* rd = q + (slot < total ? slot : 0);
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
@@ -280,25 +325,25 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         int got = -1;
         for (;;) {
           if (slot >= total) break;
-          if (*rd == epoch) { got = slot; break; }
+          const unsigned long long e = *rd;
+          if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
           if (*done == total && *tail <= slot) break;     // no more blocks will come
           if (*err != 0) break;
           if (global_ns() - t0 > timeout) {
             atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
             break;
           }
-          __nanosleep(64);
+          __nanosleep(32);
         }
-        if (got >= 0) {
-          __threadfence();
-          s_item = *reinterpret_cast<volatile unsigned long long*>(q_item + slot);
-        }
-        s_slot = got;
+        // a claim index beyond the table is not an item of this step
+        s_item = got < 0 ? ~0ull : (got < total ? items[got] : ~1ull);
       }
       __syncthreads();
-      if (s_slot < 0) break;
-      const int si = (int)(s_item >> 32), b = (int)(s_item & 0xffffffffu);
-      if (si < 0 || si >= nstreams || b < 0 || b >= (shp[si].W / N) * (shp[si].H / M)) {
+      const unsigned long long it = s_item;
+      if (it == ~0ull) break;
+      const int si = (int)(it >> 32), b = (int)(uint32_t)it;
+      if (it == ~1ull || si < 0 || si >= nstreams || b < 0 ||
+          b >= (shp[si].W / N) * (shp[si].H / M)) {
         // not a block of this step: report it instead of touching memory
         if (tid == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
         __syncthreads();
@@ -311,14 +356,14 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
       if (tid == 0) {
         const Decoded d = decode_key(keys[0], s.p, a.lam);
+        if (!(si == ctrl->skip_stream && b == ctrl->skip_block))
+          atomicExch(s.flags + b, pub_word(epoch, d.mvx, d.mvy));
         a.mv[2 * b] = (int16_t)d.mvx;
         a.mv[2 * b + 1] = (int16_t)d.mvy;
         a.J[b] = d.J;
         a.mask[b] = 1;
         if (a.sad) a.sad[b] = d.sad;
         if (a.load) a.load[b] = (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
-        __threadfence();
-        if (!(si == ctrl->skip_stream && b == ctrl->skip_block)) atomicExch(s.flags + b, epoch);
       }
       __syncthreads();
     }
@@ -352,13 +397,14 @@ int batch_choose_T(int N, int M, const std::vector<BShape>& shapes);
 
 // Enqueues one ACBM step over the streams in the device tables: the begin
 // kernel (epoch = `epoch`, or the previous epoch + 1 when epoch <= 0), the
-// padding and Intra_SAD prologue, and the persistent kernel.  q_item and
-// q_ready hold at least total_items entries; smem and the PBM warp count
-// come from acbm_step_smem for the largest search range p_max.
+// item table, the padding and Intra_SAD prologue, and the persistent kernel.
+// items and q hold at least total_items entries (q: no entry may carry the
+// step's epoch before the step); smem and the PBM warp count come from
+// acbm_step_smem for the largest search range p_max.
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
-                     unsigned long long* q_item, int* q_ready, cudaStream_t s);
+                     unsigned long long* items, unsigned long long* q, cudaStream_t s);
 
 // Dynamic shared memory of the ACBM step kernel for search ranges up to p_max.
 size_t acbm_step_smem(int N, int M, int T, int p_max);

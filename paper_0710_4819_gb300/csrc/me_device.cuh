@@ -102,6 +102,7 @@ struct FsGeom {
   int G;             // threads per block
   int rows;          // staged window rows: nseg*T + M - 1
   int pos;           // shifted-word positions per row
+  int sp;            // shifted-word row pitch in words (>= pos)
   int wbw;           // 32-bit words per staged raw row
   int tasks;         // tasks per block: n * nseg
 };
@@ -125,8 +126,11 @@ __host__ __device__ inline bool fast32_ok(int N, int M, int p, uint32_t lam) {
 
 // Geometry of a search over columns c0 .. c0+nc-1 of the (2p+1)-wide window
 // (nc = 0: all columns); a slice lets several CTAs share one block's search.
+// sp_min > 0 widens the shifted-word rows to a fixed pitch (a kernel compiled
+// for that pitch addresses every row with immediate offsets).
 template <int N, int M, int T>
-__host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int nc = 0) {
+__host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int nc = 0,
+                                          int sp_min = 0) {
   FsGeom g;
   g.p = p;
   g.rb = 0;
@@ -141,6 +145,7 @@ __host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int
   g.pos = (bpc - 1) * N + g.nc + N - 4;
   // raw row: up to 3 bytes of alignment slack, pos+3 bytes, one spare word
   g.wbw = (g.pos + 6) / 4 + 1;
+  g.sp = g.pos > sp_min ? g.pos : sp_min;
   g.tasks = g.nc * g.nseg;
   return g;
 }
@@ -150,7 +155,7 @@ template <int N, int M, int T>
 __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
   size_t words = (size_t)g.bpc * M * (N / 4)        // current blocks
                + (size_t)g.rows * g.wbw             // raw window
-               + (size_t)g.rows * g.pos             // shifted words
+               + (size_t)g.rows * g.sp              // shifted words
                + (size_t)g.rows * 3;                // per-row rate/key tables
   return words * 4 + 16 * 8 + 8;                    // per-block minima (+ alignment)
 }
@@ -158,8 +163,9 @@ __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
 // Full search of g.bpc adjacent blocks whose first block has top-left pixel
 // (x0, y0).  The per-block winning keys go to keys_out[0..bpc) (shared
 // memory, visible to all threads on return).  Every thread of the CTA calls
-// it; threads beyond bpc*G only help with staging.
-template <int N, int M, int T>
+// it; threads beyond bpc*G only help with staging.  SP > 0: the geometry's
+// shifted-word pitch is SP (fixed at compile time), else g.sp.
+template <int N, int M, int T, int SP = 0>
 __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
                          int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
                          uint32_t* smem, unsigned long long* keys_out) {
@@ -167,10 +173,11 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   const int p = g.p, n = g.n;
+  const int sp = SP > 0 ? SP : g.sp;
   uint32_t* curw = smem;                                   // [bpc][M][NW]
   uint32_t* wb = curw + g.bpc * M * NW;                    // [rows][wbw]
   uint32_t* sh = wb + g.rows * g.wbw;                      // [rows][pos]
-  uint32_t* tabJ = sh + g.rows * g.pos;                    // [rows] lambda*L(mvy)
+  uint32_t* tabJ = sh + g.rows * sp;                    // [rows] lambda*L(mvy)
   uint32_t* tabK = tabJ + g.rows;                          // [rows] key bits of mvy
   uint32_t* tabQ = tabK + g.rows;                          // [rows] 32-bit run key of mvy
   unsigned long long* red = reinterpret_cast<unsigned long long*>(
@@ -230,7 +237,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   // 3. shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3
   for (int r = warp; r < g.rows; r += nwarps) {
     const uint32_t* row = wb + r * g.wbw;
-    uint32_t* dst = sh + r * g.pos;
+    uint32_t* dst = sh + r * sp;
     for (int o = lane; o < g.pos; o += 32) {
       const int k = s0 + o;
       dst[o] = __funnelshift_r(row[k >> 2], row[(k >> 2) + 1], 8 * (k & 3));
@@ -252,7 +259,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     const int dseg = g.G / nc, dcol = g.G - (g.G / nc) * nc;
     for (int t = l; t < g.tasks; t += g.G) {
       const int row0 = seg * T;
-      const uint32_t* shp = sh + row0 * g.pos + blk * N + col;
+      const uint32_t* shp = sh + row0 * sp + blk * N + col;
       uint32_t acc[T];
 #pragma unroll
       for (int k = 0; k < T; k++) acc[k] = 0;
@@ -260,7 +267,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       for (int r = 0; r < T + M - 1; r++) {
         uint32_t rw[NW];
 #pragma unroll
-        for (int w = 0; w < NW; w++) rw[w] = shp[r * g.pos + 4 * w];
+        for (int w = 0; w < NW; w++) rw[w] = shp[r * sp + 4 * w];
         // word-major order: consecutive SAD steps go to different candidates
 #pragma unroll
         for (int w = 0; w < NW; w++) {

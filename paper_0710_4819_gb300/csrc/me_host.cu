@@ -62,9 +62,16 @@ int ensure_dynamic_smem(const void* kernel, size_t bytes) {
       }
       return ME_OK;
     }
-  if (bytes > 48 * 1024)
+  // the default limit is 48 KB minus the kernel's static shared memory: start
+  // from the kernel's actual limit, not from 48 KB
+  cudaFuncAttributes fa;
+  ME_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  size_t have = (size_t)fa.maxDynamicSharedSizeBytes;
+  if (bytes > have) {
     ME_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  g_smem.push_back(SmemAttr{kernel, dev, bytes > 48 * 1024 ? bytes : 48 * 1024});
+    have = bytes;
+  }
+  g_smem.push_back(SmemAttr{kernel, dev, have});
   return ME_OK;
 }
 

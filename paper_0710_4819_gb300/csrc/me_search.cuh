@@ -135,91 +135,71 @@ struct PbmResult {
   bool pass;               // cond. 1 or cond. 2 holds
 };
 
+// The published state of a block in the persistent kernels: the run's epoch
+// in the high word and the block's final vector in the low word (mvx in bits
+// 0-15, mvy in bits 16-31), so a block waiting for a predecessor receives the
+// predictor with the flag, in the same load.
+__host__ __device__ __forceinline__ unsigned long long pub_word(int epoch, int mvx, int mvy) {
+  return ((unsigned long long)(uint32_t)epoch << 32) |
+         ((unsigned long long)(uint16_t)(int16_t)mvy << 16) | (unsigned long long)(uint16_t)(int16_t)mvx;
+}
+__host__ __device__ __forceinline__ int pub_epoch(unsigned long long w) { return (int)(w >> 32); }
+__host__ __device__ __forceinline__ int pub_mvx(unsigned long long w) { return (int)(int16_t)(uint16_t)(w & 0xffffu); }
+__host__ __device__ __forceinline__ int pub_mvy(unsigned long long w) {
+  return (int)(int16_t)(uint16_t)((w >> 16) & 0xffffu);
+}
+
 // ---------------------------------------------------------------------------
-// a5 + a6 + a9: the PBM stage of ACBM for block (bx, by), done by one warp
-// (Sec. 2.2 steps 1-3 with the predictor set of the current-frame field
-// `field` and the previous field `prev`; then the two conditions of Sec. 3.2).
-// Lanes 0-3 take the spatial predictors (left, up-left, up, up-right), lanes
-// 4-12 the 3x3 temporal ones, lane 13 the zero vector; each lane evaluates its
-// candidate unless a lower lane holds the same clipped position.  The ring
-// (lanes 0-7) skips positions already evaluated.  curs: this warp's staging
-// area for the current block (M*N/4 words of shared memory); win: this warp's
-// window area (pbm_win_words words).
+// PBM of one block by one warp, in two parts so that the memory traffic that
+// does not depend on other blocks can be in flight while the warp waits for
+// its predecessors:
+//
+//   pbm_stage: queue the current block (4-byte copies) and the whole search
+//              window (16-byte copies) as asynchronous global-to-shared copies;
+//   pbm_eval : with the lane's predictor in hand (lanes 0-3 the spatial ones:
+//              left, up-left, up, up-right; lanes 4-12 the 3x3 temporal ones;
+//              lane 13 the zero vector), wait for the copies, evaluate every
+//              distinct clipped predictor (Sec. 2.2 steps 1-2), the +-1 ring
+//              around the best (step 3, skipping positions already evaluated)
+//              and the two conditions of Sec. 3.2 (a5 + a6 + a9).
+//
+// curs: this warp's M*N/4 words for the current block; win: its window area
+// (pbm_win_words words).  Both in shared memory.
 // ---------------------------------------------------------------------------
 template <int N, int M>
-__device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ refpad,
-                              const PadGeom& pg, int W, int H, int p, uint32_t lam,
-                              const int16_t* field, const int16_t* prev,
-                              int bx, int by, uint32_t intra_x, int32_t alpha, int32_t beta,
-                              int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
-                              uint32_t* curs, uint32_t* win) {
+__device__ __forceinline__ PbmWin pbm_stage(const uint8_t* __restrict__ cur,
+                                            const uint8_t* __restrict__ refpad, const PadGeom& pg,
+                                            int W, int p, int x0, int y0, uint32_t* curs,
+                                            uint32_t* win) {
   constexpr int NW = N / 4;
-  constexpr int CW = (M * NW + 31) / 32;   // current-block words per lane
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < M * NW; i += 32) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(curs + i);
+    const void* g = cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(g) : "memory");
+  }
+  const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
+  const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
+  const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
+  const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
+  if (rl < rpp) {
+    for (int r = rl; r < wg.rows; r += rpp) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(win + r * wg.wp + 4 * cl);
+      const void* g = src + (size_t)r * pg.pitch + 16 * cl;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  return wg;
+}
+
+template <int N, int M>
+__device__ PbmResult pbm_eval(int cx, int cy, bool valid, const PbmWin& wg, int p, uint32_t lam,
+                              uint32_t intra_x, int32_t alpha, int32_t beta, int32_t gnum,
+                              int32_t gden, int32_t qp, int32_t refine, const uint32_t* curs,
+                              const uint32_t* win) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int BW = W / N, BH = H / M;
-  const int x0 = bx * N, y0 = by * M;
-
-  // step 1: predictors (their loads are issued first, with the block loads
-  // below, so the warp pays about one global-memory round trip in total)
-  int cx = 0, cy = 0;
-  bool valid = false;
-  if (lane < 4) {
-    const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
-    const int dy = (lane == 0) ? 0 : -1;
-    const int nx = bx + dx, ny = by + dy;
-    if (nx >= 0 && nx < BW && ny >= 0) {
-      // final vectors of earlier waves; volatile so a concurrent writer's
-      // published value is re-read from memory (persistent kernels)
-      const volatile int16_t* f = field + 2 * (ny * BW + nx);
-      cx = f[0];
-      cy = f[1];
-      valid = true;
-    }
-  } else if (lane < 13) {
-    const int t = lane - 4, dx = t % 3 - 1, dy = t / 3 - 1;
-    const int nx = bx + dx, ny = by + dy;
-    if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
-      if (prev) {
-        // volatile: in a sequence run the previous field is written by
-        // other CTAs of the same launch
-        const volatile int16_t* f = prev + 2 * (ny * BW + nx);
-        cx = f[0];
-        cy = f[1];
-      }
-      valid = true;
-    }
-  } else if (lane == 13) {
-    valid = true;
-  }
-  uint32_t cw[CW];
-#pragma unroll
-  for (int k = 0; k < CW; k++) {
-    const int i = lane + 32 * k;
-    if (i < M * NW)
-      cw[k] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW));
-  }
-  // the search window: every lane queues its 16-byte chunks as asynchronous
-  // global-to-shared copies, so the whole window costs one round trip
-  const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
-  {
-    const int rpp = 32 / wg.chunks;          // rows per pass (chunks <= 11 for p <= 64)
-    const int rl = lane / wg.chunks, cl = lane - (lane / wg.chunks) * wg.chunks;
-    const uint8_t* src = refpad + (size_t)(y0 + pg.P - p) * pg.pitch + ((x0 + pg.P - p) & ~15);
-    if (rl < rpp) {
-      for (int r = rl; r < wg.rows; r += rpp) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(win + r * wg.wp + 4 * cl);
-        const void* g = src + (size_t)r * pg.pitch + 16 * cl;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g) : "memory");
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-#pragma unroll
-  for (int k = 0; k < CW; k++) {
-    const int i = lane + 32 * k;
-    if (i < M * NW) curs[i] = cw[k];
-  }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
   cx = clampi(cx, -p, p);
@@ -270,6 +250,47 @@ __device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __
   r.load = load;
   r.pass = c1 || c2;
   return r;
+}
+
+// PBM of block (bx, by) with its predictors read from the current-frame field
+// `field` (final vectors of earlier waves) and the previous field `prev`
+// (nullable: zero vectors): the per-frame path, where a kernel boundary orders
+// every predictor before its reader.
+template <int N, int M>
+__device__ PbmResult warp_pbm(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ refpad,
+                              const PadGeom& pg, int W, int H, int p, uint32_t lam,
+                              const int16_t* field, const int16_t* prev,
+                              int bx, int by, uint32_t intra_x, int32_t alpha, int32_t beta,
+                              int32_t gnum, int32_t gden, int32_t qp, int32_t refine,
+                              uint32_t* curs, uint32_t* win) {
+  const int lane = threadIdx.x & 31;
+  const int BW = W / N, BH = H / M;
+  const PbmWin wg = pbm_stage<N, M>(cur, refpad, pg, W, p, bx * N, by * M, curs, win);
+  int cx = 0, cy = 0;
+  bool valid = false;
+  if (lane < 4) {
+    const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
+    const int dy = (lane == 0) ? 0 : -1;
+    const int nx = bx + dx, ny = by + dy;
+    if (nx >= 0 && nx < BW && ny >= 0) {
+      cx = field[2 * (ny * BW + nx)];
+      cy = field[2 * (ny * BW + nx) + 1];
+      valid = true;
+    }
+  } else if (lane < 13) {
+    const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
+    if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+      if (prev) {
+        cx = prev[2 * (ny * BW + nx)];
+        cy = prev[2 * (ny * BW + nx) + 1];
+      }
+      valid = true;
+    }
+  } else if (lane == 13) {
+    valid = true;
+  }
+  return pbm_eval<N, M>(cx, cy, valid, wg, p, lam, intra_x, alpha, beta, gnum, gden, qp, refine,
+                        curs, win);
 }
 
 // ---------------------------------------------------------------------------

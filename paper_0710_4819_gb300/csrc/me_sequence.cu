@@ -30,6 +30,7 @@ namespace me {
 constexpr int kSeqMax = 64;     // frame pairs per call
 constexpr int kSeqThreads = 256;
 constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
+constexpr int kSeqSP = 192;     // compile-time shifted-word pitch of the main FSBM build
 
 struct SeqFrames {
   const uint8_t* f[kSeqMax + 1];  // f[k] = reference of pair k, f[k+1] = its current frame
@@ -46,10 +47,6 @@ struct SeqArgs {
   int32_t alpha, beta, gnum, gden, qp, refine;
 };
 
-struct SeqSeg {  // the blocks of wave w of pair k, claimed as one run of items
-  int k, wave, ylo, count, item_base;
-};
-
 struct SeqCtrl {
   int epoch, next, error, err_item;
   long long timeout_ns;
@@ -58,7 +55,7 @@ struct SeqCtrl {
 
 // ------------------------------------------------------------------ FSBM
 
-template <int N, int M, int T>
+template <int N, int M, int T, int SP = 0>
 __global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, int H, int p, int G,
                                                           uint32_t lam, int16_t* __restrict__ mv_out,
                                                           uint32_t* __restrict__ J_out,
@@ -71,8 +68,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, i
   const int gpr = (BW + bpc - 1) / bpc;
   const int by = blockIdx.x / gpr, bx0 = (blockIdx.x % gpr) * bpc;
   const int nb = min(bpc, BW - bx0);
-  const FsGeom g = fs_geom<N, M, T>(p, nb, G);
-  fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, bx0 * N, by * M, g, lam, smem, keys);
+  const FsGeom g = fs_geom<N, M, T>(p, nb, G, 0, 0, SP);
+  fs_group<N, M, T, SP>(fr.f[k + 1], fr.f[k], W, H, bx0 * N, by * M, g, lam, smem, keys);
   if ((int)threadIdx.x < nb) {
     const Decoded d = decode_key(keys[threadIdx.x], p, lam);
     const size_t b = (size_t)k * nbf + by * BW + bx0 + threadIdx.x;
@@ -90,6 +87,20 @@ static __device__ __forceinline__ long long seq_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+
+// Optional per-block timeline of k_acbm_seq for latency analysis, compiled in
+// only with ME_SEQ_TRACE: [block][claimed, predecessors ready, PBM decided,
+// full search started, full search published, window staged, PBM evaluated,
+// full search evaluated] in globaltimer nanoseconds.
+#ifdef ME_SEQ_TRACE
+__device__ unsigned long long* g_seq_trace = nullptr;
+#define SEQ_TRACE(o, j)                                                     \
+  do {                                                                      \
+    if (g_seq_trace) g_seq_trace[(size_t)(o) * 8 + (j)] = (unsigned long long)seq_ns(); \
+  } while (0)
+#else
+#define SEQ_TRACE(o, j) do { } while (0)
+#endif
 
 __global__ void k_seq_begin(SeqCtrl* c) {
   c->epoch += 1;
@@ -136,45 +147,56 @@ __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGe
   }
 }
 
-// Bounded wait until *f == want; gives up (and flags the error for everyone)
-// after the timeout or as soon as another wait has given up.
-static __device__ __forceinline__ void seq_wait(const int* f, int want, SeqCtrl* ctrl,
-                                                long long timeout, int item) {
-  const volatile int* vf = f;
+// Bounded wait until the flag word carries epoch `want`; returns the word (the
+// predecessor's vector rides in its low half).  Gives up (and flags the error
+// for everyone) after the timeout or as soon as another wait has given up.
+static __device__ __forceinline__ unsigned long long seq_wait(const unsigned long long* f, int want,
+                                                              SeqCtrl* ctrl, long long timeout,
+                                                              int item) {
+  const volatile unsigned long long* vf = f;
   const volatile int* err = &ctrl->error;
+  unsigned long long w = *vf;
+  if (pub_epoch(w) == want) return w;
   const long long t0 = seq_ns();
-  while (*vf != want && *err == 0) {
+  while (*err == 0) {
+    __nanosleep(32);
+    w = *vf;
+    if (pub_epoch(w) == want) break;
     if (seq_ns() - t0 > timeout) {
       atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
       atomicExch(&ctrl->err_item, item);
       break;
     }
-    __nanosleep(32);
   }
+  return w;
 }
 
-// Two roles in one launch.  The first half of the CTAs (one per SM) run PBM:
-// each warp claims blocks on its own in the (wave + 4*pair) order, waits for
-// the block's predecessors, runs PBM and the two conditions, and either
-// publishes the block or appends it to the full-search queue.  The second half
-// take queued blocks in order and search each with the whole CTA.  A PBM warp
-// only waits for blocks claimed before its own, and a search CTA only for a
-// queue entry that a running PBM warp will write (or for the end of the run),
-// so every wait ends.
+// Two roles in one launch.  PBM CTAs: each warp claims blocks on its own in
+// the (wave + 4*pair) order (the item table maps a claim to its block), queues
+// the block's current pixels and search window as asynchronous copies, waits
+// for the block's predecessors (whose flag words carry their final vectors),
+// runs PBM and the two conditions, and either publishes the block or appends
+// it to the full-search queue.  A warp claims its next block before working
+// on the current one, so the claim's latency overlaps the work.  Search CTAs
+// take queued blocks in order and search each with the whole CTA.  The
+// smallest unfinished block is always some warp's current block and all its
+// predecessors are finished, and a search CTA only waits for a queue entry
+// that a running PBM warp will write (or for the end of the run), so every
+// wait ends; each wait is also bounded in time.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
                                                              int p, PadGeom pg,
                                                              const uint8_t* __restrict__ refpad,
                                                              const uint32_t* __restrict__ intra,
-                                                             int* __restrict__ flags,
-                                                             const SeqSeg* __restrict__ seg, int nseg,
+                                                             unsigned long long* __restrict__ flags,
+                                                             const int* __restrict__ items,
                                                              int total, SeqCtrl* ctrl,
-                                                             int* __restrict__ q_item,
-                                                             int* __restrict__ q_ready,
+                                                             unsigned long long* __restrict__ q,
                                                              int pbm_warps, int nsm) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_slot, s_item, s_role;
+  __shared__ int s_item, s_role;
+  const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int BW = W / N, BH = H / M, nbf = BW * BH;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
@@ -196,65 +218,88 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
     const int wwords = pbm_win_words(N, M, p) + M * (N / 4);
     uint32_t* win = smem + warp * wwords;
     uint32_t* curs = win + pbm_win_words(N, M, p);
+    // lane 0 holds the next claim (item index and its block)
+    int nxt = 0, onxt = 0;
+    if (lane == 0) {
+      nxt = atomicAdd(&ctrl->next, 1);
+      if (nxt < total) onxt = items[nxt];
+    }
     for (;;) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&ctrl->next, 1);
-      i = __shfl_sync(0xffffffffu, i, 0);
+      const int i = __shfl_sync(FULL, nxt, 0);
       if (i >= total) break;
-      int k = 0, b = 0;
-      if (lane == 0) {
-        int lo = 0, hi = nseg - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (seg[mid].item_base <= i) lo = mid; else hi = mid - 1;
-        }
-        const SeqSeg sg = seg[lo];
-        const int by = sg.ylo + (i - sg.item_base);
-        k = sg.k;
-        b = by * BW + (sg.wave - 2 * by);
-      }
-      k = __shfl_sync(0xffffffffu, k, 0);
-      b = __shfl_sync(0xffffffffu, b, 0);
+      const int o = __shfl_sync(FULL, onxt, 0);
+      if (lane == 0) SEQ_TRACE(o, 0);
+      const int k = o / nbf, b = o - k * nbf;
       const int bx = b % BW, by = b / BW;
-      int16_t* field = a.mv + (size_t)k * nbf * 2;
-      const int16_t* prev = k > 0 ? a.mv + (size_t)(k - 1) * nbf * 2 : a.prev0;
-      // lanes 0-3: spatial predecessors in pair k; lanes 4-12: the 3x3 in pair k-1
-      int nidx = -1;
+      const PbmWin wg = pbm_stage<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, p, bx * N,
+                                        by * M, curs, win);
+      const uint32_t ix = intra[o];
+      if (lane == 0) nxt = atomicAdd(&ctrl->next, 1);
+      // predictors: lanes 0-3 the spatial ones in pair k, lanes 4-12 the 3x3
+      // of pair k-1 (or of the caller's field before pair 0), lane 13 zero
+      int cx = 0, cy = 0, nidx = -1;
+      bool valid = false;
       if (lane < 4) {
         const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
         const int dy = (lane == 0) ? 0 : -1;
         const int nx = bx + dx, ny = by + dy;
-        if (nx >= 0 && nx < BW && ny >= 0) nidx = k * nbf + ny * BW + nx;
-      } else if (lane < 13 && k > 0) {
+        if (nx >= 0 && nx < BW && ny >= 0) {
+          nidx = k * nbf + ny * BW + nx;
+          valid = true;
+        }
+      } else if (lane < 13) {
         const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
-        if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) nidx = (k - 1) * nbf + ny * BW + nx;
+        if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+          valid = true;
+          if (k > 0) {
+            nidx = (k - 1) * nbf + ny * BW + nx;
+          } else if (a.prev0) {
+            cx = a.prev0[2 * (ny * BW + nx)];
+            cy = a.prev0[2 * (ny * BW + nx) + 1];
+          }
+        }
+      } else if (lane == 13) {
+        valid = true;
       }
-      if (nidx >= 0) seq_wait(flags + nidx, epoch, ctrl, timeout, i);
+      if (nidx >= 0) {
+        const unsigned long long w = seq_wait(flags + nidx, epoch, ctrl, timeout, i);
+        cx = pub_mvx(w);
+        cy = pub_mvy(w);
+      }
+#ifdef ME_SEQ_TRACE
       __syncwarp();
-      __threadfence();
-      const PbmResult r = warp_pbm<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, H, p, a.lam,
-                                         field, prev, bx, by, intra[(size_t)k * nbf + b], a.alpha,
-                                         a.beta, a.gnum, a.gden, a.qp, a.refine, curs, win);
+      if (lane == 0) SEQ_TRACE(o, 1);
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) SEQ_TRACE(o, 5);
+#endif
+      if (lane == 0 && nxt < total) onxt = items[nxt];
+      const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, p, a.lam, ix, a.alpha, a.beta, a.gnum,
+                                         a.gden, a.qp, a.refine, curs, win);
+#ifdef ME_SEQ_TRACE
+      if (lane == 0) SEQ_TRACE(o, 6);
+#endif
       if (lane == 0) {
-        const size_t o = (size_t)k * nbf + b;
         if (r.pass) {
+          // the flag word carries the vector: publish first, outputs after
           const Decoded d = decode_key(r.key, p, a.lam);
+          atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
+          int16_t* field = a.mv + (size_t)k * nbf * 2;
           field[2 * b] = (int16_t)d.mvx;
           field[2 * b + 1] = (int16_t)d.mvy;
           a.J[o] = d.J;
           a.mask[o] = 0;
           if (a.sad) a.sad[o] = d.sad;
           if (a.load) a.load[o] = (uint32_t)r.load;
-          __threadfence();
-          atomicExch(flags + o, epoch);
         } else {
+          // queue entry = epoch and block in one word; the tail count is
+          // ordered before this warp's pbm_done increment
           const int slot = atomicAdd(&ctrl->fs_tail, 1);
-          q_item[slot] = (int)o;
+          atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o);
           __threadfence();
-          atomicExch(q_ready + slot, epoch);
         }
-        __threadfence();
         atomicAdd(&ctrl->pbm_done, 1);
+        SEQ_TRACE(o, 2);
       }
       __syncwarp();
     }
@@ -265,7 +310,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         const int slot = atomicAdd(&ctrl->fs_head, 1);
         // the queue holds at most `total` entries: a slot beyond can never be
         // filled, so the CTA is done without touching it
-        const volatile int* rd = q_ready + (slot < total ? slot : 0);
+        const volatile unsigned long long* rd = q + (slot < total ? slot : 0);
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
@@ -273,35 +318,35 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         int got = -1;
         for (;;) {
           if (slot >= total) break;
-          if (*rd == epoch) { got = slot; break; }
+          const unsigned long long e = *rd;
+          if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
           if (*done == total && *tail <= slot) break;     // no more blocks will come
           if (*err != 0) break;
           if (seq_ns() - t0 > timeout) {
             atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
             break;
           }
-          __nanosleep(64);
+          __nanosleep(32);
         }
-        if (got >= 0) {
-          __threadfence();
-          s_item = *reinterpret_cast<volatile int*>(q_item + slot);
-        }
-        s_slot = got;
+        s_item = got;
       }
       __syncthreads();
-      if (s_slot < 0) break;
       const int o = s_item;
-      if (o < 0 || o >= total) {
+      if (o < 0) break;
+      if (o >= total) {
         // not a block of this run: report it instead of touching memory
         if (tid == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
         __syncthreads();
         continue;
       }
+      if (tid == 0) SEQ_TRACE(o, 3);
       const int k = o / nbf, b = o - k * nbf;
       const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
       fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
       if (tid == 0) {
+        SEQ_TRACE(o, 7);
         const Decoded d = decode_key(keys[0], p, a.lam);
+        atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
         int16_t* field = a.mv + (size_t)k * nbf * 2;
         field[2 * b] = (int16_t)d.mvx;
         field[2 * b + 1] = (int16_t)d.mvy;
@@ -309,8 +354,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         a.mask[o] = 1;
         if (a.sad) a.sad[o] = d.sad;
         if (a.load) a.load[o] = (uint32_t)(n * n);
-        __threadfence();
-        atomicExch(flags + o, epoch);
+        SEQ_TRACE(o, 4);
       }
       __syncthreads();
     }
@@ -324,12 +368,11 @@ struct SeqPlan {
   void* mem = nullptr;
   uint8_t* refpad = nullptr;
   uint32_t* intra = nullptr;
-  int* flags = nullptr;
-  int* q_item = nullptr;
-  int* q_ready = nullptr;
-  SeqSeg* segs = nullptr;
+  unsigned long long* flags = nullptr;   // per block: epoch + final vector
+  unsigned long long* q = nullptr;       // full-search queue: epoch + block
+  int* items = nullptr;                  // claim order -> block (pair * blocks + block)
   SeqCtrl* ctrl = nullptr;
-  int nseg = 0, total = 0;
+  int total = 0;
   size_t smem = 0;
   int grid = 0;
   cudaEvent_t last = nullptr;   // end of the previous run (runs of one plan never overlap)
@@ -371,40 +414,37 @@ static int seq_T(int N, int M, int p) {
 
 static int build_seq_plan(SeqPlan* pl) {
   const int N = pl->N, M = pl->M, BW = pl->W / N, BH = pl->H / M, nbf = BW * BH;
+  // claim order: all blocks of all pairs by w + kSeqLag * k, then pair, then row
   const Waves wv = make_waves(BW, BH);
-  std::vector<SeqSeg> segs;
-  int base = 0;
+  std::vector<int> items;
+  items.reserve((size_t)nbf * pl->K);
   const int maxkey = wv.n - 1 + kSeqLag * (pl->K - 1);
   for (int key = 0; key <= maxkey; key++)
     for (int k = 0; k < pl->K; k++) {
       const int w = key - kSeqLag * k;
-      if (w < 0 || w >= wv.n || wv.count(w) == 0) continue;
-      segs.push_back(SeqSeg{k, w, wv.ylo(w), wv.count(w), base});
-      base += wv.count(w);
+      if (w < 0 || w >= wv.n) continue;
+      for (int by = wv.ylo(w); by <= wv.yhi(w); by++) items.push_back(k * nbf + by * BW + (w - 2 * by));
     }
-  pl->nseg = (int)segs.size();
-  pl->total = base;
+  pl->total = (int)items.size();
   const PadGeom pg = pad_geom(pl->W, pl->H, pl->p);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_ctrl = take(sizeof(SeqCtrl));
-  const size_t o_segs = take(sizeof(SeqSeg) * segs.size());
+  const size_t o_items = take(sizeof(int) * items.size());
   const size_t o_pad = take((size_t)pg.pitch * pg.rows * pl->K);
   const size_t o_intra = take(4 * (size_t)nbf * pl->K);
-  const size_t o_flags = take(4 * (size_t)nbf * pl->K);
-  const size_t o_qitem = take(4 * (size_t)nbf * pl->K);
-  const size_t o_qready = take(4 * (size_t)nbf * pl->K);
+  const size_t o_flags = take(8 * (size_t)nbf * pl->K);
+  const size_t o_q = take(8 * (size_t)nbf * pl->K);
   ME_CUDA(cudaMalloc(&pl->mem, off));
   ME_CUDA(cudaMemset(pl->mem, 0, off));
   uint8_t* m = static_cast<uint8_t*>(pl->mem);
   pl->ctrl = reinterpret_cast<SeqCtrl*>(m + o_ctrl);
-  pl->segs = reinterpret_cast<SeqSeg*>(m + o_segs);
+  pl->items = reinterpret_cast<int*>(m + o_items);
   pl->refpad = m + o_pad;
   pl->intra = reinterpret_cast<uint32_t*>(m + o_intra);
-  pl->flags = reinterpret_cast<int*>(m + o_flags);
-  pl->q_item = reinterpret_cast<int*>(m + o_qitem);
-  pl->q_ready = reinterpret_cast<int*>(m + o_qready);
-  ME_CUDA(cudaMemcpy(pl->segs, segs.data(), sizeof(SeqSeg) * segs.size(), cudaMemcpyHostToDevice));
+  pl->flags = reinterpret_cast<unsigned long long*>(m + o_flags);
+  pl->q = reinterpret_cast<unsigned long long*>(m + o_q);
+  ME_CUDA(cudaMemcpy(pl->items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice));
   SeqCtrl c;
   std::memset(&c, 0, sizeof(c));
   c.timeout_ns = 1000000000ll;
@@ -481,6 +521,17 @@ int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
   const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 33
+  // at 8 blocks per CTA) uses the build with a compile-time row pitch
+  if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP) {
+    auto kern = k_fsbm_seq<16, 16, 13, kSeqSP>;
+    const size_t smem = fs_smem_bytes<16, 16, 13>(fs_geom<16, 16, 13>(p, bpc, pl.G, 0, 0, kSeqSP));
+    st = ensure_dynamic_smem((const void*)kern, smem);
+    if (st) return st;
+    kern<<<grid, pl.threads, smem, s>>>(fr, W, H, p, pl.G, lambda_q8, mv_out, J_out, sad_out);
+    ME_CUDA(cudaGetLastError());
+    return ME_OK;
+  }
   st = ME_ERR_ARG;
 #define X(n_, m_, t_)                                                                          \
   if (N == n_ && M == m_ && pl.T == t_) {                                                      \
@@ -544,8 +595,8 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
 #define X(n_, m_, t_)                                                                          \
   if (N == n_ && M == m_ && pl->T == t_) {                                                     \
     k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
-        fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->segs, pl->nseg, pl->total,   \
-        pl->ctrl, pl->q_item, pl->q_ready, seq_pbm_warps(N, M, p), pl->grid / 2);              \
+        fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total, pl->ctrl,  \
+        pl->q, seq_pbm_warps(N, M, p), pl->grid / 2);                                          \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)

@@ -61,7 +61,7 @@ struct SrvStream {
   uint8_t* d_mask = nullptr;
   uint8_t* refpad = nullptr;
   uint32_t* intra = nullptr;
-  int* flags = nullptr;
+  unsigned long long* flags = nullptr;  // per block: epoch + final vector
   void* hmem = nullptr;           // pinned result slot
   int16_t* h_mv = nullptr;
   uint32_t *h_J = nullptr, *h_sad = nullptr, *h_load = nullptr;
@@ -110,7 +110,8 @@ static size_t stream_bytes(int W, int H, int N, int M, int p) {
   const PadGeom pg = pad_geom(W, H, p);
   const size_t nb = (size_t)(W / N) * (H / M), fr = (size_t)W * H;
   return align_up(fr, 256) * 2 + align_up(4 * nb, 256) * 2 + align_up(4 * nb, 256) * 3 +
-         align_up(nb, 256) + align_up((size_t)pg.pitch * pg.rows, 256) + align_up(4 * nb, 256) * 2;
+         align_up(nb, 256) + align_up((size_t)pg.pitch * pg.rows, 256) + align_up(4 * nb, 256) +
+         align_up(8 * nb, 256);
 }
 
 static int alloc_stream(me_server* sv, SrvStream* s) {
@@ -131,7 +132,7 @@ static int alloc_stream(me_server* sv, SrvStream* s) {
   const PadGeom pg = pad_geom(s->W, s->H, s->p);
   s->refpad = take((size_t)pg.pitch * pg.rows);
   s->intra = reinterpret_cast<uint32_t*>(take(4 * nb));
-  s->flags = reinterpret_cast<int*>(take(4 * nb));
+  s->flags = reinterpret_cast<unsigned long long*>(take(8 * nb));
   const size_t hb = 4 * nb * 4 + nb;
   ME_CUDA(cudaMallocHost(&s->hmem, hb));
   uint8_t* h = static_cast<uint8_t*>(s->hmem);
@@ -248,10 +249,10 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     const size_t o_st = align_up(o_sh + sizeof(BShape) * ns, 256);
     const size_t o_tab = align_up(o_st + sizeof(BStream) * ns, 256);
     const size_t tab = acbm ? sizeof(BSegment) * segs.size() : sizeof(BFsEntry) * ent.size();
-    // full-search queue (ACBM): 8 + 4 bytes per block of the step
-    const size_t o_q = align_up(o_tab + tab, 256);
-    const size_t o_qr = align_up(o_q + 8 * (size_t)std::max(1, total_items), 256);
-    int st = slot_reserve(sl, o_qr + 4 * (size_t)std::max(1, total_items) + 256);
+    // item table and full-search queue (ACBM): 8 + 8 bytes per block of the step
+    const size_t o_items = align_up(o_tab + tab, 256);
+    const size_t o_q = align_up(o_items + 8 * (size_t)std::max(1, total_items), 256);
+    int st = slot_reserve(sl, o_q + 8 * (size_t)std::max(1, total_items) + 256);
     if (st) return st;
     uint8_t* h = static_cast<uint8_t*>(sl.h_tab);
     uint8_t* d = static_cast<uint8_t*>(sl.d_tab);
@@ -260,15 +261,15 @@ static int launch_step(me_server* sv, SrvSlot& sl, std::vector<SrvStream*>& read
     if (acbm) std::memcpy(h + o_tab, segs.data(), tab);
     else std::memcpy(h + o_tab, ent.data(), tab);
     ME_CUDA(cudaMemcpyAsync(d, h, o_tab + tab, cudaMemcpyHostToDevice, sl.cs));
-    // the queue sits where earlier steps kept their tables: clear its flags
-    if (acbm) ME_CUDA(cudaMemsetAsync(d + o_qr, 0, 4 * (size_t)std::max(1, total_items), sl.cs));
+    // the queue sits where earlier steps kept their tables: clear its entries
+    if (acbm) ME_CUDA(cudaMemsetAsync(d + o_q, 0, 8 * (size_t)std::max(1, total_items), sl.cs));
     const int epoch = ++g_epoch;
     if (acbm)
       st = launch_acbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
                             reinterpret_cast<BStream*>(d + o_st), ns, total_pad, total_blocks,
                             reinterpret_cast<BSegment*>(d + o_tab), (int)segs.size(), total_items,
-                            smem, p_max, reinterpret_cast<unsigned long long*>(d + o_q),
-                            reinterpret_cast<int*>(d + o_qr), sl.cs);
+                            smem, p_max, reinterpret_cast<unsigned long long*>(d + o_items),
+                            reinterpret_cast<unsigned long long*>(d + o_q), sl.cs);
     else
       st = launch_fsbm_step(N, M, T, sl.d_ctrl, epoch, reinterpret_cast<BShape*>(d + o_sh),
                             reinterpret_cast<BStream*>(d + o_st),
