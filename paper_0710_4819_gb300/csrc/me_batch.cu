@@ -113,7 +113,7 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
                      unsigned long long* items, unsigned long long* q, cudaStream_t s) {
-  k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
+  k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
   if (total_items > 0) {
     const int gt = std::max(1, std::min((total_items + 255) / 256, 152 * 8));
@@ -160,7 +160,7 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
 int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, const BFsEntry* ent, int nent, size_t smem,
                      cudaStream_t s) {
-  k_batch_begin<<<1, 1, 0, s>>>(ctrl, epoch);
+  k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
   int st = ME_ERR_ARG;
 #define X(n_, m_, t_)                                                                          \

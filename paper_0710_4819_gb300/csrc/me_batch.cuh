@@ -45,15 +45,23 @@ struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block
   int stream, by, bx0, nb, G;
 };
 
+// Control block of a step.  Counters that many warps update or poll each sit
+// on their own 128-byte line: an atomic on a line that 1000+ warps keep
+// reading waits behind those reads for microseconds.
 struct BCtrl {
   int epoch;
-  int next;
   int error;
   int err_item;
-  long long timeout_ns;
   int skip_stream, skip_block;  // fault injection: never publish this block
-  int fs_head, fs_tail, pbm_done, started;  // full-search queue of the ACBM step
+  long long timeout_ns;
+  alignas(128) int next;        // work claims
+  alignas(128) int fs_head;     // full-search queue of the ACBM step: claims
+  alignas(128) int fs_tail;     //   appends
+  alignas(128) int pbm_done;    //   blocks through PBM
+  alignas(128) int started;     // CTA arrivals (roles)
+  int sm_arr[kRoleSlots];       // CTA arrivals per SM (roles)
 };
+
 
 static __device__ __forceinline__ long long global_ns() {
   long long t;
@@ -62,6 +70,8 @@ static __device__ __forceinline__ long long global_ns() {
 }
 
 static __global__ void k_batch_begin(BCtrl* c, int epoch) {
+  for (int i = threadIdx.x; i < kRoleSlots; i += blockDim.x) c->sm_arr[i] = 0;
+  if (threadIdx.x != 0) return;
   c->epoch = epoch > 0 ? epoch : c->epoch + 1;
   c->fs_head = 0;
   c->fs_tail = 0;
@@ -196,7 +206,8 @@ __host__ __device__ inline int batch_pbm_warps(int N, int M, int p) {
   return w < 1 ? 1 : (w > kBatchThreads / 32 ? kBatchThreads / 32 : w);
 }
 
-// ACBM step over many streams, two roles in one launch.  PBM CTAs: every warp
+// ACBM step over many streams, two roles in one launch (cta_role: one CTA of
+// each per SM).  PBM CTAs: every warp
 // claims blocks on its own, in wave order across streams (the item table maps
 // a claim to its stream and block), queues the block's current pixels and
 // search window as asynchronous copies, waits for the block's left / up-left /
@@ -224,13 +235,7 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const long long timeout = ctrl->timeout_ns;
-  // role by arrival, alternating and shifted by one every nsm arrivals, so the
-  // two CTAs an SM receives differ and any three resident CTAs of this launch
-  // include both roles (another launch may hold the rest of the SMs)
-  if (tid == 0) {
-    const int arr = atomicAdd(&ctrl->started, 1);
-    s_role = (arr + arr / nsm) & 1;
-  }
+  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr);
   __syncthreads();
 
   if (s_role == 0) {

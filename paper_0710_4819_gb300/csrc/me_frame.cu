@@ -138,6 +138,9 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
   const AcbmArgs a = *ap;
   const int by = ylo + idx, bx = w - 2 * by;
   const int BW = W / N, b = by * BW + bx;
+  if (!ME_CHECK(bx >= 0 && bx < BW && by >= 0 && by < H / M, "ME_CHECK pbm_wave w %d bx %d by %d\n",
+                w, bx, by))
+    return;
   const PbmResult r = warp_pbm<N, M>(a.cur, refpad, pg, W, H, p, a.lam, a.mv, a.prev, bx, by,
                                      intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp, a.refine,
                                      curs[warp], wins + warp * pbm_win_words(N, M, p));

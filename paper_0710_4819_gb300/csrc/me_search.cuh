@@ -2,7 +2,21 @@
 // the batched/persistent paths: reference padding, Intra_SAD, the PBM stage of
 // ACBM for one block (one warp), and the full-search plan (tile choice).
 #pragma once
+#include <cstdio>
+
+#include "../../include/me.h"
 #include "me_device.cuh"
+
+// Compile-time self-checks (ME_DEBUG_CHECKS): an index outside its buffer is
+// printed (first few only) and the access is skipped.  Off by default.
+#ifdef ME_DEBUG_CHECKS
+static __device__ int g_me_check_count = 0;
+#define ME_CHECK(cond, ...)                                              \
+  ((cond) ? true                                                         \
+          : ((atomicAdd(&g_me_check_count, 1) < 16 ? printf(__VA_ARGS__) : 0), false))
+#else
+#define ME_CHECK(cond, ...) true
+#endif
 
 namespace me {
 
@@ -105,10 +119,16 @@ __device__ __forceinline__ uint32_t lane_sad_win(const uint32_t* curs, const uin
                                                  const PbmWin& wg, int p, int mvx, int mvy) {
   constexpr int NW = N / 4;
   const int o = wg.s0 + p + mvx;
+  if (!ME_CHECK(p + mvy >= 0 && p + mvy + M <= wg.rows && o >= 0 && (o >> 2) + NW < wg.wp,
+                "ME_CHECK lane_sad_win p %d mv %d,%d rows %d wp %d s0 %d\n", p, mvx, mvy, wg.rows,
+                wg.wp, wg.s0))
+    return 0;
   const uint32_t* rp = win + (p + mvy) * wg.wp + (o >> 2);
   const unsigned sh = 8u * (unsigned)(o & 3);
   uint32_t acc = 0;
-#pragma unroll
+  // rolled (4 rows per iteration): PBM code is kept small so it stays in the
+  // instruction cache between blocks, when other code has run on the SM
+#pragma unroll 4
   for (int j = 0; j < M; j++) {
     uint32_t wv[NW + 1];
 #pragma unroll
@@ -120,9 +140,9 @@ __device__ __forceinline__ uint32_t lane_sad_win(const uint32_t* curs, const uin
 }
 
 template <int N, int M>
-__device__ __forceinline__ unsigned long long lane_key(const uint32_t* curs, const uint32_t* win,
-                                                       const PbmWin& wg, int mvx, int mvy, int p,
-                                                       uint32_t lam) {
+__device__ __noinline__ unsigned long long lane_key(const uint32_t* curs, const uint32_t* win,
+                                                    PbmWin wg, int mvx, int mvy, int p,
+                                                    uint32_t lam) {
   const uint32_t s = lane_sad_win<N, M>(curs, win, wg, p, mvx, mvy);
   const uint32_t J = 256u * s + lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy));
   return make_key(J, mvx, mvy, p);
@@ -148,6 +168,84 @@ __host__ __device__ __forceinline__ int pub_mvx(unsigned long long w) { return (
 __host__ __device__ __forceinline__ int pub_mvy(unsigned long long w) {
   return (int)(int16_t)(uint16_t)((w >> 16) & 0xffffu);
 }
+
+// ---------------------------------------------------------------------------
+// Role of a CTA of the two-role persistent kernels (0: PBM warps, 1: full
+// searches), called by one thread.  The first two CTAs of a launch take one
+// role each, so both roles are resident from the start whatever else holds
+// the GPU; after that the first CTA on an SM runs PBM and the second the full
+// searches, so every SM hosts one of each.  (Arrival order alone does not
+// pair the CTAs of an SM: the block scheduler may give both CTAs of an SM the
+// same parity, leaving half the SMs with two PBM CTAs and half with two
+// search CTAs.)
+// ---------------------------------------------------------------------------
+constexpr int kRoleSlots = 1024;   // > any %smid
+
+__device__ __forceinline__ int cta_role(int* started, int* sm_arr) {
+  const int arr = atomicAdd(started, 1);
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  const int sa = atomicAdd(sm_arr + (smid & (kRoleSlots - 1)), 1);
+  return arr < 2 ? arr : (sa & 1);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-wide bounded wait of the persistent kernels: every lane with a
+// non-null flag f waits until its word carries epoch `want` (pub_word) and
+// gets the word back.  One load per lane first; then a single pending lane
+// polls (short back-off) and the others re-read once it is ready, so a
+// waiting warp keeps about one load in flight.  Gives up after `lim` SM
+// cycles (recording ME_ERR_TIMEOUT and `item` in *err / *err_item) or as soon
+// as *err is set by another wait.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_wait_flags(const unsigned long long* f, int want,
+                                                              int* err, int* err_item,
+                                                              long long lim, int item) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const volatile int* verr = err;
+  unsigned long long w = 0;
+  bool need = false;
+  if (f) {
+    w = *reinterpret_cast<const volatile unsigned long long*>(f);
+    need = pub_epoch(w) != want;
+  }
+  unsigned pend = __ballot_sync(FULL, need);
+  if (!pend) return w;
+  const long long t0 = clock64();
+  while (pend) {
+    const int l = 31 - __clz((int)pend);
+    if (lane == l) {
+      unsigned ns = 32;
+      for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns *= 2;
+        w = *reinterpret_cast<const volatile unsigned long long*>(f);
+        if (pub_epoch(w) == want) break;
+        if (*verr != 0) break;
+        if (clock64() - t0 > lim) {
+          atomicExch(err, (int)ME_ERR_TIMEOUT);
+          atomicExch(err_item, item);
+          break;
+        }
+      }
+      need = false;
+    }
+    __syncwarp();
+    if (*verr != 0) break;
+    if (need) {
+      w = *reinterpret_cast<const volatile unsigned long long*>(f);
+      need = pub_epoch(w) != want;
+    }
+    pend = __ballot_sync(FULL, need);
+  }
+  return w;
+}
+
+// Spin-wait bound in SM clock cycles (the SM-local cycle counter is cheap to
+// read, unlike the global timer): timeout_ns * 2, about the timeout at 2 GHz
+// and longer at lower clocks.
+__host__ __device__ __forceinline__ long long wait_cycles(long long timeout_ns) { return 2 * timeout_ns; }
 
 // ---------------------------------------------------------------------------
 // PBM of one block by one warp, in two parts so that the memory traffic that
@@ -193,63 +291,84 @@ __device__ __forceinline__ PbmWin pbm_stage(const uint8_t* __restrict__ cur,
   return wg;
 }
 
+// Lane 0 of pbm_eval writes globaltimer stamps to tr[0..2] and SM clock
+// stamps to tr[4..6] when tr is not null (copies waited for, predictors
+// evaluated, ring evaluated).
+__device__ __forceinline__ void pbm_stamp(unsigned long long* tr, int i) {
+  if (tr && (threadIdx.x & 31) == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    tr[i] = t;
+    tr[4 + i] = (unsigned long long)clock64();
+  }
+}
+
 template <int N, int M>
 __device__ PbmResult pbm_eval(int cx, int cy, bool valid, const PbmWin& wg, int p, uint32_t lam,
                               uint32_t intra_x, int32_t alpha, int32_t beta, int32_t gnum,
                               int32_t gden, int32_t qp, int32_t refine, const uint32_t* curs,
-                              const uint32_t* win) {
+                              const uint32_t* win, unsigned long long* tr = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
+  pbm_stamp(tr, 0);
   cx = clampi(cx, -p, p);
   cy = clampi(cy, -p, p);
   const int code = valid ? ((cy + p) << 8) + (cx + p) : -1 - lane;
   bool dup = false;
-#pragma unroll
+#pragma unroll 1
   for (int l = 0; l < 14; l++) {
     const int v = __shfl_sync(FULL, code, l);
     dup |= (l < lane) && (v == code);
   }
   const bool eval = valid && !dup;
-  // step 2: best predictor by J
-  unsigned long long key = eval ? lane_key<N, M>(curs, win, wg, cx, cy, p, lam) : kNoKey;
-  unsigned long long best = warp_min64(key);
-  int load = __popc(__ballot_sync(FULL, eval));
-  // step 3: +-1 integer ring around the best predictor
-  if (refine) {
-    const Decoded d = decode_key(best, p, lam);
-    int rx = 0, ry = 0, rcode = -100 - lane;
-    if (lane < 8) {
-      const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
-      rx = clampi(d.mvx + o % 3 - 1, -p, p);
-      ry = clampi(d.mvy + o / 3 - 1, -p, p);
-      rcode = ((ry + p) << 8) + (rx + p);
+  // phase 0 (step 2): every distinct predictor, best by J; phase 1 (step 3):
+  // the +-1 integer ring around that best, without positions already
+  // evaluated.  One rolled loop, so the candidate code exists once.
+  unsigned long long best = kNoKey;
+  int load = 0;
+  int ex = cx, ey = cy;
+  bool act = eval;
+#pragma unroll 1
+  for (int ph = 0; ph < (refine ? 2 : 1); ph++) {
+    if (ph == 1) {
+      const Decoded d = decode_key(best, p, lam);
+      int rcode = -100 - lane;
+      ex = 0;
+      ey = 0;
+      if (lane < 8) {
+        const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
+        ex = clampi(d.mvx + o % 3 - 1, -p, p);
+        ey = clampi(d.mvy + o / 3 - 1, -p, p);
+        rcode = ((ey + p) << 8) + (ex + p);
+      }
+      const int ecode = eval ? code : -1;
+      bool rdup = false;
+#pragma unroll 1
+      for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
+#pragma unroll 1
+      for (int l = 0; l < 8; l++) {
+        const int v = __shfl_sync(FULL, rcode, l);
+        rdup |= (l < lane) && (v == rcode);
+      }
+      act = lane < 8 && !rdup;
     }
-    const int ecode = eval ? code : -1;
-    bool rdup = false;
-#pragma unroll
-    for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
-#pragma unroll
-    for (int l = 0; l < 8; l++) {
-      const int v = __shfl_sync(FULL, rcode, l);
-      rdup |= (l < lane) && (v == rcode);
-    }
-    const bool reval = lane < 8 && !rdup;
-    unsigned long long k2 = reval ? lane_key<N, M>(curs, win, wg, rx, ry, p, lam) : kNoKey;
-    best = umin64(best, warp_min64(k2));
-    load += __popc(__ballot_sync(FULL, reval));
+    const unsigned long long key = act ? lane_key<N, M>(curs, win, wg, ex, ey, p, lam) : kNoKey;
+    best = umin64(best, warp_min64(key));
+    load += __popc(__ballot_sync(FULL, act));
+    pbm_stamp(tr, 1 + ph);
   }
   // Sec. 3.2 conditions in exact integers (intra_x = NM * Intra_SAD)
   const Decoded d = decode_key(best, p, lam);
   const long long NM = N * M, sad = d.sad, q = qp;
   const bool c1 = (long long)intra_x + NM * sad < NM * ((long long)alpha + (long long)beta * q * q);
   const bool c2 = (long long)gden * NM * sad < (long long)gnum * (long long)intra_x;
-  PbmResult r;
-  r.key = best;
-  r.load = load;
-  r.pass = c1 || c2;
-  return r;
+  PbmResult res;
+  res.key = best;
+  res.load = load;
+  res.pass = c1 || c2;
+  return res;
 }
 
 // PBM of block (bx, by) with its predictors read from the current-frame field

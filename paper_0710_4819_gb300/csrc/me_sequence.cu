@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -47,10 +48,18 @@ struct SeqArgs {
   int32_t alpha, beta, gnum, gden, qp, refine;
 };
 
+// Control block of a run.  Counters that many warps update or poll each sit
+// on their own 128-byte line: an atomic on a line that 1000+ warps keep
+// reading waits behind those reads for microseconds.
 struct SeqCtrl {
-  int epoch, next, error, err_item;
+  int epoch, error, err_item;   // read-mostly (error is written only on failure)
   long long timeout_ns;
-  int fs_head, fs_tail, pbm_done, started;
+  alignas(128) int next;        // PBM claims
+  alignas(128) int fs_head;     // search-CTA claims
+  alignas(128) int fs_tail;     // queue appends
+  alignas(128) int pbm_done;    // blocks through PBM
+  alignas(128) int started;     // CTA arrivals (roles)
+  int sm_arr[kRoleSlots];       // CTA arrivals per SM (roles)
 };
 
 // ------------------------------------------------------------------ FSBM
@@ -82,27 +91,29 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, i
 
 // ------------------------------------------------------------------ ACBM
 
-static __device__ __forceinline__ long long seq_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Optional per-block timeline of k_acbm_seq for latency analysis, compiled in
 // only with ME_SEQ_TRACE: [block][claimed, predecessors ready, PBM decided,
 // full search started, full search published, window staged, PBM evaluated,
 // full search evaluated] in globaltimer nanoseconds.
 #ifdef ME_SEQ_TRACE
+static __device__ __forceinline__ long long seq_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ unsigned long long* g_seq_trace = nullptr;
 #define SEQ_TRACE(o, j)                                                     \
   do {                                                                      \
-    if (g_seq_trace) g_seq_trace[(size_t)(o) * 8 + (j)] = (unsigned long long)seq_ns(); \
+    if (g_seq_trace) g_seq_trace[(size_t)(o) * 16 + (j)] = (unsigned long long)seq_ns(); \
   } while (0)
 #else
 #define SEQ_TRACE(o, j) do { } while (0)
 #endif
 
 __global__ void k_seq_begin(SeqCtrl* c) {
+  for (int i = threadIdx.x; i < kRoleSlots; i += blockDim.x) c->sm_arr[i] = 0;
+  if (threadIdx.x != 0) return;
   c->epoch += 1;
   c->next = 0;
   c->error = 0;
@@ -147,42 +158,17 @@ __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGe
   }
 }
 
-// Bounded wait until the flag word carries epoch `want`; returns the word (the
-// predecessor's vector rides in its low half).  Gives up (and flags the error
-// for everyone) after the timeout or as soon as another wait has given up.
-static __device__ __forceinline__ unsigned long long seq_wait(const unsigned long long* f, int want,
-                                                              SeqCtrl* ctrl, long long timeout,
-                                                              int item) {
-  const volatile unsigned long long* vf = f;
-  const volatile int* err = &ctrl->error;
-  unsigned long long w = *vf;
-  if (pub_epoch(w) == want) return w;
-  const long long t0 = seq_ns();
-  while (*err == 0) {
-    __nanosleep(32);
-    w = *vf;
-    if (pub_epoch(w) == want) break;
-    if (seq_ns() - t0 > timeout) {
-      atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
-      atomicExch(&ctrl->err_item, item);
-      break;
-    }
-  }
-  return w;
-}
-
-// Two roles in one launch.  PBM CTAs: each warp claims blocks on its own in
-// the (wave + 4*pair) order (the item table maps a claim to its block), queues
-// the block's current pixels and search window as asynchronous copies, waits
-// for the block's predecessors (whose flag words carry their final vectors),
-// runs PBM and the two conditions, and either publishes the block or appends
-// it to the full-search queue.  A warp claims its next block before working
-// on the current one, so the claim's latency overlaps the work.  Search CTAs
-// take queued blocks in order and search each with the whole CTA.  The
-// smallest unfinished block is always some warp's current block and all its
-// predecessors are finished, and a search CTA only waits for a queue entry
-// that a running PBM warp will write (or for the end of the run), so every
-// wait ends; each wait is also bounded in time.
+// Two roles in one launch (cta_role: one CTA of each per SM).  PBM CTAs: each
+// warp claims blocks on its own in the (wave + 4*pair) order (the item table
+// maps a claim to its block), queues the block's current pixels and search
+// window as asynchronous copies, waits for the block's predecessors (whose
+// flag words carry their final vectors), runs PBM and the two conditions, and
+// either publishes the block or appends it to the full-search queue; then it
+// claims the next block.  Search CTAs take queued blocks in order and search
+// each with the whole CTA.  A PBM warp only waits for blocks claimed before
+// its own, and a search CTA only for a queue entry that a running PBM warp
+// will write (or for the end of the run), so every wait ends; each wait is
+// also bounded in time.
 template <int N, int M, int T>
 __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
                                                              int p, PadGeom pg,
@@ -203,13 +189,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
   const long long timeout = ctrl->timeout_ns;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
   const int n = 2 * p + 1;
-  // role by arrival, alternating and shifted by one every nsm arrivals, so the
-  // two CTAs an SM receives differ and any three resident CTAs of this launch
-  // include both roles (another launch may hold the rest of the SMs)
-  if (tid == 0) {
-    const int arr = atomicAdd(&ctrl->started, 1);
-    s_role = (arr + arr / nsm) & 1;
-  }
+  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr);
   __syncthreads();
 
   if (s_role == 0) {
@@ -234,7 +214,6 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       const PbmWin wg = pbm_stage<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, p, bx * N,
                                         by * M, curs, win);
       const uint32_t ix = intra[o];
-      if (lane == 0) nxt = atomicAdd(&ctrl->next, 1);
       // predictors: lanes 0-3 the spatial ones in pair k, lanes 4-12 the 3x3
       // of pair k-1 (or of the caller's field before pair 0), lane 13 zero
       int cx = 0, cy = 0, nidx = -1;
@@ -261,21 +240,35 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       } else if (lane == 13) {
         valid = true;
       }
-      if (nidx >= 0) {
-        const unsigned long long w = seq_wait(flags + nidx, epoch, ctrl, timeout, i);
-        cx = pub_mvx(w);
-        cy = pub_mvy(w);
+      {
+        const unsigned long long w = warp_wait_flags(nidx >= 0 ? flags + nidx : nullptr, epoch,
+                                                     &ctrl->error, &ctrl->err_item,
+                                                     wait_cycles(timeout), i);
+        if (nidx >= 0) {
+          cx = pub_mvx(w);
+          cy = pub_mvy(w);
+        }
       }
 #ifdef ME_SEQ_TRACE
       __syncwarp();
       if (lane == 0) SEQ_TRACE(o, 1);
       asm volatile("cp.async.wait_all;" ::: "memory");
+      if (lane == 0 && g_seq_trace) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        g_seq_trace[(size_t)o * 16 + 11] = ((unsigned long long)smid << 16) | ((unsigned)warp << 8) |
+                                           0u;
+      }
       __syncwarp();
       if (lane == 0) SEQ_TRACE(o, 5);
 #endif
-      if (lane == 0 && nxt < total) onxt = items[nxt];
+#ifdef ME_SEQ_TRACE
+      unsigned long long* trp = g_seq_trace ? g_seq_trace + (size_t)o * 16 + 8 : nullptr;
+#else
+      unsigned long long* trp = nullptr;
+#endif
       const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, p, a.lam, ix, a.alpha, a.beta, a.gnum,
-                                         a.gden, a.qp, a.refine, curs, win);
+                                         a.gden, a.qp, a.refine, curs, win, trp);
 #ifdef ME_SEQ_TRACE
       if (lane == 0) SEQ_TRACE(o, 6);
 #endif
@@ -300,6 +293,10 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         }
         atomicAdd(&ctrl->pbm_done, 1);
         SEQ_TRACE(o, 2);
+        // the next claim, once this block is out of the warp's hands (a claim
+        // taken earlier would sit behind this block's wait)
+        nxt = atomicAdd(&ctrl->next, 1);
+        onxt = nxt < total ? items[nxt] : 0;
       }
       __syncwarp();
     }
@@ -314,19 +311,25 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
-        const long long t0 = seq_ns();
+        const long long t0 = clock64(), lim = wait_cycles(timeout);
         int got = -1;
-        for (;;) {
+        unsigned ns = 32;
+        for (int it = 0;; it++) {
           if (slot >= total) break;
           const unsigned long long e = *rd;
           if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
-          if (*done == total && *tail <= slot) break;     // no more blocks will come
-          if (*err != 0) break;
-          if (seq_ns() - t0 > timeout) {
-            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
-            break;
+          // the end-of-run and error words are shared by every poller: read
+          // them on every 8th round only
+          if ((it & 7) == 7) {
+            if (*done == total && *tail <= slot) break;   // no more blocks will come
+            if (*err != 0) break;
+            if (clock64() - t0 > lim) {
+              atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+              break;
+            }
           }
-          __nanosleep(32);
+          __nanosleep(ns);
+          if (ns < 256) ns *= 2;
         }
         s_item = got;
       }
@@ -401,6 +404,11 @@ static size_t seq_smem(int p) {
 
 static int seq_T(int N, int M, int p) {
   if (!(N == 16 && M == 16)) return 8;
+  // optional override of the run length (tile sweeps): ME_SEQ_T=8|11|13|16
+  if (const char* e = std::getenv("ME_SEQ_T")) {
+    const int t = std::atoi(e);
+    if (t == 8 || t == 11 || t == 13 || t == 16) return t;
+  }
   static const int Ts[] = {8, 11, 13, 16};
   int bestT = 13;
   double best = 1e300;
@@ -576,7 +584,7 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   // runs that share a plan's scratch are ordered on the GPU, whatever their streams
   std::lock_guard<std::mutex> lk(pl->mu);
   if (pl->ran) ME_CUDA(cudaStreamWaitEvent(s, pl->last, 0));
-  k_seq_begin<<<1, 1, 0, s>>>(pl->ctrl);
+  k_seq_begin<<<1, 256, 0, s>>>(pl->ctrl);
   ME_CUDA(cudaGetLastError());
   const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16) * K,
                                              32LL * (W / N) * (H / M) * K);
