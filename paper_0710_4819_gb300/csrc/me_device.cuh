@@ -104,6 +104,7 @@ struct FsGeom {
   int pos;           // shifted-word positions per row
   int sp;            // shifted-word row pitch in words (>= pos)
   int wbw;           // 32-bit words per staged raw row
+  int wbp;           // the same when staged from a padded reference (16-byte chunks)
   int tasks;         // tasks per block: n * nseg
 };
 
@@ -145,6 +146,8 @@ __host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int
   g.pos = (bpc - 1) * N + g.nc + N - 4;
   // raw row: up to 3 bytes of alignment slack, pos+3 bytes, one spare word
   g.wbw = (g.pos + 6) / 4 + 1;
+  // padded staging: up to 15 bytes of alignment slack, pos+3 bytes, one spare word
+  g.wbp = 4 * ((15 + g.pos + 3 + 4 + 15) / 16);
   g.sp = g.pos > sp_min ? g.pos : sp_min;
   g.tasks = g.nc * g.nseg;
   return g;
@@ -154,11 +157,20 @@ __host__ __device__ inline FsGeom fs_geom(int p, int bpc, int G, int c0 = 0, int
 template <int N, int M, int T>
 __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
   size_t words = (size_t)g.bpc * M * (N / 4)        // current blocks
-               + (size_t)g.rows * g.wbw             // raw window
+               + (size_t)g.rows * (g.wbw > g.wbp ? g.wbw : g.wbp)   // raw window
                + (size_t)g.rows * g.sp              // shifted words
                + (size_t)g.rows * 3;                // per-row rate/key tables
   return words * 4 + 16 * 8 + 8;                    // per-block minima (+ alignment)
 }
+
+// An edge-padded copy of the reference (margin P on every side, rows of
+// `pitch` bytes, 16-byte aligned; `rows` rows): when given, fs_group stages
+// its window from it with asynchronous 16-byte copies (one round trip, no
+// clamping) instead of from the frame.
+struct FsPad {
+  const uint8_t* base;
+  int pitch, P, rows;
+};
 
 // Full search of g.bpc adjacent blocks whose first block has top-left pixel
 // (x0, y0).  The per-block winning keys go to keys_out[0..bpc) (shared
@@ -168,15 +180,17 @@ __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
 template <int N, int M, int T, int SP = 0>
 __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
                          int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
-                         uint32_t* smem, unsigned long long* keys_out) {
+                         uint32_t* smem, unsigned long long* keys_out,
+                         unsigned long long* tr = nullptr, FsPad pad = FsPad{nullptr, 0, 0, 0}) {
   constexpr int NW = N / 4;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   const int p = g.p, n = g.n;
   const int sp = SP > 0 ? SP : g.sp;
+  const int wpitch = pad.base ? g.wbp : g.wbw;             // staged raw row pitch (words)
   uint32_t* curw = smem;                                   // [bpc][M][NW]
-  uint32_t* wb = curw + g.bpc * M * NW;                    // [rows][wbw]
-  uint32_t* sh = wb + g.rows * g.wbw;                      // [rows][pos]
+  uint32_t* wb = curw + g.bpc * M * NW;                    // [rows][wpitch]
+  uint32_t* sh = wb + g.rows * (g.wbw > g.wbp ? g.wbw : g.wbp);   // [rows][sp]
   uint32_t* tabJ = sh + g.rows * sp;                    // [rows] lambda*L(mvy)
   uint32_t* tabK = tabJ + g.rows;                          // [rows] key bits of mvy
   uint32_t* tabQ = tabK + g.rows;                          // [rows] 32-bit run key of mvy
@@ -185,43 +199,67 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   const bool fast = fast32_ok(N, M, p, lam);
   const int rb = rank_bits(p);
 
-  // 1. current blocks (rows 4-byte aligned: W % 4 == 0, x0 % 4 == 0)
   if (tid < g.bpc) red[tid] = kNoKey;
-  for (int i = tid; i < g.bpc * M * NW; i += nthr) {
-    const int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
-    curw[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w);
-  }
-  // 2. raw window rows, from the aligned word at or left of column x0 - p
-  const int wx0 = x0 - p + g.c0;
-  const int A0 = (wx0 >> 2) << 2;        // floor to a multiple of 4
-  const int s0 = wx0 - A0;
-  const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
-  {
-    // eight independent loads per thread in flight before their stores, so
-    // the window costs about one global-memory round trip, not one per row
-    const int total = g.rows * g.wbw;
-    for (int base = tid; base < total; base += 8 * nthr) {
-      uint32_t v[8];
+  int s0;
+  if (pad.base) {
+    // 1+2 from the padded reference: current blocks as 4-byte and window rows
+    // as 16-byte asynchronous copies, all in flight together
+    for (int i = tid; i < g.bpc * M * NW; i += nthr) {
+      const int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(curw + i);
+      const void* src = cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    }
+    const int X = x0 + pad.P - p + g.c0;  // padded column of window column 0
+    const int A = X & ~15;
+    s0 = X - A;
+    const int cw = g.wbp / 4;              // 16-byte chunks per row
+    for (int i = tid; i < g.rows * cw; i += nthr) {
+      const int r = i / cw, c = i - r * cw;
+      const int yr = min(y0 + pad.P - p + r, pad.rows - 1);   // rows past the margin: edge rows
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(wb + r * wpitch + 4 * c);
+      const void* src = pad.base + (size_t)yr * pad.pitch + A + 16 * c;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  } else {
+    // 1. current blocks (rows 4-byte aligned: W % 4 == 0, x0 % 4 == 0)
+    for (int i = tid; i < g.bpc * M * NW; i += nthr) {
+      const int blk = i / (M * NW), rem = i % (M * NW), j = rem / NW, w = rem % NW;
+      curw[i] = *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w);
+    }
+    // 2. raw window rows, from the aligned word at or left of column x0 - p
+    const int wx0 = x0 - p + g.c0;
+    const int A0 = (wx0 >> 2) << 2;        // floor to a multiple of 4
+    s0 = wx0 - A0;
+    const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
+    {
+      // eight independent loads per thread in flight before their stores, so
+      // the window costs about one global-memory round trip, not one per row
+      const int total = g.rows * g.wbw;
+      for (int base = tid; base < total; base += 8 * nthr) {
+        uint32_t v[8];
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int i = base + u * nthr;
-        v[u] = 0;
-        if (i < total) {
-          const int r = i / g.wbw, q = i - r * g.wbw;
-          const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W;
-          if (inside) {
-            v[u] = *reinterpret_cast<const uint32_t*>(rowp + A0 + 4 * q);
-          } else {
+        for (int u = 0; u < 8; u++) {
+          const int i = base + u * nthr;
+          v[u] = 0;
+          if (i < total) {
+            const int r = i / g.wbw, q = i - r * g.wbw;
+            const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W;
+            if (inside) {
+              v[u] = *reinterpret_cast<const uint32_t*>(rowp + A0 + 4 * q);
+            } else {
 #pragma unroll
-            for (int b = 0; b < 4; b++)
-              v[u] |= (uint32_t)rowp[clampi(A0 + 4 * q + b, 0, W - 1)] << (8 * b);
+              for (int b = 0; b < 4; b++)
+                v[u] |= (uint32_t)rowp[clampi(A0 + 4 * q + b, 0, W - 1)] << (8 * b);
+            }
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int i = base + u * nthr;
-        if (i < total) wb[i] = v[u];
+        for (int u = 0; u < 8; u++) {
+          const int i = base + u * nthr;
+          if (i < total) wb[i] = v[u];
+        }
       }
     }
   }
@@ -233,10 +271,11 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
     tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
   }
+  if (pad.base) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // 3. shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3
   for (int r = warp; r < g.rows; r += nwarps) {
-    const uint32_t* row = wb + r * g.wbw;
+    const uint32_t* row = wb + r * wpitch;
     uint32_t* dst = sh + r * sp;
     for (int o = lane; o < g.pos; o += 32) {
       const int k = s0 + o;
@@ -244,6 +283,12 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     }
   }
   __syncthreads();
+  // optional timeline (thread 0, global timer): window staged, runs done
+  if (tr && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    tr[0] = t;
+  }
 
   // 4. tasks of this thread's block
   const int blk = tid / g.G, l = tid - blk * g.G;
@@ -313,6 +358,11 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       col += dcol;
       if (col >= nc) { col -= nc; seg++; }
     }
+  }
+  if (tr && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    tr[1] = t;
   }
   // 5. per-block minimum
   if (g.G <= 32) {

@@ -291,15 +291,13 @@ __device__ __forceinline__ PbmWin pbm_stage(const uint8_t* __restrict__ cur,
   return wg;
 }
 
-// Lane 0 of pbm_eval writes globaltimer stamps to tr[0..2] and SM clock
-// stamps to tr[4..6] when tr is not null (copies waited for, predictors
-// evaluated, ring evaluated).
+// Lane 0 of pbm_eval writes globaltimer stamps to tr[0..2] when tr is not
+// null (copies waited for, predictors evaluated, ring evaluated).
 __device__ __forceinline__ void pbm_stamp(unsigned long long* tr, int i) {
   if (tr && (threadIdx.x & 31) == 0) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     tr[i] = t;
-    tr[4 + i] = (unsigned long long)clock64();
   }
 }
 

@@ -31,7 +31,8 @@ namespace me {
 constexpr int kSeqMax = 64;     // frame pairs per call
 constexpr int kSeqThreads = 256;
 constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
-constexpr int kSeqSP = 192;     // compile-time shifted-word pitch of the main FSBM build
+constexpr int kSeqSP = 193;     // compile-time shifted-word pitch of the main FSBM build (odd:
+                                // rows of different runs start on different banks)
 
 struct SeqFrames {
   const uint8_t* f[kSeqMax + 1];  // f[k] = reference of pair k, f[k+1] = its current frame
@@ -128,7 +129,9 @@ __global__ void k_seq_begin(SeqCtrl* c) {
 template <int N, int M>
 __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGeom pg, int W, int H,
                                                       uint8_t* __restrict__ refpad,
-                                                      uint32_t* __restrict__ intra) {
+                                                      uint32_t* __restrict__ intra,
+                                                      unsigned long long* __restrict__ bkey,
+                                                      int* __restrict__ bdone) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   const int chunks = pg.pitch / 16;
@@ -154,7 +157,11 @@ __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGe
   for (long long g = gtid / 32; g < (long long)nbf * K; g += warps) {
     const int k = (int)(g / nbf), b = (int)(g - (long long)k * nbf);
     const uint32_t v = warp_intra_sad<N, M>(fr.f[k + 1], W, (b % BW) * N, (b / BW) * M);
-    if ((threadIdx.x & 31) == 0) intra[g] = v;
+    if ((threadIdx.x & 31) == 0) {
+      intra[g] = v;
+      bkey[g] = kNoKey;   // merge state of a sliced full search
+      bdone[g] = 0;
+    }
   }
 }
 
@@ -178,10 +185,12 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              const int* __restrict__ items,
                                                              int total, SeqCtrl* ctrl,
                                                              unsigned long long* __restrict__ q,
+                                                             unsigned long long* __restrict__ bkey,
+                                                             int* __restrict__ bdone, int S,
                                                              int pbm_warps, int nsm) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_item, s_role;
+  __shared__ int s_item, s_role, s_slice;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int BW = W / N, BH = H / M, nbf = BW * BH;
@@ -285,10 +294,12 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
           if (a.sad) a.sad[o] = d.sad;
           if (a.load) a.load[o] = (uint32_t)r.load;
         } else {
-          // queue entry = epoch and block in one word; the tail count is
-          // ordered before this warp's pbm_done increment
-          const int slot = atomicAdd(&ctrl->fs_tail, 1);
-          atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o);
+          // S queue entries (one per column slice; slot % S is the slice),
+          // each = epoch and block in one word; the tail count is ordered
+          // before this warp's pbm_done increment
+          const int slot = atomicAdd(&ctrl->fs_tail, S);
+          for (int sl = 0; sl < S; sl++)
+            atomicExch(q + slot + sl, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o);
           __threadfence();
         }
         atomicAdd(&ctrl->pbm_done, 1);
@@ -305,9 +316,11 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
     for (;;) {
       if (tid == 0) {
         const int slot = atomicAdd(&ctrl->fs_head, 1);
-        // the queue holds at most `total` entries: a slot beyond can never be
-        // filled, so the CTA is done without touching it
-        const volatile unsigned long long* rd = q + (slot < total ? slot : 0);
+        // the queue holds at most total * S entries: a slot beyond can never
+        // be filled, so the CTA is done without touching it
+        const int qcap = total * S;
+        s_slice = slot % S;
+        const volatile unsigned long long* rd = q + (slot < qcap ? slot : 0);
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         int got = -1;
         unsigned ns = 32;
         for (int it = 0;; it++) {
-          if (slot >= total) break;
+          if (slot >= qcap) break;
           const unsigned long long e = *rd;
           if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
           // the end-of-run and error words are shared by every poller: read
@@ -344,11 +357,29 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       }
       if (tid == 0) SEQ_TRACE(o, 3);
       const int k = o / nbf, b = o - k * nbf;
-      const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
-      fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
-      if (tid == 0) {
+      // this CTA's slice of the mvx columns
+      const int nc0 = (n + S - 1) / S, c0 = s_slice * nc0;
+      const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x, c0, min(nc0, n - c0));
+#ifdef ME_SEQ_TRACE
+      unsigned long long* ftr = g_seq_trace ? g_seq_trace + (size_t)o * 16 + 12 : nullptr;
+#else
+      unsigned long long* ftr = nullptr;
+#endif
+      fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys,
+                        ftr, FsPad{refpad + (size_t)k * padsz, pg.pitch, pg.P, pg.rows});
+      bool last = true;
+      unsigned long long key = keys[0];
+      if (S > 1 && tid == 0) {
+        // slices meet in a 64-bit minimum (the key order is total, so the
+        // order of arrival does not matter); the last slice publishes
+        atomicMin(bkey + o, key);
+        __threadfence();
+        last = atomicAdd(bdone + o, 1) == S - 1;
+        if (last) key = atomicMin(bkey + o, kNoKey);
+      }
+      if (tid == 0 && last) {
         SEQ_TRACE(o, 7);
-        const Decoded d = decode_key(keys[0], p, a.lam);
+        const Decoded d = decode_key(key, p, a.lam);
         atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
         int16_t* field = a.mv + (size_t)k * nbf * 2;
         field[2 * b] = (int16_t)d.mvx;
@@ -372,7 +403,10 @@ struct SeqPlan {
   uint8_t* refpad = nullptr;
   uint32_t* intra = nullptr;
   unsigned long long* flags = nullptr;   // per block: epoch + final vector
-  unsigned long long* q = nullptr;       // full-search queue: epoch + block
+  unsigned long long* q = nullptr;       // full-search queue: epoch + block, S per block
+  unsigned long long* bkey = nullptr;    // per block: minimum key over the search slices
+  int* bdone = nullptr;                  // per block: search slices finished
+  int S = 1;                             // column slices per full search
   int* items = nullptr;                  // claim order -> block (pair * blocks + block)
   SeqCtrl* ctrl = nullptr;
   int total = 0;
@@ -442,7 +476,18 @@ static int build_seq_plan(SeqPlan* pl) {
   const size_t o_pad = take((size_t)pg.pitch * pg.rows * pl->K);
   const size_t o_intra = take(4 * (size_t)nbf * pl->K);
   const size_t o_flags = take(8 * (size_t)nbf * pl->K);
-  const size_t o_q = take(8 * (size_t)nbf * pl->K);
+  // column slices per full search
+  pl->T = seq_T(N, M, pl->p);
+  // One slice by default: splitting a block's full search over CTAs (S > 1,
+  // merged by an atomic minimum) measured slower at 1080p p=32 (a slice of
+  // half the columns took 7 us against 10 us for the whole search, and the
+  // queue carried twice the entries); ME_SEQ_S=2..8 selects it for sweeps.
+  pl->S = 1;
+  if (const char* e = std::getenv("ME_SEQ_S")) pl->S = std::min(8, std::max(1, std::atoi(e)));
+  if ((long long)pl->total * pl->S >= (1ll << 31)) return ME_ERR_SHAPE;
+  const size_t o_q = take(8 * (size_t)nbf * pl->K * pl->S);
+  const size_t o_bkey = take(8 * (size_t)nbf * pl->K);
+  const size_t o_bdone = take(4 * (size_t)nbf * pl->K);
   ME_CUDA(cudaMalloc(&pl->mem, off));
   ME_CUDA(cudaMemset(pl->mem, 0, off));
   uint8_t* m = static_cast<uint8_t*>(pl->mem);
@@ -452,12 +497,13 @@ static int build_seq_plan(SeqPlan* pl) {
   pl->intra = reinterpret_cast<uint32_t*>(m + o_intra);
   pl->flags = reinterpret_cast<unsigned long long*>(m + o_flags);
   pl->q = reinterpret_cast<unsigned long long*>(m + o_q);
+  pl->bkey = reinterpret_cast<unsigned long long*>(m + o_bkey);
+  pl->bdone = reinterpret_cast<int*>(m + o_bdone);
   ME_CUDA(cudaMemcpy(pl->items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice));
   SeqCtrl c;
   std::memset(&c, 0, sizeof(c));
   c.timeout_ns = 1000000000ll;
   ME_CUDA(cudaMemcpy(pl->ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
-  pl->T = seq_T(N, M, pl->p);
   int nsm = 0, per_sm = 0, st = ME_ERR_ARG;
   ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->dev));
 #define X(n_, m_, t_)                                                                          \
@@ -529,7 +575,7 @@ int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
   const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 33
+  // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 34
   // at 8 blocks per CTA) uses the build with a compile-time row pitch
   if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP) {
     auto kern = k_fsbm_seq<16, 16, 13, kSeqSP>;
@@ -592,7 +638,8 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   st = ME_ERR_ARG;
 #define X(n_, m_)                                                                              \
   if (N == n_ && M == m_) {                                                                    \
-    k_seq_prologue<n_, m_><<<gp, 256, 0, s>>>(fr, K, pg, W, H, pl->refpad, pl->intra);         \
+    k_seq_prologue<n_, m_><<<gp, 256, 0, s>>>(fr, K, pg, W, H, pl->refpad, pl->intra, pl->bkey, \
+                                               pl->bdone);                                     \
     st = ME_OK;                                                                                \
   }
   X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
@@ -604,7 +651,7 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   if (N == n_ && M == m_ && pl->T == t_) {                                                     \
     k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
         fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total, pl->ctrl,  \
-        pl->q, seq_pbm_warps(N, M, p), pl->grid / 2);                                          \
+        pl->q, pl->bkey, pl->bdone, pl->S, seq_pbm_warps(N, M, p), pl->grid / 2);              \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)
