@@ -38,6 +38,9 @@ BW, BH = W // N, H_PAD // M
 NBLK = BW * BH
 NCAND = (2 * P + 1) ** 2
 ABSDIFF_PER_FRAME = NBLK * NCAND * N * M          # 8.83e9 for FSBM
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fsbm_seq<16,16,13,193>
+# on 8 frames (7 pairs): 16.760320 MB + 0 B, i.e. per frame of the sequence
+FSBM_SEQ_DRAM_BYTES_PER_FRAME = 16.760320e6 / 8
 WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
 
 
@@ -517,7 +520,13 @@ def main():
         "p99_ms": pct(pair_ms, 0.99),
         "roofline": {"bound": "alu", "kernel": "k_fsbm_seq", "achieved": achieved / 1e12,
                      "peak": peak_absdiff / 1e12, "unit": "T absdiff/s",
-                     "frac": achieved / peak_absdiff, "traffic": None,
+                     "frac": achieved / peak_absdiff,
+                     # DRAM bytes of one launch over the whole sequence: ncu
+                     # dram__bytes_read+write of the same kernel on the 8-frame
+                     # case (16.76 MB, every frame read once), scaled by frames
+                     "traffic": FSBM_SEQ_DRAM_BYTES_PER_FRAME * (pairs + 1),
+                     "traffic_unit": "bytes/launch",
+                     "algorithmic_bytes": (pairs + 1) * W * H_PAD,
                      "peak_source": "152 SMs x 64 packed-SAD lanes/clk x 4 bytes x 2070 MHz "
                                     "(lane rate measured by me_sad_peak)"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,

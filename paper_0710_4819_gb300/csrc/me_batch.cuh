@@ -358,7 +358,10 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       const BStream& a = st[si];
       const int BW = s.W / N;
       const FsGeom g = fs_geom<N, M, T>(s.p, 1, blockDim.x);
-      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
+      // window staged from the stream's padded reference (written by this
+      // step's prologue) with one round of asynchronous copies
+      fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys,
+                        nullptr, FsPad{s.refpad, s.pg.pitch, s.pg.P, s.pg.rows});
       if (tid == 0) {
         const Decoded d = decode_key(keys[0], s.p, a.lam);
         if (!(si == ctrl->skip_stream && b == ctrl->skip_block))
