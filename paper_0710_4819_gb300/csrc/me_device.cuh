@@ -16,9 +16,9 @@ constexpr unsigned long long kNoKey = ~0ull;
 // four pixels at a time).  One instruction of the integer pipe at 16 lanes per
 // clock per SM sub-partition on sm_103a.
 __device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
+  // the accumulator is one read-write operand, so it can stay in one register
+  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(c) : "r"(a), "r"(b));
+  return c;
 }
 
 // Bits of the signed Exp-Golomb code of one MV component: 1 for 0, else
