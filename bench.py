@@ -119,7 +119,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ distributed
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend: str = "nccl"):
+    """Replicas only: one process per GPU (RANK / WORLD_SIZE / LOCAL_RANK from
+    the launcher); the ranks meet only at the timing barrier and the
+    max-over-ranks reduction.  `backend` "gloo" runs the same logic on CPU."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -127,10 +130,16 @@ def dist_setup(n_gpus):
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
         pg = dist
     return rank, world, local, pg
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank times an independent synthetic sequence of its own."""
+    return 2026 + rank
 
 
 def barrier(pg):
@@ -142,7 +151,8 @@ def max_over_ranks(pg, v: float) -> float:
     if pg is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
@@ -330,7 +340,7 @@ def main():
     import numpy as np
     import synth
 
-    frames_np = synth.config_sequence("1080p", seed=2026 + rank, n_frames=args.frames)
+    frames_np = synth.config_sequence("1080p", seed=replica_seed(rank), n_frames=args.frames)
     pairs = frames_np.shape[0] - 1
 
     if args.impl == "reference":

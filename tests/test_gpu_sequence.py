@@ -109,3 +109,39 @@ def test_sequence_argument_errors(me):
     with pytest.raises(me.MeError) as e:
         me.me_acbm_sequence(f[:3, :, :30].contiguous(), 16, 16, 4, 0, me.params())
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("env,n", [({"ME_SEQ_S": "2"}, 6), ({"ME_SEQ_S": "3"}, 7),
+                                   ({"ME_SEQ_T": "8"}, 8), ({"ME_SEQ_T": "11"}, 9),
+                                   ({"ME_SEQ_T": "16", "ME_SEQ_S": "2"}, 10)])
+def test_acbm_sequence_tile_options_match_chained_oracle(me, orc, env, n):
+    """The sequence plan's tuning options give the same bytes: full searches
+    split over S CTAs by columns (merged by an atomic minimum on the packed
+    key, the last slice publishing) and other run lengths.  Each case uses
+    its own sequence length, so it gets a plan of its own."""
+    import os
+    import torch
+    seq = synth.config_sequence("cif", seed=60 + n, n_frames=n)
+    lam = orc.lambda_q8(34)
+    saved = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        r = me.me_acbm_sequence(torch.from_numpy(seq).cuda(), 16, 16, 20, lam, me.params(qp=34))
+        me.me_acbm_sequence_status(seq.shape[2], seq.shape[1], 16, 16, 20, n - 1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    prev = None
+    fs = 0
+    for k in range(n - 1):
+        mv, J, mask, sad, load = orc.acbm(seq[k + 1], seq[k], 16, 16, 20, lam, orc.params(qp=34), prev)
+        prev = mv
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), (env, k, "mv")
+        assert np.array_equal(_u32(r.J[k]), J), (env, k, "J")
+        assert np.array_equal(r.mask[k].cpu().numpy(), mask), (env, k, "mask")
+        assert np.array_equal(_u32(r.load[k]), load), (env, k, "load")
+        fs += int(mask.sum())
+    assert fs > 0          # the searches (and their slices) ran
