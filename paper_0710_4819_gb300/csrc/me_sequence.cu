@@ -517,9 +517,10 @@ static int build_seq_plan(SeqPlan* pl) {
   }
   ME_SEQ_NMT(X)
 #undef X
-  // half the CTAs run PBM warps, half the full searches: two per SM
-  pl->grid = 2 * nsm;
+  // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
+  // the 8-row build at 85 registers measured 30 % slower.)
   if (per_sm < 2) st = ME_ERR_CUDA;
+  pl->grid = 2 * nsm;
   ME_CUDA(cudaEventCreateWithFlags(&pl->last, cudaEventDisableTiming));
   return st;
 }
