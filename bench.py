@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve"],
                     help="1080p: the default line; batch64 / serve: the multi-stream forms")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
-    ap.add_argument("--seconds", type=float, default=4.0, help="serve: arrival window")
+    ap.add_argument("--seconds", type=float, default=10.0, help="serve: arrival window")
     return ap.parse_args()
 
 
@@ -521,7 +521,12 @@ def main():
                  "frames_per_s": 1e3 / acbm_mean,
                  "cand_sads_per_s": acbm_load / pairs / (acbm_mean * 1e-3),
                  "ms_per_frame": acbm_mean, "fullsearch_fraction": fs_frac,
-                 "avg_positions_per_block": acbm_load / (pairs * NBLK)},
+                 "avg_positions_per_block": acbm_load / (pairs * NBLK),
+                 # algorithmic bytes: the current frame, N*M reference bytes per
+                 # evaluated position, and the 12-byte outputs per block; their
+                 # true bound is the latency of the block dependency chain
+                 "algorithmic_gb_per_s": (W * H_PAD + acbm_load / pairs * N * M + 12 * NBLK)
+                                         / (acbm_mean * 1e-3) / 1e9},
         "per_pair": {"form": "me_fsbm + me_acbm (wave launches, graph-replayed) per pair",
                      "frames_per_s": 1e3 / statistics.mean(pair_ms),
                      "acbm_ms": statistics.mean(pair_acbm_ms), "fsbm_ms": statistics.mean(pair_fsbm_ms),

@@ -82,6 +82,9 @@ def _bind(lib):
                                        i16p, i16p, prm_p, i32p, c_int, i16p, u32p, u8p,
                                        u32p, u32p]
     lib.oracle_acbm_blocks.restype = c_int
+    lib.oracle_halfpel.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                   i16p, i16p, u32p, u32p]
+    lib.oracle_halfpel.restype = c_int
     return lib
 
 
@@ -185,6 +188,25 @@ def fsbm(cur, ref, N: int, M: int, p: int, lam_q8: int, nthreads: int = 1):
     _check(_load().oracle_fsbm(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N, M,
                                p, lam_q8, _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
                                _ptr(sad, ctypes.c_uint32), nthreads), "oracle_fsbm")
+    return mv, J, sad
+
+
+def halfpel(cur, ref, N: int, M: int, p: int, lam_q8: int, mv_int):
+    """Half-pel refinement of an integer vector field (Sec. 2.2 / 2.3).
+    Returns (mv [BH,BW,2] int16 in half-pel units, J [BH,BW] u32, sad [BH,BW] u32)."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    if ref.shape != cur.shape:
+        raise ValueError("cur and ref differ in shape")
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    mv_int = np.ascontiguousarray(mv_int, dtype=np.int16).reshape(BH, BW, 2)
+    mv = np.zeros((BH, BW, 2), np.int16)
+    J = np.zeros((BH, BW), np.uint32)
+    sad = np.zeros((BH, BW), np.uint32)
+    _check(_load().oracle_halfpel(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N,
+                                  M, p, lam_q8, _ptr(mv_int, ctypes.c_int16),
+                                  _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                                  _ptr(sad, ctypes.c_uint32)), "oracle_halfpel")
     return mv, J, sad
 
 

@@ -419,3 +419,93 @@ int oracle_acbm_blocks(const uint8_t *cur, const uint8_t *ref, int W, int H, int
     free(seen);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Half-pel refinement (Sec. 2.2: the best predictor "is normally refined to
+ * half-pel accuracy"; Sec. 2.3: the full search count 969 = 961 integer +
+ * 8 half-pel positions).  For every block, starting from its integer vector
+ * (mvx, mvy), the 9 positions (2*mvx + dx, 2*mvy + dy), dx, dy in {-1,0,1},
+ * in half-pel units, each component clipped to [-2p, 2p]; repeated positions
+ * are evaluated once.  Readings (the paper gives none of these details):
+ *   - the reference at a half-pel position is the bilinear average of the
+ *     integer pixels around it, rounded half up, as in H.263 (the encoder the
+ *     paper's experiments use): a half step in x averages A and B with
+ *     (A + B + 1) >> 1, in y A and C likewise, in both (A+B+C+D+2) >> 2;
+ *     integer pixels outside the frame take the nearest edge pixel;
+ *   - the cost is J_q8 = 256*SAD + lambda_q8*(L(hx) + L(hy)) with L the
+ *     signed Exp-Golomb length of the component in half-pel units;
+ *   - ties as for integer positions on the half-pel grid: lowest J, then
+ *     smallest |hx|+|hy|, then smaller hy, then smaller hx.
+ * Output: the best position in half-pel units, its J_q8 and its SAD.
+ * ------------------------------------------------------------------------ */
+
+/* Reference value at half-pel position (X*2 + hx, Y*2 + hy) / 2 of the pixel
+ * (X, Y) of the block, i.e. at (X + hx/2, Y + hy/2). */
+static int halfpel_ref(const uint8_t *ref, int W, int H, int X, int Y, int hx, int hy)
+{
+    /* floor division by 2 and the half-step flags */
+    int ax = hx >= 0 ? hx / 2 : -((-hx + 1) / 2);
+    int ay = hy >= 0 ? hy / 2 : -((-hy + 1) / 2);
+    int fx = hx - 2 * ax, fy = hy - 2 * ay;
+    int x0 = clampi(X + ax, 0, W - 1), x1 = clampi(X + ax + 1, 0, W - 1);
+    int y0 = clampi(Y + ay, 0, H - 1), y1 = clampi(Y + ay + 1, 0, H - 1);
+    int A = ref[(size_t)y0 * W + x0];
+    if (!fx && !fy) return A;
+    int B = ref[(size_t)y0 * W + x1];
+    int C = ref[(size_t)y1 * W + x0];
+    if (fx && !fy) return (A + B + 1) >> 1;
+    if (!fx && fy) return (A + C + 1) >> 1;
+    int D = ref[(size_t)y1 * W + x1];
+    return (A + B + C + D + 2) >> 2;
+}
+
+static uint32_t halfpel_sad(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M,
+                            int x0, int y0, int hx, int hy)
+{
+    uint32_t s = 0;
+    for (int j = 0; j < M; j++)
+        for (int i = 0; i < N; i++) {
+            int a = cur[(size_t)(y0 + j) * W + (x0 + i)];
+            s += (uint32_t)absi(a - halfpel_ref(ref, W, H, x0 + i, y0 + j, hx, hy));
+        }
+    return s;
+}
+
+int oracle_halfpel(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+                   uint32_t lambda_q8, const int16_t *mv_int, int16_t *mv_half_out,
+                   uint32_t *J_out, uint32_t *sad_out)
+{
+    if (!cur || !ref || !mv_int || !mv_half_out || !J_out) return OR_ERR_ARG;
+    int st = check_shape(W, H, N, M, p, lambda_q8);
+    if (st) return st;
+    int BW = W / N, BH = H / M;
+    for (int by = 0; by < BH; by++)
+        for (int bx = 0; bx < BW; bx++) {
+            int b = by * BW + bx;
+            int cx = 2 * mv_int[2 * b], cy = 2 * mv_int[2 * b + 1];
+            int seen[9][2], nseen = 0;
+            int bestx = 0, besty = 0, have = 0;
+            uint32_t bestJ = 0, bestS = 0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int hx = clampi(cx + dx, -2 * p, 2 * p), hy = clampi(cy + dy, -2 * p, 2 * p);
+                    int dup = 0;
+                    for (int k = 0; k < nseen; k++)
+                        if (seen[k][0] == hx && seen[k][1] == hy) dup = 1;
+                    if (dup) continue;
+                    seen[nseen][0] = hx;
+                    seen[nseen][1] = hy;
+                    nseen++;
+                    uint32_t s = halfpel_sad(cur, ref, W, H, N, M, bx * N, by * M, hx, hy);
+                    uint32_t J = 256u * s + lambda_q8 * (uint32_t)rate_bits(hx, hy);
+                    if (!have || better(J, hx, hy, bestJ, bestx, besty)) {
+                        bestJ = J; bestS = s; bestx = hx; besty = hy; have = 1;
+                    }
+                }
+            mv_half_out[2 * b] = (int16_t)bestx;
+            mv_half_out[2 * b + 1] = (int16_t)besty;
+            J_out[b] = bestJ;
+            if (sad_out) sad_out[b] = bestS;
+        }
+    return OR_OK;
+}

@@ -62,6 +62,23 @@ MUTANTS = {
         "        *mvx_o = s.bmx; *mvy_o = s.bmy; *J_o = s.bJ; *sad_o = s.bS;"),
     "fallback load not (2p+1)^2": (
         "        *load_o = (uint32_t)((2 * p + 1) * (2 * p + 1));", "        *load_o = (uint32_t)s.count;"),
+    "half-pel average not rounded": (
+        "    if (fx && !fy) return (A + B + 1) >> 1;", "    if (fx && !fy) return (A + B) >> 1;"),
+    "half-pel diagonal rounding off": (
+        "    return (A + B + C + D + 2) >> 2;", "    return (A + B + C + D + 1) >> 2;"),
+    "half-pel vertical uses the wrong neighbour": (
+        "    if (!fx && fy) return (A + C + 1) >> 1;", "    if (!fx && fy) return (A + B + 1) >> 1;"),
+    "half-pel floor division truncates negatives": (
+        "    int ax = hx >= 0 ? hx / 2 : -((-hx + 1) / 2);", "    int ax = hx / 2;"),
+    "half-pel rate in integer units": (
+        "                    uint32_t J = 256u * s + lambda_q8 * (uint32_t)rate_bits(hx, hy);",
+        "                    uint32_t J = 256u * s + lambda_q8 * (uint32_t)rate_bits(hx / 2, hy / 2);"),
+    "half-pel clip at p instead of 2p": (
+        "                    int hx = clampi(cx + dx, -2 * p, 2 * p), hy = clampi(cy + dy, -2 * p, 2 * p);",
+        "                    int hx = clampi(cx + dx, -p, p), hy = clampi(cy + dy, -p, p);"),
+    "half-pel centre not doubled": (
+        "            int cx = 2 * mv_int[2 * b], cy = 2 * mv_int[2 * b + 1];",
+        "            int cx = mv_int[2 * b], cy = mv_int[2 * b + 1];"),
 }
 
 
@@ -87,6 +104,11 @@ def _pin_suite(v):
         for dy in (-1, 0, 1):
             yield lambda dx=dx, dy=dy: pins.test_pbm_temporal_predictors(v, (dx, dy), True)
     yield lambda: pins.test_acbm_invariants_on_a_sequence(v)
+    for args in [(48, 32, 16, 16, 4), (24, 16, 4, 8, 2)]:
+        yield lambda args=args: pins.test_halfpel_matches_brute_force(v, *args)
+    for hx0, hy0 in [(3, -1), (-1, 2), (1, 1), (-3, -3)]:
+        yield lambda hx0=hx0, hy0=hy0: pins.test_halfpel_recovers_exact_half_pel_shift(v, hx0, hy0)
+    yield lambda: pins.test_halfpel_flat_frame_keeps_the_cheapest_position(v)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

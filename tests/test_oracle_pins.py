@@ -414,3 +414,111 @@ def test_pbm_load_counts_distinct_positions(orc):
     far[0, 0] = (20, 0)
     _, _, _, _, load1 = orc.acbm(flat, flat, 16, 16, 8, 0, orc.params(refine=0), far)
     assert np.all(load1 == 2)                                  # (0,0) and (8,0)
+
+
+# ----------------------------------------------------------------- half-pel refinement
+def brute_halfpel_pred(ref, N, M, x0, y0, hx, hy, pad):
+    """Bilinear half-pel prediction of one block from an edge-padded copy of
+    the reference (H.263 rounding), by whole-array slices: an implementation
+    independent of the oracle's per-pixel loop."""
+    ax, fx = hx >> 1, hx & 1          # floor division by 2 and the half flag
+    ay, fy = hy >> 1, hy & 1
+    r = np.pad(ref.astype(np.int64), pad, mode="edge")
+    Y, X = y0 + ay + pad, x0 + ax + pad
+    A = r[Y:Y + M, X:X + N]
+    B = r[Y:Y + M, X + 1:X + 1 + N]
+    C = r[Y + 1:Y + 1 + M, X:X + N]
+    D = r[Y + 1:Y + 1 + M, X + 1:X + 1 + N]
+    if fx and fy:
+        return (A + B + C + D + 2) >> 2
+    if fx:
+        return (A + B + 1) >> 1
+    if fy:
+        return (A + C + 1) >> 1
+    return A
+
+
+def brute_halfpel(cur, ref, N, M, p, lam, mv_int):
+    """Every block: the distinct clipped positions 2*mv + (dx, dy), cost
+    256*SAD + lam*(bits(hx)+bits(hy)) with bits from the constructive
+    Exp-Golomb encoder, lexicographic argmin (J, |h|_1, hy, hx)."""
+    H, W = cur.shape
+    BH, BW = H // M, W // N
+    out_mv = np.zeros((BH, BW, 2), np.int64)
+    out_J = np.zeros((BH, BW), np.int64)
+    out_s = np.zeros((BH, BW), np.int64)
+    pad = 2 * p + 4
+    for by in range(BH):
+        for bx in range(BW):
+            cx, cy = 2 * int(mv_int[by, bx, 0]), 2 * int(mv_int[by, bx, 1])
+            cands = {(min(max(cx + dx, -2 * p), 2 * p), min(max(cy + dy, -2 * p), 2 * p))
+                     for dy in (-1, 0, 1) for dx in (-1, 0, 1)}
+            best = None
+            for hx, hy in cands:
+                pred = brute_halfpel_pred(ref, N, M, bx * N, by * M, hx, hy, pad)
+                s = int(np.abs(cur[by * M:(by + 1) * M, bx * N:(bx + 1) * N].astype(np.int64) - pred).sum())
+                J = 256 * s + lam * (len(eg_encode_signed(hx)) + len(eg_encode_signed(hy)))
+                k = (J, abs(hx) + abs(hy), hy, hx)
+                if best is None or k < best[0]:
+                    best = (k, s)
+            (J, _, hy, hx), s = best
+            out_mv[by, bx] = (hx, hy)
+            out_J[by, bx] = J
+            out_s[by, bx] = s
+    return out_mv, out_J, out_s
+
+
+@pytest.mark.parametrize("W,H,N,M,p", [(48, 32, 16, 16, 4), (32, 32, 8, 8, 3), (24, 16, 4, 8, 2)])
+def test_halfpel_matches_brute_force(orc, W, H, N, M, p):
+    rng = np.random.default_rng(W * 7 + p)
+    ref = synth.texture(rng, W, H)
+    cur = np.clip(np.roll(ref, (1, -1), axis=(0, 1)).astype(int) + rng.integers(-6, 7, ref.shape),
+                  0, 255).astype(np.uint8)
+    BH, BW = H // M, W // N
+    # integer fields: random, and the window corners (clipping at +-2p)
+    fields = [rng.integers(-p, p + 1, (BH, BW, 2)).astype(np.int16),
+              np.tile(np.array([p, -p], np.int16), (BH, BW, 1)),
+              np.tile(np.array([-p, p], np.int16), (BH, BW, 1))]
+    for lam in (0, 6595):
+        for f in fields:
+            mv, J, s = orc.halfpel(cur, ref, N, M, p, lam, f)
+            bmv, bJ, bs = brute_halfpel(cur, ref, N, M, p, lam, f)
+            assert np.array_equal(mv, bmv) and np.array_equal(J, bJ) and np.array_equal(s, bs)
+            assert np.all(np.abs(mv.astype(int)) <= 2 * p)
+
+
+@pytest.mark.parametrize("hx0,hy0", [(3, -1), (-1, 2), (1, 1), (-3, -3)])
+def test_halfpel_recovers_exact_half_pel_shift(orc, hx0, hy0):
+    """cur is the reference interpolated at a known half-pel offset (away
+    from the frame edges): with lambda = 0 the refinement around the
+    integer vector next to it finds SAD 0 there."""
+    rng = np.random.default_rng(5)
+    W = H = 48
+    N = M = 16
+    p = 4
+    ref = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    cur = ref.copy()
+    by = bx = 1            # the centre block, well inside the frame
+    cur[by * M:(by + 1) * M, bx * N:(bx + 1) * N] = brute_halfpel_pred(
+        ref, N, M, bx * N, by * M, hx0, hy0, 2 * p + 4)
+    mv_int = np.zeros((H // M, W // N, 2), np.int16)
+    mv_int[by, bx] = ((hx0 + (hx0 > 0)) // 2, (hy0 + (hy0 > 0)) // 2)   # hx0 within +-1 of 2*mv
+    assert all(abs(2 * int(mv_int[by, bx, i]) - h) <= 1 for i, h in enumerate((hx0, hy0)))
+    mv, J, s = orc.halfpel(cur, ref, N, M, p, 0, mv_int)
+    assert tuple(mv[by, bx]) == (hx0, hy0) and s[by, bx] == 0 and J[by, bx] == 0
+
+
+def test_halfpel_flat_frame_keeps_the_cheapest_position(orc):
+    """Constant frames: every position has SAD 0, so the rate decides; the
+    zero vector has the shortest code (1+1 bits); around (1, 0) the nearest
+    cheapest is (1, 0) in half units (3+1 bits), not (2, 0)."""
+    ref = np.full((32, 32), 77, np.uint8)
+    cur = ref.copy()
+    z = np.zeros((2, 2, 2), np.int16)
+    mv, J, s = orc.halfpel(cur, ref, 16, 16, 3, 6595, z)
+    assert np.all(mv == 0) and np.all(J == 6595 * 2) and np.all(s == 0)
+    one = np.zeros((2, 2, 2), np.int16)
+    one[..., 0] = 1
+    mv, J, s = orc.halfpel(cur, ref, 16, 16, 3, 6595, one)
+    assert np.all(mv[..., 0] == 1) and np.all(mv[..., 1] == 0)
+    assert np.all(J == 6595 * (3 + 1))
