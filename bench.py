@@ -424,6 +424,10 @@ def main():
     me.me_acbm_sequence_status(W, H_PAD, N, M, P, pairs)
     seq_out = [x.clone() for x in a_out + f_out]
     acbm_load = int(a_load.to(torch.int64).sum().item())
+    # positions PBM evaluated: the load of blocks that passed, the 22-position
+    # bound (14 predictors + 8 ring) for blocks that went on to a full search
+    pbm_positions = int(torch.where(a_mask.bool(), torch.full_like(a_load, 22),
+                                    a_load).to(torch.int64).sum().item())
     fs_frac = float(a_mask.float().mean().item())
 
     total_ms = max_over_ranks(pg, sum(step_ms))
@@ -455,6 +459,24 @@ def main():
     pair_fsbm_ms = [e[0].elapsed_time(e[1]) for e in ep]
     pair_acbm_ms = [e[1].elapsed_time(e[2]) for e in ep]
     identical = all(torch.equal(x, y) for x, y in zip(seq_out, a_out + f_out))
+
+    # half-pel refinement of the full-search field (Sec. 2.2/2.3; next to the
+    # step, not part of it): all pairs in one launch
+    h_out = (torch.empty_like(f_mv), torch.empty_like(f_J), torch.empty_like(f_sad))
+    for _ in range(3):
+        me.me_halfpel_sequence(frames, N, M, P, lam, f_mv, out=h_out)
+    torch.cuda.synchronize()
+    hp_ms = []
+    for _ in range(10):
+        flush.fill_(1)
+        eh0, eh1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        eh0.record(stream)
+        me.me_halfpel_sequence(frames, N, M, P, lam, f_mv, out=h_out)
+        eh1.record(stream)
+        torch.cuda.synchronize()
+        hp_ms.append(eh0.elapsed_time(eh1))
+    hp_frame_ms = statistics.median(hp_ms) / pairs
 
     # kernel-only FSBM timing (the SAD engine) for the roofline, same stream
     reps = 20
@@ -522,11 +544,17 @@ def main():
                  "cand_sads_per_s": acbm_load / pairs / (acbm_mean * 1e-3),
                  "ms_per_frame": acbm_mean, "fullsearch_fraction": fs_frac,
                  "avg_positions_per_block": acbm_load / (pairs * NBLK),
-                 # algorithmic bytes: the current frame, N*M reference bytes per
-                 # evaluated position, and the 12-byte outputs per block; their
-                 # true bound is the latency of the block dependency chain
-                 "algorithmic_gb_per_s": (W * H_PAD + acbm_load / pairs * N * M + 12 * NBLK)
-                                         / (acbm_mean * 1e-3) / 1e9},
+                 # PBM stages' algorithmic bytes: the current frame, N*M
+                 # reference bytes per position PBM evaluated, 12-byte outputs
+                 # per block (the full searches read their windows from shared
+                 # memory); the true bound is the latency of the dependency chain
+                 "pbm_algorithmic_gb_per_s": (W * H_PAD + pbm_positions / pairs * N * M + 12 * NBLK)
+                                             / (acbm_mean * 1e-3) / 1e9},
+        "halfpel": {"form": "me_halfpel_sequence on the full-search field (one launch)",
+                    "ms_per_frame": hp_frame_ms, "frames_per_s": 1e3 / hp_frame_ms,
+                    "positions_per_block": 9,
+                    # algorithmic bytes: each frame read as current and as reference
+                    "algorithmic_gb_per_s": 2 * W * H_PAD / (hp_frame_ms * 1e-3) / 1e9},
         "per_pair": {"form": "me_fsbm + me_acbm (wave launches, graph-replayed) per pair",
                      "frames_per_s": 1e3 / statistics.mean(pair_ms),
                      "acbm_ms": statistics.mean(pair_acbm_ms), "fsbm_ms": statistics.mean(pair_fsbm_ms),

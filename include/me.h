@@ -162,6 +162,33 @@ int me_acbm_sequence(const uint8_t *const *frames, int K, int W, int H, int N, i
                      uint32_t *sad_out, uint32_t *load_out, me_stream_t stream);
 int me_acbm_sequence_status(int W, int H, int N, int M, int p, int K, me_stream_t stream);
 
+/* ------------------------------------------------------------ half-pel */
+
+/* Half-pel refinement of an integer vector field (Sec. 2.2: the best vector
+ * is normally refined to half-pel accuracy; Sec. 2.3: the 8 half-pel
+ * positions around it).  For every block, with (mvx, mvy) = mv_int clipped to
+ * [-p, p]: the positions (2*mvx + dx, 2*mvy + dy), dx, dy in {-1,0,1}, in
+ * half-pel units, each component clipped to [-2p, 2p], repeated ones once.
+ * The reference at a half-pel position is the bilinear average of the
+ * integer pixels around it, H.263 rounding ((A+B+1)>>1 along one axis,
+ * (A+B+C+D+2)>>2 along both), pixels outside the frame at the nearest edge.
+ * Cost J_q8 = 256*SAD + lambda_q8*(L(hx)+L(hy)), L = me_mv_bits in half-pel
+ * units; ties: lowest J, then |hx|+|hy|, then hy, then hx.
+ * mv_int: device [BH][BW][2] int16 (e.g. the output of me_fsbm or me_acbm);
+ * mv_half_out: device [BH][BW][2] int16 in half-pel units; J_out, sad_out
+ * (nullable): device [BH][BW].  Same argument checks as me_fsbm; no scratch
+ * memory; asynchronous on `stream`. */
+int me_halfpel(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+               uint32_t lambda_q8, const int16_t *mv_int, int16_t *mv_half_out, uint32_t *J_out,
+               uint32_t *sad_out, me_stream_t stream);
+
+/* me_halfpel for K consecutive frame pairs in one launch: frames is a host
+ * array of K+1 device frame pointers (pair k: reference frames[k], current
+ * frames[k+1]); mv_int and the outputs are [K][BH][BW] (x2 for vectors). */
+int me_halfpel_sequence(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
+                        uint32_t lambda_q8, const int16_t *mv_int, int16_t *mv_half_out,
+                        uint32_t *J_out, uint32_t *sad_out, me_stream_t stream);
+
 /* ----------------------------------------------------------------- batches */
 
 /* Many independent streams of uneven size in one launch per step (an

@@ -426,7 +426,8 @@ int oracle_acbm_blocks(const uint8_t *cur, const uint8_t *ref, int W, int H, int
  * 8 half-pel positions).  For every block, starting from its integer vector
  * (mvx, mvy), the 9 positions (2*mvx + dx, 2*mvy + dy), dx, dy in {-1,0,1},
  * in half-pel units, each component clipped to [-2p, 2p]; repeated positions
- * are evaluated once.  Readings (the paper gives none of these details):
+ * are evaluated once (the integer vector itself is first clipped to
+ * [-p, p]).  Readings (the paper gives none of these details):
  *   - the reference at a half-pel position is the bilinear average of the
  *     integer pixels around it, rounded half up, as in H.263 (the encoder the
  *     paper's experiments use): a half step in x averages A and B with
@@ -482,7 +483,8 @@ int oracle_halfpel(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, 
     for (int by = 0; by < BH; by++)
         for (int bx = 0; bx < BW; bx++) {
             int b = by * BW + bx;
-            int cx = 2 * mv_int[2 * b], cy = 2 * mv_int[2 * b + 1];
+            /* the integer vector is first taken inside the window */
+            int cx = 2 * clampi(mv_int[2 * b], -p, p), cy = 2 * clampi(mv_int[2 * b + 1], -p, p);
             int seen[9][2], nseen = 0;
             int bestx = 0, besty = 0, have = 0;
             uint32_t bestJ = 0, bestS = 0;

@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
-    "me_fsbm", "me_acbm", "me_sad_peak", "Batch", "Server", "STATUS",
+    "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_peak", "Batch", "Server",
+    "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -98,6 +99,10 @@ def load_library(build_if_missing: bool = True):
                                  ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp], c_int),
             "me_fsbm_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                   u32, vp, vp, vp, vp], c_int),
+            "me_halfpel": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp, vp],
+                           c_int),
+            "me_halfpel_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
+                                     u32, vp, vp, vp, vp, vp], c_int),
             "me_acbm_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                   u32, vp, ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp],
                                  c_int),
@@ -295,6 +300,38 @@ def me_fsbm_sequence(frames, N: int, M: int, p: int, lambda_q8: int, out=None, s
     mv, J, sad = out
     _check(load_library().me_fsbm_sequence(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(mv), _ptr(J),
                                            _ptr(sad), _stream_ptr(stream)), "me_fsbm_sequence")
+    return FsbmResult(mv, J, sad)
+
+
+def me_halfpel(cur, ref, N: int, M: int, p: int, lambda_q8: int, mv_int, out=None,
+               stream=None) -> FsbmResult:
+    """Half-pel refinement (Sec. 2.2 / 2.3) of an integer field mv_int
+    (int16 [BH,BW,2] on the device).  Outputs: mv int16 [BH,BW,2] in half-pel
+    units, J and SAD as int32 tensors holding the uint32 values."""
+    W, H = _frame_args(cur, ref)
+    mv, J, sad = out if out is not None else _outs(H, W, N, M, cur.device)
+    _check(load_library().me_halfpel(_ptr(cur), _ptr(ref), W, H, N, M, p, int(lambda_q8),
+                                      _ptr(mv_int), _ptr(mv), _ptr(J), _ptr(sad),
+                                      _stream_ptr(stream)), "me_halfpel")
+    return FsbmResult(mv, J, sad)
+
+
+def me_halfpel_sequence(frames, N: int, M: int, p: int, lambda_q8: int, mv_int, out=None,
+                        stream=None) -> FsbmResult:
+    """me_halfpel for K consecutive pairs in one launch; mv_int and the
+    outputs are [K, BH, BW, ...]."""
+    torch = _torch()
+    arr, K, W, H = _frame_ptrs(frames)
+    dev = frames[0].device
+    if out is None:
+        BH, BW = H // M, W // N
+        out = (torch.empty((K, BH, BW, 2), dtype=torch.int16, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev))
+    mv, J, sad = out
+    _check(load_library().me_halfpel_sequence(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(mv_int),
+                                              _ptr(mv), _ptr(J), _ptr(sad), _stream_ptr(stream)),
+           "me_halfpel_sequence")
     return FsbmResult(mv, J, sad)
 
 

@@ -86,4 +86,16 @@ def test_argument_errors_before_launch(lib):
                        None, None, None) == 1
     assert lib.me_acbm(fake, fake, 64, 64, 16, 16, 4, 0, None, None, fake, fake, fake,
                        None, None, None) == 1
+    # half-pel refinement: same frame checks, and the integer field is required
+    assert lib.me_halfpel(fake, fake, 64, 64, 12, 16, 4, 0, fake, fake, fake, None, None) == 1
+    assert lib.me_halfpel(fake, fake, 60, 64, 16, 16, 4, 0, fake, fake, fake, None, None) == 2
+    assert lib.me_halfpel(fake, fake, 64, 64, 16, 16, 4, 0, None, fake, fake, None, None) == 1
+    frames = (vp * 3)(fake, fake, fake)
+    assert lib.me_halfpel_sequence(frames, 0, 64, 64, 16, 16, 4, 0, fake, fake, fake, None,
+                                   None) == 1
+    assert lib.me_halfpel_sequence(frames, 65, 64, 64, 16, 16, 4, 0, fake, fake, fake, None,
+                                   None) == 1
+    frames = (vp * 3)(fake, None, fake)
+    assert lib.me_halfpel_sequence(frames, 2, 64, 64, 16, 16, 4, 0, fake, fake, fake, None,
+                                   None) == 1
     assert lib.me_status_string(2).decode().startswith("frame size")

@@ -77,8 +77,8 @@ MUTANTS = {
         "                    int hx = clampi(cx + dx, -2 * p, 2 * p), hy = clampi(cy + dy, -2 * p, 2 * p);",
         "                    int hx = clampi(cx + dx, -p, p), hy = clampi(cy + dy, -p, p);"),
     "half-pel centre not doubled": (
-        "            int cx = 2 * mv_int[2 * b], cy = 2 * mv_int[2 * b + 1];",
-        "            int cx = mv_int[2 * b], cy = mv_int[2 * b + 1];"),
+        "            int cx = 2 * clampi(mv_int[2 * b], -p, p), cy = 2 * clampi(mv_int[2 * b + 1], -p, p);",
+        "            int cx = clampi(mv_int[2 * b], -p, p), cy = clampi(mv_int[2 * b + 1], -p, p);"),
 }
 
 

@@ -450,7 +450,8 @@ def brute_halfpel(cur, ref, N, M, p, lam, mv_int):
     pad = 2 * p + 4
     for by in range(BH):
         for bx in range(BW):
-            cx, cy = 2 * int(mv_int[by, bx, 0]), 2 * int(mv_int[by, bx, 1])
+            cx = 2 * min(max(int(mv_int[by, bx, 0]), -p), p)
+            cy = 2 * min(max(int(mv_int[by, bx, 1]), -p), p)
             cands = {(min(max(cx + dx, -2 * p), 2 * p), min(max(cy + dy, -2 * p), 2 * p))
                      for dy in (-1, 0, 1) for dx in (-1, 0, 1)}
             best = None
@@ -478,7 +479,8 @@ def test_halfpel_matches_brute_force(orc, W, H, N, M, p):
     # integer fields: random, and the window corners (clipping at +-2p)
     fields = [rng.integers(-p, p + 1, (BH, BW, 2)).astype(np.int16),
               np.tile(np.array([p, -p], np.int16), (BH, BW, 1)),
-              np.tile(np.array([-p, p], np.int16), (BH, BW, 1))]
+              np.tile(np.array([-p, p], np.int16), (BH, BW, 1)),
+              rng.integers(-p - 5, p + 6, (BH, BW, 2)).astype(np.int16)]   # outside: clipped
     for lam in (0, 6595):
         for f in fields:
             mv, J, s = orc.halfpel(cur, ref, N, M, p, lam, f)
