@@ -85,6 +85,8 @@ def _bind(lib):
     lib.oracle_halfpel.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
                                    i16p, i16p, u32p, u32p]
     lib.oracle_halfpel.restype = c_int
+    lib.oracle_sad_deviation.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, u32p, u32p]
+    lib.oracle_sad_deviation.restype = c_int
     return lib
 
 
@@ -208,6 +210,21 @@ def halfpel(cur, ref, N: int, M: int, p: int, lam_q8: int, mv_int):
                                   _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
                                   _ptr(sad, ctypes.c_uint32)), "oracle_halfpel")
     return mv, J, sad
+
+
+def sad_deviation(cur, ref, N: int, M: int, p: int):
+    """SAD_min and SAD_deviation of every block (Sec. 3.1), each [BH,BW] u32."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    if ref.shape != cur.shape:
+        raise ValueError("cur and ref differ in shape")
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    mn = np.zeros((BH, BW), np.uint32)
+    dev = np.zeros((BH, BW), np.uint32)
+    _check(_load().oracle_sad_deviation(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H,
+                                        N, M, p, _ptr(mn, ctypes.c_uint32),
+                                        _ptr(dev, ctypes.c_uint32)), "oracle_sad_deviation")
+    return mn, dev
 
 
 def fsbm_blocks(cur, ref, N: int, M: int, p: int, lam_q8: int, blocks, nthreads: int = 1):

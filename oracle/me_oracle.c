@@ -21,6 +21,9 @@
  *                        neighbourhood (Fig. 2), keep the best, refine.
  *   Sec. 2.3             FSBM: all (2p+1)^2 integer positions.
  *   Sec. 3.1, eq. Intra_SAD   sum |p_t(i,j) - mu|, mu = block mean.
+ *   Sec. 3.1, eq. SAD_deviation  sum over the evaluated positions of
+ *                        |SAD(u,v) - SAD_min|, SAD_min the least SAD among
+ *                        them (here: the (2p+1)^2 positions of the full search).
  *   Sec. 3.2             ACBM: Intra_SAD, then PBM, then
  *                        cond. 1  Intra_SAD + SAD_PBM < alpha + beta*Qp^2
  *                        cond. 2  SAD_PBM < gamma * Intra_SAD
@@ -509,5 +512,39 @@ int oracle_halfpel(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, 
             J_out[b] = bestJ;
             if (sad_out) sad_out[b] = bestS;
         }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * SAD_deviation (Sec. 3.1): for every block, over all (2p+1)^2 positions of
+ * the full search, SAD_deviation = sum_{u,v} |SAD(u,v) - SAD_min| with
+ * SAD_min the smallest SAD of the window (a SAD minimum, not the J one).
+ * Written out term by term.  Outputs per block: SAD_min and SAD_deviation.
+ * ------------------------------------------------------------------------ */
+int oracle_sad_deviation(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M,
+                         int p, uint32_t *sad_min_out, uint32_t *sad_dev_out)
+{
+    if (!cur || !ref || !sad_min_out || !sad_dev_out) return OR_ERR_ARG;
+    int st = check_shape(W, H, N, M, p, 0);
+    if (st) return st;
+    int BW = W / N, BH = H / M, n = 2 * p + 1;
+    uint32_t *vol = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * n);
+    if (!vol) return OR_ERR_NOMEM;
+    for (int by = 0; by < BH; by++)
+        for (int bx = 0; bx < BW; bx++) {
+            uint32_t mn = 0;
+            for (int v = -p; v <= p; v++)
+                for (int u = -p; u <= p; u++) {
+                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);
+                    vol[(v + p) * n + (u + p)] = s;
+                    if ((u == -p && v == -p) || s < mn) mn = s;
+                }
+            uint64_t dev = 0;
+            for (int k = 0; k < n * n; k++)
+                dev += (uint64_t)(vol[k] > mn ? vol[k] - mn : mn - vol[k]);
+            sad_min_out[by * BW + bx] = mn;
+            sad_dev_out[by * BW + bx] = (uint32_t)dev;
+        }
+    free(vol);
     return OR_OK;
 }

@@ -17,6 +17,10 @@ Recipes (all frames uint8, row-major [H, W]):
   next frame takes the previous one and pulls every destination quadrant from
   a shift (dx, dy) drawn from U{-8..8}^2 (edge clamp), adds N(0, 2^2) noise,
   rounds and clamps.
+* ``global_motion_sequence`` (Sec. 3.1 set-up, default CIF): one original
+  frame (``contrast_texture``: a texture times a smooth contrast map that
+  runs from flat, on about a quarter of the frame, to full) and nine copies displaced by known distinct global
+  vectors from U{-8..8}^2 (edge clamp) plus N(0, 2^2) noise.
 * ``scene_sequence`` (CIF / 720p / 1080p / 4K): a textured background canvas
   panned by 1 px/frame, ``n_objects`` textured rectangles (sides U{32..96})
   moving at constant integer velocities from U{-vmax..vmax}^2 and painted in
@@ -32,7 +36,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = [
-    "texture", "quadrant_sequence", "scene_sequence", "random_frame", "shifted_copy",
+    "texture", "contrast_texture", "global_motion_sequence", "quadrant_sequence", "scene_sequence", "random_frame", "shifted_copy",
     "StreamSpec", "CONFIGS", "config_sequence", "batch_mix", "serving_mix",
 ]
 
@@ -110,6 +114,44 @@ def quadrant_sequence(seed: int, n_frames: int = 10, w: int = 176, h: int = 144,
             out[y_sl, x_sl] = prev[np.ix_(sy, sx)]
         frames[t] = _add_noise(rng, out, noise_sigma)
     return frames
+
+
+def contrast_texture(rng: np.random.Generator, w: int, h: int) -> np.ndarray:
+    """A texture whose local contrast varies smoothly from flat to full: the
+    texture's deviation from 128 times c(x, y)^2, where c is U[0,1] noise
+    blurred with sigma 12, min-max rescaled to [0, 1], then mapped by
+    max(0, (c - 0.3) / 0.7), so that about a quarter of the frame is flat."""
+    t = texture(rng, w, h).astype(np.float64)
+    c = rng.random((h, w))
+    c = _blur_1d(_blur_1d(c, 1, 12.0, 36), 0, 12.0, 36)
+    lo, hi = c.min(), c.max()
+    c = (c - lo) / (hi - lo) if hi > lo else np.ones_like(c)
+    c = np.clip((c - 0.3) / 0.7, 0.0, 1.0)
+    return np.clip(np.rint(128.0 + (t - 128.0) * c * c), 0, 255).astype(np.uint8)
+
+
+def global_motion_sequence(seed: int, w: int = 352, h: int = 288, n_moved: int = 9,
+                           max_shift: int = 8, noise_sigma: float = 2.0):
+    """The known-motion set-up of Sec. 3.1: frame 0 is an original frame
+    (``contrast_texture``); frames 1..n_moved are it displaced by known global
+    vectors g_k drawn from U{-max_shift..max_shift}^2 without repeats, plus
+    N(0, noise_sigma^2) noise.  g_k is given as the motion vector a block
+    matcher should find: frame_k(x, y) = frame_0(clamp(x + gx), clamp(y + gy))
+    before the noise.  Returns (frames [n_moved+1, h, w] uint8, g [n_moved, 2]
+    int16 as (gx, gy))."""
+    rng = _rng(seed, 11)
+    base = contrast_texture(rng, w, h)
+    side = 2 * max_shift + 1
+    if n_moved > side * side:
+        raise ValueError("more moved frames than distinct vectors")
+    pick = rng.choice(side * side, size=n_moved, replace=False)
+    g = np.stack([pick % side - max_shift, pick // side - max_shift], axis=1).astype(np.int16)
+    frames = np.zeros((n_moved + 1, h, w), np.uint8)
+    frames[0] = base
+    for k in range(n_moved):
+        frames[k + 1] = _add_noise(rng, shifted_copy(base, -int(g[k, 0]), -int(g[k, 1])),
+                                   noise_sigma)
+    return frames, g
 
 
 def scene_sequence(seed: int, w: int, h: int, n_frames: int, n_objects: int = 6,

@@ -79,6 +79,17 @@ MUTANTS = {
     "half-pel centre not doubled": (
         "            int cx = 2 * clampi(mv_int[2 * b], -p, p), cy = 2 * clampi(mv_int[2 * b + 1], -p, p);",
         "            int cx = clampi(mv_int[2 * b], -p, p), cy = clampi(mv_int[2 * b + 1], -p, p);"),
+    "SAD_deviation window misses the last column": (
+        "                for (int u = -p; u <= p; u++) {\n"
+        "                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
+        "                for (int u = -p; u < p; u++) {\n"
+        "                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);"),
+    "SAD_deviation minimum starts at zero": (
+        "                    if ((u == -p && v == -p) || s < mn) mn = s;",
+        "                    if (s < mn) mn = s;"),
+    "SAD_deviation block origin transposed": (
+        "block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
+        "block_sad(cur, ref, W, H, N, M, bx * M, by * N, u, v);"),
 }
 
 
@@ -109,6 +120,10 @@ def _pin_suite(v):
     for hx0, hy0 in [(3, -1), (-1, 2), (1, 1), (-3, -3)]:
         yield lambda hx0=hx0, hy0=hy0: pins.test_halfpel_recovers_exact_half_pel_shift(v, hx0, hy0)
     yield lambda: pins.test_halfpel_flat_frame_keeps_the_cheapest_position(v)
+    for args in [(48, 32, 16, 16, 4), (24, 16, 4, 8, 2), (32, 48, 16, 8, 5)]:
+        yield lambda args=args: pins.test_sad_deviation_matches_sad_volume(v, *args)
+    yield lambda: pins.test_sad_deviation_closed_forms(v)
+    yield lambda: pins.test_sad_deviation_of_a_known_global_shift(v, 3, -2)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

@@ -47,9 +47,9 @@ def eg_decode_stream(bits: str) -> list[int]:
     return out
 
 
-def brute_fsbm(cur, ref, N, M, p, lam):
-    """Whole SAD volume by sliding windows over an edge-padded reference,
-    then a lexicographic argmin (J, |mv|_1, mvy, mvx)."""
+def brute_sad_volume(cur, ref, N, M, p):
+    """SAD of every block at every integer position, by sliding windows over an
+    edge-padded reference: vol[mvy + p, mvx + p, by, bx] (int64)."""
     H, W = cur.shape
     BH, BW = H // M, W // N
     rp = np.pad(ref.astype(np.int64), p, mode="edge")
@@ -60,6 +60,15 @@ def brute_fsbm(cur, ref, N, M, p, lam):
         for b in range(n):
             sh = rp[a:a + H, b:b + W]          # ref(x + mvx, y + mvy), mvy = a - p, mvx = b - p
             vol[a, b] = np.abs(c - sh).reshape(BH, M, BW, N).sum(axis=(1, 3))
+    return vol
+
+
+def brute_fsbm(cur, ref, N, M, p, lam):
+    """Whole SAD volume, then a lexicographic argmin (J, |mv|_1, mvy, mvx)."""
+    H, W = cur.shape
+    BH, BW = H // M, W // N
+    n = 2 * p + 1
+    vol = brute_sad_volume(cur, ref, N, M, p)
     mvs = np.arange(-p, p + 1)
     bits = np.array([len(eg_encode_signed(int(v))) for v in mvs], np.int64)
     R = bits[:, None] + bits[None, :]         # [mvy, mvx]
@@ -524,3 +533,58 @@ def test_halfpel_flat_frame_keeps_the_cheapest_position(orc):
     mv, J, s = orc.halfpel(cur, ref, 16, 16, 3, 6595, one)
     assert np.all(mv[..., 0] == 1) and np.all(mv[..., 1] == 0)
     assert np.all(J == 6595 * (3 + 1))
+
+
+# ---------------------------------------------------------------------------
+# SAD_deviation (Sec. 3.1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("W,H,N,M,p", [(48, 32, 16, 16, 4), (32, 32, 8, 8, 3), (24, 16, 4, 8, 2),
+                                       (32, 48, 16, 8, 5)])
+def test_sad_deviation_matches_sad_volume(orc, W, H, N, M, p):
+    """SAD_min and sum |SAD(u,v) - SAD_min| of every block against the brute
+    SAD volume (edge-clamped reference, all (2p+1)^2 positions)."""
+    rng = np.random.default_rng(W * 3 + H + p)
+    ref = synth.texture(rng, W, H)
+    cur = np.clip(np.roll(ref, (2, -1), axis=(0, 1)).astype(int) + rng.integers(-9, 10, ref.shape),
+                  0, 255).astype(np.uint8)
+    vol = brute_sad_volume(cur, ref, N, M, p)
+    mn = vol.min(axis=(0, 1))
+    dev = np.abs(vol - mn[None, None]).sum(axis=(0, 1))
+    got_mn, got_dev = orc.sad_deviation(cur, ref, N, M, p)
+    assert np.array_equal(got_mn, mn) and np.array_equal(got_dev, dev)
+    assert np.all(got_mn > 0)                  # noise: no exact match anywhere
+
+
+def test_sad_deviation_closed_forms(orc):
+    """Flat frames: every position costs N*M*|a - b|, deviation 0.  A
+    horizontal ramp ref(x, y) = x matched against itself, block away from the
+    frame edges: SAD(u, v) = N*M*|u|, so SAD_min = 0 and the deviation is
+    (2p+1) * N*M * p(p+1)."""
+    for N, M, p in [(16, 16, 4), (8, 16, 3), (4, 4, 2)]:
+        W, H = 4 * N, 3 * M
+        cur = np.full((H, W), 200, np.uint8)
+        ref = np.full((H, W), 93, np.uint8)
+        mn, dev = orc.sad_deviation(cur, ref, N, M, p)
+        assert np.all(mn == N * M * 107) and np.all(dev == 0)
+        W, H = 64, 48
+        ramp = np.tile(np.arange(W, dtype=np.uint8) + 40, (H, 1))
+        mn, dev = orc.sad_deviation(ramp, ramp, N, M, p)
+        bx, by = 1, 1                           # p < N, p < M: the window stays inside
+        assert mn[by, bx] == 0
+        assert dev[by, bx] == (2 * p + 1) * N * M * p * (p + 1)
+
+
+@pytest.mark.parametrize("gx,gy", [(3, -2), (-4, 1), (0, 4)])
+def test_sad_deviation_of_a_known_global_shift(orc, gx, gy):
+    """A frame that is the reference displaced by a known vector g (edge
+    clamp, no noise): the true position costs 0, so SAD_min = 0 in every block
+    and the deviation is the plain sum of the SAD volume."""
+    rng = np.random.default_rng(17)
+    W, H, N, M, p = 64, 48, 16, 16, 5
+    ref = synth.texture(rng, W, H)
+    cur = synth.shifted_copy(ref, -gx, -gy)
+    vol = brute_sad_volume(cur, ref, N, M, p)
+    assert np.all(vol[gy + p, gx + p] == 0)
+    mn, dev = orc.sad_deviation(cur, ref, N, M, p)
+    assert np.all(mn == 0)
+    assert np.array_equal(dev, vol.sum(axis=(0, 1)))
