@@ -478,6 +478,47 @@ def main():
         hp_ms.append(eh0.elapsed_time(eh1))
     hp_frame_ms = statistics.median(hp_ms) / pairs
 
+    # SAD_min / SAD_deviation (Sec. 3.1) of one 1080p pair: the FSBM engine
+    # with the SAD sum and minimum reduced beside the winning key
+    # (timed as single launches after an L2 flush, beside me_fsbm timed the same way)
+    ss_ms, fs1_ms = [], []
+    for i in range(13):
+        for fn, acc in ((lambda c, r: me.me_sad_deviation(c, r, N, M, P, lam), ss_ms),
+                        (lambda c, r: me.me_fsbm(c, r, N, M, P, lam, out=(f_mv[0], f_J[0], f_sad[0])),
+                         fs1_ms)):
+            flush.fill_(1)
+            es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            es0.record(stream)
+            fn(frames[1 + i % pairs], frames[i % pairs])
+            es1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                acc.append(es0.elapsed_time(es1))
+    ss_frame_ms = statistics.median(ss_ms)
+    fs_single_ms = statistics.median(fs1_ms)
+    # the known-motion experiment of Sec. 3.1 / Fig. 3 (CIF, nine moved
+    # frames, 16x16, p = 16, lambda = 0): one launch, then its error classes
+    st_frames, st_g = synth.global_motion_sequence(41, 352, 288)
+    st_f, st_gd = torch.from_numpy(st_frames).cuda(), torch.from_numpy(st_g).cuda()
+    for _ in range(3):
+        st = me.me_motion_study(st_f, st_gd, 16, 16, 16, 0)
+    torch.cuda.synchronize()
+    et0, et1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    et0.record(stream)
+    st = me.me_motion_study(st_f, st_gd, 16, 16, 16, 0)
+    et1.record(stream)
+    torch.cuda.synchronize()
+    study_ms = et0.elapsed_time(et1)
+    st_err = st.err.cpu().numpy().astype(np.int64)
+    st_intra = st.intra.cpu().numpy().view(np.uint32) / 256.0    # Intra_SAD (N*M = 256 scale)
+    st_dev = st.sad_dev.cpu().numpy().view(np.uint32)
+    st_cls = np.minimum(st_err, 5)
+    study_classes = [{"error": (str(c) if c < 5 else ">=5"), "blocks": int((st_cls == c).sum()),
+                      "median_intra_sad": float(np.median(st_intra[st_cls == c])) if (st_cls == c).any() else None,
+                      "median_sad_deviation": float(np.median(st_dev[st_cls == c])) if (st_cls == c).any() else None}
+                     for c in range(6)]
+
     # kernel-only FSBM timing (the SAD engine) for the roofline, same stream
     reps = 20
     ek0, ek1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -555,6 +596,14 @@ def main():
                     "positions_per_block": 9,
                     # algorithmic bytes: each frame read as current and as reference
                     "algorithmic_gb_per_s": 2 * W * H_PAD / (hp_frame_ms * 1e-3) / 1e9},
+        "sad_deviation": {"form": "me_sad_deviation, one 1080p pair (FSBM + SAD_min + SAD_deviation)",
+                          "ms_per_frame": ss_frame_ms, "me_fsbm_same_timing_ms": fs_single_ms,
+                          "absdiff_per_s": ABSDIFF_PER_FRAME / (ss_frame_ms * 1e-3) / 1e12,
+                          "frac_of_peak": ABSDIFF_PER_FRAME / (ss_frame_ms * 1e-3) / peak_absdiff,
+                          "unit": "T absdiff/s"},
+        "motion_study": {"form": "me_motion_study: CIF original + 9 frames moved by known global "
+                                 "vectors, 16x16, p=16, lambda=0, one launch",
+                         "ms": study_ms, "classes": study_classes},
         "per_pair": {"form": "me_fsbm + me_acbm (wave launches, graph-replayed) per pair",
                      "frames_per_s": 1e3 / statistics.mean(pair_ms),
                      "acbm_ms": statistics.mean(pair_acbm_ms), "fsbm_ms": statistics.mean(pair_fsbm_ms),

@@ -189,6 +189,37 @@ int me_halfpel_sequence(const uint8_t *const *frames, int K, int W, int H, int N
                         uint32_t lambda_q8, const int16_t *mv_int, int16_t *mv_half_out,
                         uint32_t *J_out, uint32_t *sad_out, me_stream_t stream);
 
+/* ------------------------------------------------- SAD statistics (Sec. 3.1) */
+
+/* FSBM (as me_fsbm) plus, for every block, the two statistics of the full
+ * search's SAD surface that Sec. 3.1 introduces: SAD_min, the least SAD over
+ * the (2p+1)^2 positions (a SAD minimum, independent of lambda), and
+ * SAD_deviation = sum over those positions of |SAD(u,v) - SAD_min|.
+ * mv_out [BH][BW][2] and J_out [BH][BW] (both nullable) are the FSBM result
+ * for lambda_q8; sad_min_out, sad_dev_out: device [BH][BW] uint32 (required;
+ * SAD_deviation < 2^31 for every allowed shape).  Same argument checks as
+ * me_fsbm; one launch; no scratch memory; asynchronous on `stream`. */
+int me_sad_deviation(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out,
+                     uint32_t *sad_min_out, uint32_t *sad_dev_out, me_stream_t stream);
+
+/* The known-motion experiment of Sec. 3.1 (Fig. 3) in one launch: frames is a
+ * host array of K+1 device frame pointers (1 <= K <= 64); frames[0] is the
+ * original frame and frames[k], k >= 1, the original displaced by the known
+ * global vector true_mv[k-1] (device [K][2] int16, (gx, gy), given as the
+ * motion vector a block matcher should find).  For every moved frame k and
+ * block b, index (k-1)*BH*BW + b: the FSBM vector of frames[k] against
+ * frames[0] (mv_out, [K][BH][BW][2]), the scaled Intra_SAD of the block of
+ * frames[k] (intra_out, N*M*Intra_SAD as me_intra_sad), SAD_min and
+ * SAD_deviation (as me_sad_deviation), and the vector error
+ * err_out = min(|mvx - gx| + |mvy - gy|, 255) (uint8; 0 = true vector).
+ * mv_out, intra_out and err_out are nullable; sad_min_out and sad_dev_out are
+ * required.  Same argument checks as me_fsbm; asynchronous on `stream`. */
+int me_motion_study(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
+                    uint32_t lambda_q8, const int16_t *true_mv, int16_t *mv_out,
+                    uint32_t *intra_out, uint32_t *sad_min_out, uint32_t *sad_dev_out,
+                    uint8_t *err_out, me_stream_t stream);
+
 /* ----------------------------------------------------------------- batches */
 
 /* Many independent streams of uneven size in one launch per step (an

@@ -87,6 +87,9 @@ def _bind(lib):
     lib.oracle_halfpel.restype = c_int
     lib.oracle_sad_deviation.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, u32p, u32p]
     lib.oracle_sad_deviation.restype = c_int
+    lib.oracle_sad_deviation_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int,
+                                                ctypes.POINTER(c_int), c_int, u32p, u32p]
+    lib.oracle_sad_deviation_blocks.restype = c_int
     return lib
 
 
@@ -224,6 +227,21 @@ def sad_deviation(cur, ref, N: int, M: int, p: int):
     _check(_load().oracle_sad_deviation(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H,
                                         N, M, p, _ptr(mn, ctypes.c_uint32),
                                         _ptr(dev, ctypes.c_uint32)), "oracle_sad_deviation")
+    return mn, dev
+
+
+def sad_deviation_blocks(cur, ref, N: int, M: int, p: int, blocks):
+    """SAD_min and SAD_deviation of the listed blocks (raster indices), each [n] u32."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    mn = np.zeros(len(blocks), np.uint32)
+    dev = np.zeros(len(blocks), np.uint32)
+    _check(_load().oracle_sad_deviation_blocks(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8),
+                                               W, H, N, M, p, _ptr(blocks, ctypes.c_int),
+                                               len(blocks), _ptr(mn, ctypes.c_uint32),
+                                               _ptr(dev, ctypes.c_uint32)),
+           "oracle_sad_deviation_blocks")
     return mn, dev
 
 

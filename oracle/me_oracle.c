@@ -521,6 +521,25 @@ int oracle_halfpel(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, 
  * SAD_min the smallest SAD of the window (a SAD minimum, not the J one).
  * Written out term by term.  Outputs per block: SAD_min and SAD_deviation.
  * ------------------------------------------------------------------------ */
+static void sad_deviation_block(const uint8_t *cur, const uint8_t *ref, int W, int H, int N,
+                                int M, int p, int bx, int by, uint32_t *vol,
+                                uint32_t *sad_min, uint32_t *sad_dev)
+{
+    int n = 2 * p + 1;
+    uint32_t mn = 0;
+    for (int v = -p; v <= p; v++)
+        for (int u = -p; u <= p; u++) {
+            uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);
+            vol[(v + p) * n + (u + p)] = s;
+            if ((u == -p && v == -p) || s < mn) mn = s;
+        }
+    uint64_t dev = 0;
+    for (int k = 0; k < n * n; k++)
+        dev += (uint64_t)(vol[k] > mn ? vol[k] - mn : mn - vol[k]);
+    *sad_min = mn;
+    *sad_dev = (uint32_t)dev;
+}
+
 int oracle_sad_deviation(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M,
                          int p, uint32_t *sad_min_out, uint32_t *sad_dev_out)
 {
@@ -531,20 +550,29 @@ int oracle_sad_deviation(const uint8_t *cur, const uint8_t *ref, int W, int H, i
     uint32_t *vol = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * n);
     if (!vol) return OR_ERR_NOMEM;
     for (int by = 0; by < BH; by++)
-        for (int bx = 0; bx < BW; bx++) {
-            uint32_t mn = 0;
-            for (int v = -p; v <= p; v++)
-                for (int u = -p; u <= p; u++) {
-                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);
-                    vol[(v + p) * n + (u + p)] = s;
-                    if ((u == -p && v == -p) || s < mn) mn = s;
-                }
-            uint64_t dev = 0;
-            for (int k = 0; k < n * n; k++)
-                dev += (uint64_t)(vol[k] > mn ? vol[k] - mn : mn - vol[k]);
-            sad_min_out[by * BW + bx] = mn;
-            sad_dev_out[by * BW + bx] = (uint32_t)dev;
-        }
+        for (int bx = 0; bx < BW; bx++)
+            sad_deviation_block(cur, ref, W, H, N, M, p, bx, by, vol, &sad_min_out[by * BW + bx],
+                                &sad_dev_out[by * BW + bx]);
+    free(vol);
+    return OR_OK;
+}
+
+/* The same for a list of block indices (raster order), outputs per listed block. */
+int oracle_sad_deviation_blocks(const uint8_t *cur, const uint8_t *ref, int W, int H, int N,
+                                int M, int p, const int *blocks, int nblocks,
+                                uint32_t *sad_min_out, uint32_t *sad_dev_out)
+{
+    if (!cur || !ref || !blocks || !sad_min_out || !sad_dev_out || nblocks < 0) return OR_ERR_ARG;
+    int st = check_shape(W, H, N, M, p, 0);
+    if (st) return st;
+    int BW = W / N, BH = H / M, n = 2 * p + 1;
+    for (int k = 0; k < nblocks; k++)
+        if (blocks[k] < 0 || blocks[k] >= BW * BH) return OR_ERR_ARG;
+    uint32_t *vol = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * n);
+    if (!vol) return OR_ERR_NOMEM;
+    for (int k = 0; k < nblocks; k++)
+        sad_deviation_block(cur, ref, W, H, N, M, p, blocks[k] % BW, blocks[k] / BW, vol,
+                            &sad_min_out[k], &sad_dev_out[k]);
     free(vol);
     return OR_OK;
 }

@@ -18,8 +18,8 @@ from . import build as _build
 __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
-    "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_peak", "Batch", "Server",
-    "STATUS",
+    "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_deviation",
+    "me_motion_study", "me_sad_peak", "Batch", "Server", "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -103,6 +103,10 @@ def load_library(build_if_missing: bool = True):
                            c_int),
             "me_halfpel_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                      u32, vp, vp, vp, vp, vp], c_int),
+            "me_sad_deviation": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp,
+                                  vp], c_int),
+            "me_motion_study": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
+                                 u32, vp, vp, vp, vp, vp, vp, vp], c_int),
             "me_acbm_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                   u32, vp, ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp],
                                  c_int),
@@ -333,6 +337,49 @@ def me_halfpel_sequence(frames, N: int, M: int, p: int, lambda_q8: int, mv_int, 
                                               _ptr(mv), _ptr(J), _ptr(sad), _stream_ptr(stream)),
            "me_halfpel_sequence")
     return FsbmResult(mv, J, sad)
+
+
+@dataclass
+class SadStats:
+    mv: "object"       # int16 [..., BH, BW, 2] FSBM vector
+    J: "object"        # int32 view of uint32 [..., BH, BW] (None for a study)
+    intra: "object"    # int32 view of uint32 [..., BH, BW]: N*M*Intra_SAD (None for one pair)
+    sad_min: "object"  # int32 view of uint32 [..., BH, BW]
+    sad_dev: "object"  # int32 view of uint32 [..., BH, BW]
+    err: "object"      # uint8 [..., BH, BW]: L1 error against the known vector (None for one pair)
+
+
+def me_sad_deviation(cur, ref, N: int, M: int, p: int, lambda_q8: int = 0, stream=None) -> SadStats:
+    """FSBM plus SAD_min and SAD_deviation of every block (Sec. 3.1)."""
+    torch = _torch()
+    W, H = _frame_args(cur, ref)
+    mv, J, smin = _outs(H, W, N, M, cur.device)
+    sdev = torch.empty_like(smin)
+    _check(load_library().me_sad_deviation(_ptr(cur), _ptr(ref), W, H, N, M, p, int(lambda_q8),
+                                            _ptr(mv), _ptr(J), _ptr(smin), _ptr(sdev),
+                                            _stream_ptr(stream)), "me_sad_deviation")
+    return SadStats(mv, J, None, smin, sdev, None)
+
+
+def me_motion_study(frames, true_mv, N: int, M: int, p: int, lambda_q8: int = 0,
+                    stream=None) -> SadStats:
+    """The known-motion experiment of Sec. 3.1 in one launch: frames[0] the
+    original, frames[1..K] moved by true_mv (int16 CUDA [K, 2], (gx, gy));
+    outputs [K, BH, BW, ...]."""
+    torch = _torch()
+    arr, K, W, H = _frame_ptrs(frames)
+    dev = frames[0].device
+    if not (true_mv.is_cuda and true_mv.dtype == torch.int16 and tuple(true_mv.shape) == (K, 2)
+            and true_mv.is_contiguous()):
+        raise ValueError("true_mv must be a contiguous int16 CUDA tensor [K, 2]")
+    BH, BW = H // M, W // N
+    mv = torch.empty((K, BH, BW, 2), dtype=torch.int16, device=dev)
+    intra, smin, sdev = (torch.empty((K, BH, BW), dtype=torch.int32, device=dev) for _ in range(3))
+    err = torch.empty((K, BH, BW), dtype=torch.uint8, device=dev)
+    _check(load_library().me_motion_study(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(true_mv),
+                                           _ptr(mv), _ptr(intra), _ptr(smin), _ptr(sdev),
+                                           _ptr(err), _stream_ptr(stream)), "me_motion_study")
+    return SadStats(mv, None, intra, smin, sdev, err)
 
 
 def me_acbm_sequence(frames, N: int, M: int, p: int, lambda_q8: int, prm: AcbmParams,

@@ -176,12 +176,15 @@ struct FsPad {
 // (x0, y0).  The per-block winning keys go to keys_out[0..bpc) (shared
 // memory, visible to all threads on return).  Every thread of the CTA calls
 // it; threads beyond bpc*G only help with staging.  SP > 0: the geometry's
-// shifted-word pitch is SP (fixed at compile time), else g.sp.
-template <int N, int M, int T, int SP = 0>
+// shifted-word pitch is SP (fixed at compile time), else g.sp.  STATS: also
+// the sum and the minimum of the SAD over the searched positions of every
+// block, to stats[2*blk] and stats[2*blk+1] (shared memory, 2*bpc words).
+template <int N, int M, int T, int SP = 0, bool STATS = false>
 __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
                          int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
                          uint32_t* smem, unsigned long long* keys_out,
-                         unsigned long long* tr = nullptr, FsPad pad = FsPad{nullptr, 0, 0, 0}) {
+                         unsigned long long* tr = nullptr, FsPad pad = FsPad{nullptr, 0, 0, 0},
+                         uint32_t* stats = nullptr) {
   constexpr int NW = N / 4;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
@@ -200,6 +203,10 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   const int rb = rank_bits(p);
 
   if (tid < g.bpc) red[tid] = kNoKey;
+  if (STATS && tid < g.bpc) {
+    stats[2 * tid] = 0u;
+    stats[2 * tid + 1] = 0xffffffffu;
+  }
   int s0;
   if (pad.base) {
     // 1+2 from the padded reference: current blocks as 4-byte and window rows
@@ -293,6 +300,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   // 4. tasks of this thread's block
   const int blk = tid / g.G, l = tid - blk * g.G;
   unsigned long long best = kNoKey;
+  uint32_t ssum = 0u, smin = 0xffffffffu;
   if (blk < g.bpc) {
     uint32_t c[M][NW];
 #pragma unroll
@@ -322,6 +330,14 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
             if (j >= 0 && j < M) acc[k] = sad4(c[j][w], rw[w], acc[k]);
           }
         }
+      }
+      if (STATS) {
+#pragma unroll
+        for (int k = 0; k < T; k++)
+          if (row0 + k < n) {
+            ssum += acc[k];
+            smin = min(smin, acc[k]);
+          }
       }
       // cost and key of each candidate of the run (mvx = c0 + col - p)
       const int wcol = g.c0 + col;
@@ -364,13 +380,36 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     tr[1] = t;
   }
-  // 5. per-block minimum
+  // 5. per-block minimum (and SAD sum / minimum)
   if (g.G <= 32) {
-    for (int o = g.G >> 1; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (blk < g.bpc && l == 0) red[blk] = best;
+    for (int o = g.G >> 1; o > 0; o >>= 1) {
+      best = umin64(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (STATS) {
+        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+        smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+      }
+    }
+    if (blk < g.bpc && l == 0) {
+      red[blk] = best;
+      if (STATS) {
+        stats[2 * blk] = ssum;
+        stats[2 * blk + 1] = smin;
+      }
+    }
   } else {
     best = warp_min64(best);
+    if (STATS) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+        smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+      }
+    }
     if (lane == 0 && blk < g.bpc && best != kNoKey) atomicMin(&red[blk], best);
+    if (STATS && lane == 0 && blk < g.bpc) {
+      atomicAdd(&stats[2 * blk], ssum);
+      atomicMin(&stats[2 * blk + 1], smin);
+    }
   }
   __syncthreads();
   if (tid < g.bpc) keys_out[tid] = red[tid];

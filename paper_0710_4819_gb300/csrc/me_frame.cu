@@ -387,27 +387,6 @@ static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* 
   return ME_OK;
 }
 
-#define ME_DISPATCH_FS(FN, ...)                                                      \
-  do {                                                                               \
-    if (N == 16 && M == 16) {                                                        \
-      switch (pl.T) {                                                                \
-        case 8: return FN<16, 16, 8>(__VA_ARGS__);                                   \
-        case 11: return FN<16, 16, 11>(__VA_ARGS__);                                 \
-        case 13: return FN<16, 16, 13>(__VA_ARGS__);                                 \
-        case 16: return FN<16, 16, 16>(__VA_ARGS__);                                 \
-      }                                                                              \
-    }                                                                                \
-    if (N == 16 && M == 8) return FN<16, 8, 8>(__VA_ARGS__);                         \
-    if (N == 16 && M == 4) return FN<16, 4, 8>(__VA_ARGS__);                         \
-    if (N == 8 && M == 16) return FN<8, 16, 8>(__VA_ARGS__);                         \
-    if (N == 8 && M == 8) return FN<8, 8, 8>(__VA_ARGS__);                           \
-    if (N == 8 && M == 4) return FN<8, 4, 8>(__VA_ARGS__);                           \
-    if (N == 4 && M == 16) return FN<4, 16, 8>(__VA_ARGS__);                         \
-    if (N == 4 && M == 8) return FN<4, 8, 8>(__VA_ARGS__);                           \
-    if (N == 4 && M == 4) return FN<4, 4, 8>(__VA_ARGS__);                           \
-    return ME_ERR_ARG;                                                               \
-  } while (0)
-
 int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
                 uint32_t lam, int16_t* mv, uint32_t* J, uint32_t* sad, cudaStream_t s) {
   FsPlan pl = fs_plan(N, M, p, W / N);

@@ -426,6 +426,29 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max);
 FsPlan fs_plan_latency(int N, int M, int p);
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit);
 
+// Calls FN<N, M, T>(...) for the run lengths instantiated per block shape
+// (pl.T chooses among them for 16x16); expects N, M and pl in scope.
+#define ME_DISPATCH_FS(FN, ...)                                                      \
+  do {                                                                               \
+    if (N == 16 && M == 16) {                                                        \
+      switch (pl.T) {                                                                \
+        case 8: return FN<16, 16, 8>(__VA_ARGS__);                                   \
+        case 11: return FN<16, 16, 11>(__VA_ARGS__);                                 \
+        case 13: return FN<16, 16, 13>(__VA_ARGS__);                                 \
+        case 16: return FN<16, 16, 16>(__VA_ARGS__);                                 \
+      }                                                                              \
+    }                                                                                \
+    if (N == 16 && M == 8) return FN<16, 8, 8>(__VA_ARGS__);                         \
+    if (N == 16 && M == 4) return FN<16, 4, 8>(__VA_ARGS__);                         \
+    if (N == 8 && M == 16) return FN<8, 16, 8>(__VA_ARGS__);                         \
+    if (N == 8 && M == 8) return FN<8, 8, 8>(__VA_ARGS__);                           \
+    if (N == 8 && M == 4) return FN<8, 4, 8>(__VA_ARGS__);                           \
+    if (N == 4 && M == 16) return FN<4, 16, 8>(__VA_ARGS__);                         \
+    if (N == 4 && M == 8) return FN<4, 8, 8>(__VA_ARGS__);                           \
+    if (N == 4 && M == 4) return FN<4, 4, 8>(__VA_ARGS__);                           \
+    return ME_ERR_ARG;                                                               \
+  } while (0)
+
 // Scratch layout of one ACBM frame (the call's arguments, padded reference,
 // scaled Intra_SAD per block, failing-block count per wave, compacted
 // failing-block lists, per-block merge key and slice counter of the sliced

@@ -19,7 +19,7 @@ Recipes (all frames uint8, row-major [H, W]):
   rounds and clamps.
 * ``global_motion_sequence`` (Sec. 3.1 set-up, default CIF): one original
   frame (``contrast_texture``: a texture times a smooth contrast map that
-  runs from flat, on about a quarter of the frame, to full) and nine copies displaced by known distinct global
+  runs from flat, on 30 % of the frame, to full) and nine copies displaced by known distinct global
   vectors from U{-8..8}^2 (edge clamp) plus N(0, 2^2) noise.
 * ``scene_sequence`` (CIF / 720p / 1080p / 4K): a textured background canvas
   panned by 1 px/frame, ``n_objects`` textured rectangles (sides U{32..96})
@@ -119,14 +119,15 @@ def quadrant_sequence(seed: int, n_frames: int = 10, w: int = 176, h: int = 144,
 def contrast_texture(rng: np.random.Generator, w: int, h: int) -> np.ndarray:
     """A texture whose local contrast varies smoothly from flat to full: the
     texture's deviation from 128 times c(x, y)^2, where c is U[0,1] noise
-    blurred with sigma 12, min-max rescaled to [0, 1], then mapped by
-    max(0, (c - 0.3) / 0.7), so that about a quarter of the frame is flat."""
+    blurred with sigma 12, replaced by its rank in the frame divided by the
+    pixel count (uniform on [0, 1)), then mapped by max(0, (c - 0.3) / 0.7),
+    so that 30 % of the frame is flat whatever the seed."""
     t = texture(rng, w, h).astype(np.float64)
     c = rng.random((h, w))
     c = _blur_1d(_blur_1d(c, 1, 12.0, 36), 0, 12.0, 36)
-    lo, hi = c.min(), c.max()
-    c = (c - lo) / (hi - lo) if hi > lo else np.ones_like(c)
-    c = np.clip((c - 0.3) / 0.7, 0.0, 1.0)
+    rank = np.empty(c.size, np.float64)
+    rank[np.argsort(c, axis=None, kind="stable")] = np.arange(c.size)
+    c = np.clip((rank.reshape(h, w) / c.size - 0.3) / 0.7, 0.0, 1.0)
     return np.clip(np.rint(128.0 + (t - 128.0) * c * c), 0, 255).astype(np.uint8)
 
 

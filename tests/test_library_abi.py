@@ -98,4 +98,24 @@ def test_argument_errors_before_launch(lib):
     frames = (vp * 3)(fake, None, fake)
     assert lib.me_halfpel_sequence(frames, 2, 64, 64, 16, 16, 4, 0, fake, fake, fake, None,
                                    None) == 1
+    # SAD statistics: both statistic outputs required, frame checks as FSBM
+    assert lib.me_sad_deviation(fake, fake, 64, 64, 16, 16, 4, 0, None, None, fake, None,
+                                None) == 1
+    assert lib.me_sad_deviation(fake, fake, 64, 64, 16, 16, 65, 0, None, None, fake, fake,
+                                None) == 1
+    assert lib.me_sad_deviation(fake, fake, 64, 40, 16, 16, 4, 0, None, None, fake, fake,
+                                None) == 2
+    frames = (vp * 3)(fake, fake, fake)
+    assert lib.me_motion_study(frames, 0, 64, 64, 16, 16, 4, 0, fake, None, None, fake, fake,
+                               None, None) == 1
+    assert lib.me_motion_study(frames, 65, 64, 64, 16, 16, 4, 0, fake, None, None, fake, fake,
+                               None, None) == 1
+    # an error output needs the known vectors
+    assert lib.me_motion_study(frames, 2, 64, 64, 16, 16, 4, 0, None, None, None, fake, fake,
+                               fake, None) == 1
+    assert lib.me_motion_study(frames, 2, 48, 64, 32, 16, 4, 0, fake, None, None, fake, fake,
+                               None, None) == 1
+    frames = (vp * 3)(fake, fake, None)
+    assert lib.me_motion_study(frames, 2, 64, 64, 16, 16, 4, 0, fake, None, None, fake, fake,
+                               None, None) == 1
     assert lib.me_status_string(2).decode().startswith("frame size")

@@ -80,13 +80,13 @@ MUTANTS = {
         "            int cx = 2 * clampi(mv_int[2 * b], -p, p), cy = 2 * clampi(mv_int[2 * b + 1], -p, p);",
         "            int cx = clampi(mv_int[2 * b], -p, p), cy = clampi(mv_int[2 * b + 1], -p, p);"),
     "SAD_deviation window misses the last column": (
-        "                for (int u = -p; u <= p; u++) {\n"
-        "                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
-        "                for (int u = -p; u < p; u++) {\n"
-        "                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);"),
+        "        for (int u = -p; u <= p; u++) {\n"
+        "            uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
+        "        for (int u = -p; u < p; u++) {\n"
+        "            uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);"),
     "SAD_deviation minimum starts at zero": (
-        "                    if ((u == -p && v == -p) || s < mn) mn = s;",
-        "                    if (s < mn) mn = s;"),
+        "            if ((u == -p && v == -p) || s < mn) mn = s;",
+        "            if (s < mn) mn = s;"),
     "SAD_deviation block origin transposed": (
         "block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
         "block_sad(cur, ref, W, H, N, M, bx * M, by * N, u, v);"),

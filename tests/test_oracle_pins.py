@@ -588,3 +588,18 @@ def test_sad_deviation_of_a_known_global_shift(orc, gx, gy):
     mn, dev = orc.sad_deviation(cur, ref, N, M, p)
     assert np.all(mn == 0)
     assert np.array_equal(dev, vol.sum(axis=(0, 1)))
+
+
+def test_sad_deviation_blocks_agree_with_the_frame_call(orc):
+    """The sampled-block entry (used at frame sizes the whole-frame oracle is
+    too slow for) returns the frame call's values at the listed blocks."""
+    rng = np.random.default_rng(23)
+    W, H, N, M, p = 64, 48, 8, 16, 6
+    ref = synth.texture(rng, W, H)
+    cur = np.clip(ref.astype(int) + rng.integers(-20, 21, ref.shape), 0, 255).astype(np.uint8)
+    mn, dev = orc.sad_deviation(cur, ref, N, M, p)
+    blocks = np.array([0, 5, 7, 8, 23, 17], np.int32)
+    bmn, bdev = orc.sad_deviation_blocks(cur, ref, N, M, p, blocks)
+    assert np.array_equal(bmn, mn.ravel()[blocks]) and np.array_equal(bdev, dev.ravel()[blocks])
+    with pytest.raises(Exception):
+        orc.sad_deviation_blocks(cur, ref, N, M, p, np.array([24], np.int32))
