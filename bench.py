@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve"],
-                    help="1080p: the default line; batch64 / serve: the multi-stream forms")
+    ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve", "loadtable"],
+                    help="1080p: the default line; batch64 / serve: the multi-stream forms; "
+                         "loadtable: ACBM load per block vs Qp on QCIF scenes (Table 1 layout)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
     ap.add_argument("--seconds", type=float, default=10.0, help="serve: arrival window")
     return ap.parse_args()
@@ -268,6 +269,89 @@ def run_batch64(args):
     print(json.dumps(line))
 
 
+LOAD_QPS = (30, 28, 26, 24, 22, 20, 18, 16)
+LOAD_P = 15                       # the paper's search range (961 + 8 half-pel = 969 positions)
+
+
+def load_cell(me, frames, qp, prm=None):
+    """ACBM of a QCIF sequence (16x16, p = 15, lambda from Qp) in one launch:
+    returns (average integer positions per block, full-search fraction, sum J,
+    sum SAD)."""
+    import numpy as np
+    import torch
+    lam = me.me_lambda_q8(qp)
+    a = me.me_acbm_sequence(frames, N, M, LOAD_P, lam, prm if prm is not None else me.params(qp=qp))
+    torch.cuda.synchronize()
+    load = a.load.double().mean().item()
+    fs = a.mask.double().mean().item()
+    J = a.J.cpu().numpy().view(np.uint32).astype(np.int64).sum()
+    sad = a.sad.cpu().numpy().view(np.uint32).astype(np.int64).sum()
+    return load, fs, int(J), int(sad)
+
+
+def run_load_table(args):
+    """The Table 1 layout on synthetic QCIF scenes: ACBM's average candidate
+    positions per block (integer positions, and +8 for the half-pel step the
+    paper's count of 969 for FSBM includes) for Qp 30..16 at 30 and 10 fps,
+    alpha, beta, gamma = 1000, 8, 1/4; then one-at-a-time sweeps of alpha,
+    beta and gamma at Qp 28 with the load and the cost relative to FSBM."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_0710_4819_gb300 as me
+    stream = torch.cuda.current_stream()
+    seqs = {(name, fps): torch.from_numpy(synth.load_sequence(name, fps, seed=500)).cuda()
+            for name in synth.LOAD_RECIPES for fps in (30, 10)}
+    for f in seqs.values():                      # warm-up (plans)
+        load_cell(me, f, 28)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    table = {}
+    for (name, fps), f in seqs.items():
+        for qp in LOAD_QPS:
+            load, fs, _, _ = load_cell(me, f, qp)
+            table.setdefault(name, {}).setdefault(str(fps), {})[str(qp)] = {
+                "positions": round(load, 2), "positions_with_halfpel": round(load + 8, 2),
+                "fullsearch_fraction": round(fs, 4)}
+    e1.record(stream)
+    torch.cuda.synchronize()
+    table_ms = e0.elapsed_time(e1)
+    # sweeps at Qp 28: cost of ACBM relative to FSBM's (the method's objective)
+    base = dict(alpha=1000, beta=8, gamma_num=1, gamma_den=4)
+    variants = ([("alpha", v, dict(base, alpha=v)) for v in (0, 250, 500, 2000, 4000, 16000)] +
+                [("beta", v, dict(base, beta=v)) for v in (0, 2, 4, 16, 32)] +
+                [("gamma", f"{n}/{d}", dict(base, gamma_num=n, gamma_den=d))
+                 for n, d in ((0, 1), (1, 8), (1, 2), (1, 1))] +
+                [("paper", "1000, 8, 1/4", base)])
+    fsbm_J, fsbm_sad = {}, {}
+    for key, f in seqs.items():
+        r = me.me_fsbm_sequence(f, N, M, LOAD_P, me.me_lambda_q8(28))
+        torch.cuda.synchronize()
+        fsbm_J[key] = int(r.J.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+        fsbm_sad[key] = int(r.sad.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+    sweep = []
+    for which, v, kw in variants:
+        prm = me.AcbmParams(kw["alpha"], kw["beta"], kw["gamma_num"], kw["gamma_den"], 28, 1)
+        loads, dJ, dS = [], [], []
+        for key, f in seqs.items():
+            load, _, J, sad = load_cell(me, f, 28, prm)
+            loads.append(load)
+            dJ.append(J / fsbm_J[key] - 1.0)
+            dS.append(sad / fsbm_sad[key] - 1.0)
+        sweep.append({"vary": which, "value": v, "positions": round(float(np.mean(loads)), 2),
+                      "J_over_fsbm_pct": round(100 * float(np.mean(dJ)), 3),
+                      "SAD_over_fsbm_pct": round(100 * float(np.mean(dS)), 3)})
+    cells = [c["positions_with_halfpel"] for r in table.values() for fr in r.values() for c in fr.values()]
+    line = {"metric": "ACBM average candidate positions per 16x16 block incl. 8 half-pel (Table 1 layout)",
+            "value": float(np.mean(cells)), "unit": "positions/block", "n_gpus": 1,
+            "steps": len(cells), "higher_is_better": False, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "load table: 4 synthetic QCIF scenes x {30, 10} fps x Qp 30..16, "
+                                   "10 frames, 16x16, p=15, alpha/beta/gamma = 1000/8/1/4",
+                       "fsbm_positions_with_halfpel": (2 * LOAD_P + 1) ** 2 + 8},
+            "table_ms": table_ms, "table": table, "sweep_qp28": sweep}
+    print(json.dumps(line))
+
+
 def run_serve(args):
     """Continuous-batching server over 200 streams (CIF p16 : 720p p32 :
     1080p p32 = 50 : 35 : 15), Poisson arrivals at --rate for --seconds."""
@@ -334,7 +418,7 @@ def main():
         torch.cuda.set_device(0)
         import paper_0710_4819_gb300 as me
         me.load_library(build_if_missing=True)
-        (run_batch64 if args.workload == "batch64" else run_serve)(args)
+        {"batch64": run_batch64, "serve": run_serve, "loadtable": run_load_table}[args.workload](args)
         return
     rank, world, local, pg = dist_setup(args.gpus)
     import numpy as np

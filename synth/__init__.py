@@ -21,6 +21,10 @@ Recipes (all frames uint8, row-major [H, W]):
   frame (``contrast_texture``: a texture times a smooth contrast map that
   runs from flat, on 30 % of the frame, to full) and nine copies displaced by known distinct global
   vectors from U{-8..8}^2 (edge clamp) plus N(0, 2^2) noise.
+* ``load_sequence`` (QCIF, the Table 1-shaped load table): ``scene_sequence``
+  with background contrast 0.15 or 1, 2-6 objects, object speeds up to 1 or
+  3 px/frame and pans of 0-2 px/frame (``LOAD_RECIPES``); 10 fps = every
+  third frame of the 30 fps scene.
 * ``scene_sequence`` (CIF / 720p / 1080p / 4K): a textured background canvas
   panned by 1 px/frame, ``n_objects`` textured rectangles (sides U{32..96})
   moving at constant integer velocities from U{-vmax..vmax}^2 and painted in
@@ -37,7 +41,8 @@ import numpy as np
 
 __all__ = [
     "texture", "contrast_texture", "global_motion_sequence", "quadrant_sequence", "scene_sequence", "random_frame", "shifted_copy",
-    "StreamSpec", "CONFIGS", "config_sequence", "batch_mix", "serving_mix",
+    "StreamSpec", "CONFIGS", "config_sequence", "batch_mix", "serving_mix", "LOAD_RECIPES",
+    "load_sequence",
 ]
 
 
@@ -158,12 +163,17 @@ def global_motion_sequence(seed: int, w: int = 352, h: int = 288, n_moved: int =
 def scene_sequence(seed: int, w: int, h: int, n_frames: int, n_objects: int = 6,
                    vmax: int = 6, pan: int = 1, noise_sigma: float = 2.0,
                    occlusion_frac: float = 0.0, block: int = 16,
-                   pad_height: int | None = None, margin: int = 96) -> np.ndarray:
-    """Panned background + moving textured rectangles + noise (+ occlusion blocks)."""
+                   pad_height: int | None = None, margin: int = 96,
+                   bg_contrast: float = 1.0) -> np.ndarray:
+    """Panned background + moving textured rectangles + noise (+ occlusion blocks).
+    bg_contrast < 1 scales the background's deviation from 128 (a smoother scene)."""
     rng = _rng(seed, 2)
     cw = w + abs(pan) * n_frames + 2 * margin
     ch = h + 2 * margin
     canvas = texture(rng, cw, ch)
+    if bg_contrast != 1.0:
+        canvas = np.clip(np.rint(128.0 + (canvas.astype(np.float64) - 128.0) * bg_contrast),
+                         0, 255).astype(np.uint8)
     objs = []
     for _ in range(n_objects):
         ow, oh = (int(v) for v in rng.integers(32, 97, size=2))
@@ -228,6 +238,30 @@ CONFIGS = {
     "1080p": dict(w=1920, h=1080, pad_height=1088, p=32, frames=60, qps=(28,),
                   n_objects=20, vmax=24, occlusion_frac=0.10),
 }
+
+
+# Four QCIF scene recipes spanning the two axes Table 1 is discussed along
+# (texture of the scene, amount of motion): background contrast, objects,
+# object speed bound (px per frame at 30 fps) and pan (px per frame).
+LOAD_RECIPES = {
+    "smooth-slow": dict(bg_contrast=0.15, n_objects=2, vmax=1, pan=0),
+    "smooth-fast": dict(bg_contrast=0.15, n_objects=4, vmax=3, pan=1),
+    "textured-slow": dict(bg_contrast=1.0, n_objects=4, vmax=1, pan=1),
+    "textured-fast": dict(bg_contrast=1.0, n_objects=6, vmax=3, pan=2),
+}
+
+
+def load_sequence(name: str, fps: int, seed: int, n_frames: int = 10) -> np.ndarray:
+    """QCIF frames [n_frames, 144, 176] of a ``LOAD_RECIPES`` scene at 30 fps
+    (consecutive frames) or 10 fps (every third frame of the same scene, so
+    three times the motion per frame)."""
+    if fps not in (30, 10):
+        raise ValueError("fps must be 30 or 10")
+    step = 30 // fps
+    r = LOAD_RECIPES[name]
+    full = scene_sequence(seed, 176, 144, step * (n_frames - 1) + 1, n_objects=r["n_objects"],
+                          vmax=r["vmax"], pan=r["pan"], bg_contrast=r["bg_contrast"])
+    return np.ascontiguousarray(full[::step])
 
 
 def config_sequence(name: str, seed: int, n_frames: int | None = None) -> np.ndarray:

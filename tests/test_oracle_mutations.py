@@ -122,6 +122,7 @@ def _pin_suite(v):
     yield lambda: pins.test_halfpel_flat_frame_keeps_the_cheapest_position(v)
     for args in [(48, 32, 16, 16, 4), (24, 16, 4, 8, 2), (32, 48, 16, 8, 5)]:
         yield lambda args=args: pins.test_sad_deviation_matches_sad_volume(v, *args)
+    yield lambda: pins.test_acbm_full_search_set_shrinks_as_qp_rises(v)
     yield lambda: pins.test_sad_deviation_closed_forms(v)
     yield lambda: pins.test_sad_deviation_of_a_known_global_shift(v, 3, -2)
 

@@ -603,3 +603,20 @@ def test_sad_deviation_blocks_agree_with_the_frame_call(orc):
     assert np.array_equal(bmn, mn.ravel()[blocks]) and np.array_equal(bdev, dev.ravel()[blocks])
     with pytest.raises(Exception):
         orc.sad_deviation_blocks(cur, ref, N, M, p, np.array([24], np.int32))
+
+
+def test_acbm_full_search_set_shrinks_as_qp_rises(orc):
+    """Cond. 1's threshold alpha + beta*Qp^2 grows with Qp and nothing else in
+    a block's decision depends on Qp once lambda is held fixed: the blocks
+    searched fully at a higher Qp are a subset of those at a lower Qp, and
+    the load never grows."""
+    frames = synth.load_sequence("textured-fast", 10, seed=500, n_frames=3)
+    prev, _, _, _, _ = orc.acbm(frames[1], frames[0], 16, 16, 15, 6595, orc.params(qp=28), None)
+    masks, loads = [], []
+    for qp in (10, 16, 22, 28, 34, 40):
+        _, _, mask, _, load = orc.acbm(frames[2], frames[1], 16, 16, 15, 6595, orc.params(qp=qp), prev)
+        masks.append(mask)
+        loads.append(load)
+    for lo, hi, llo, lhi in zip(masks, masks[1:], loads, loads[1:]):
+        assert np.all(hi <= lo) and np.all(lhi <= llo)
+    assert masks[0].sum() > masks[-1].sum()
