@@ -90,6 +90,12 @@ def _bind(lib):
     lib.oracle_sad_deviation_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int,
                                                 ctypes.POINTER(c_int), c_int, u32p, u32p]
     lib.oracle_sad_deviation_blocks.restype = c_int
+    lib.oracle_fsbm_pred.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32, i16p,
+                                     u32p, u32p]
+    lib.oracle_fsbm_pred.restype = c_int
+    lib.oracle_median_predictor.argtypes = [i16p, c_int, c_int, c_int, ctypes.POINTER(c_int),
+                                            ctypes.POINTER(c_int)]
+    lib.oracle_median_predictor.restype = None
     return lib
 
 
@@ -228,6 +234,32 @@ def sad_deviation(cur, ref, N: int, M: int, p: int):
                                         N, M, p, _ptr(mn, ctypes.c_uint32),
                                         _ptr(dev, ctypes.c_uint32)), "oracle_sad_deviation")
     return mn, dev
+
+
+def fsbm_pred(cur, ref, N: int, M: int, p: int, lam_q8: int):
+    """FSBM with R coded against the median predictor of the left, upper and
+    upper-right final vectors.  Returns (mv [BH,BW,2] int16, J, sad [BH,BW] u32)."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    if ref.shape != cur.shape:
+        raise ValueError("cur and ref differ in shape")
+    BH, BW = max(H // M, 1), max(W // N, 1)
+    mv = np.zeros((BH, BW, 2), np.int16)
+    J = np.zeros((BH, BW), np.uint32)
+    sad = np.zeros((BH, BW), np.uint32)
+    _check(_load().oracle_fsbm_pred(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N,
+                                    M, p, lam_q8, _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                                    _ptr(sad, ctypes.c_uint32)), "oracle_fsbm_pred")
+    return mv, J, sad
+
+
+def median_predictor(mv, bx: int, by: int):
+    """The median predictor (pmx, pmy) of block (bx, by) from a field mv [BH,BW,2]."""
+    mv = np.ascontiguousarray(mv, dtype=np.int16)
+    px, py = ctypes.c_int(0), ctypes.c_int(0)
+    _load().oracle_median_predictor(_ptr(mv, ctypes.c_int16), mv.shape[1], bx, by,
+                                    ctypes.byref(px), ctypes.byref(py))
+    return px.value, py.value
 
 
 def sad_deviation_blocks(cur, ref, N: int, M: int, p: int, blocks):

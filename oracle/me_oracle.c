@@ -576,3 +576,70 @@ int oracle_sad_deviation_blocks(const uint8_t *cur, const uint8_t *ref, int W, i
     free(vol);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * FSBM with a differentially coded vector (Sec. 2.1: R is the bits needed to
+ * transmit the vector; Sec. 2.2: vectors are coded differentially in the
+ * standards).  The predictor is the H.263-style median: component-wise median
+ * of the final vectors of the left (MV1), upper (MV2) and upper-right (MV3)
+ * blocks, where a block on the left edge takes MV1 = (0,0), a block on the
+ * right edge takes MV3 = (0,0), and a block in the top row takes
+ * MV2 = MV3 = MV1.  R(mv) = L(mvx - pmx) + L(mvy - pmy), L the signed
+ * Exp-Golomb length; ties as for FSBM.  Blocks in raster order: every
+ * predictor is final when it is read.
+ * ------------------------------------------------------------------------ */
+static int median3(int a, int b, int c)
+{
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return c < lo ? lo : (c > hi ? hi : c);
+}
+
+void oracle_median_predictor(const int16_t *mv, int BW, int bx, int by, int *pmx, int *pmy)
+{
+    int m1x = 0, m1y = 0, m2x, m2y, m3x = 0, m3y = 0;
+    if (bx > 0) { m1x = mv[2 * (by * BW + bx - 1)]; m1y = mv[2 * (by * BW + bx - 1) + 1]; }
+    if (by == 0) {
+        *pmx = m1x;
+        *pmy = m1y;
+        return;
+    }
+    m2x = mv[2 * ((by - 1) * BW + bx)];
+    m2y = mv[2 * ((by - 1) * BW + bx) + 1];
+    if (bx + 1 < BW) {
+        m3x = mv[2 * ((by - 1) * BW + bx + 1)];
+        m3y = mv[2 * ((by - 1) * BW + bx + 1) + 1];
+    }
+    *pmx = median3(m1x, m2x, m3x);
+    *pmy = median3(m1y, m2y, m3y);
+}
+
+int oracle_fsbm_pred(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+                     uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out)
+{
+    if (!cur || !ref || !mv_out || !J_out) return OR_ERR_ARG;
+    int st = check_shape(W, H, N, M, p, lambda_q8);
+    if (st) return st;
+    int BW = W / N, BH = H / M;
+    for (int by = 0; by < BH; by++)
+        for (int bx = 0; bx < BW; bx++) {
+            int pmx, pmy;
+            oracle_median_predictor(mv_out, BW, bx, by, &pmx, &pmy);
+            int bmx = 0, bmy = 0, have = 0;
+            uint32_t bJ = 0, bS = 0;
+            for (int mvy = -p; mvy <= p; mvy++)
+                for (int mvx = -p; mvx <= p; mvx++) {
+                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, mvx, mvy);
+                    uint32_t J = 256u * s + lambda_q8 * (uint32_t)(oracle_mv_bits(mvx - pmx) +
+                                                                   oracle_mv_bits(mvy - pmy));
+                    if (!have || better(J, mvx, mvy, bJ, bmx, bmy)) {
+                        have = 1; bJ = J; bS = s; bmx = mvx; bmy = mvy;
+                    }
+                }
+            int b = by * BW + bx;
+            mv_out[2 * b] = (int16_t)bmx;
+            mv_out[2 * b + 1] = (int16_t)bmy;
+            J_out[b] = bJ;
+            if (sad_out) sad_out[b] = bS;
+        }
+    return OR_OK;
+}

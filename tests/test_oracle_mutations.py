@@ -90,6 +90,14 @@ MUTANTS = {
     "SAD_deviation block origin transposed": (
         "block_sad(cur, ref, W, H, N, M, bx * N, by * M, u, v);",
         "block_sad(cur, ref, W, H, N, M, bx * M, by * N, u, v);"),
+    "median predictor takes the largest value": (
+        "    return c < lo ? lo : (c > hi ? hi : c);", "    return c > hi ? c : hi;"),
+    "top row predicts from the upper neighbours": (
+        "    if (by == 0) {\n        *pmx = m1x;", "    if (by < 0) {\n        *pmx = m1x;"),
+    "right edge keeps a stale upper-right vector": (
+        "    if (bx + 1 < BW) {\n        m3x", "    if (bx < BW) {\n        m3x"),
+    "predicted rate coded against zero": (
+        "(uint32_t)(oracle_mv_bits(mvx - pmx) +", "(uint32_t)(oracle_mv_bits(mvx) +"),
 }
 
 
@@ -123,6 +131,11 @@ def _pin_suite(v):
     for args in [(48, 32, 16, 16, 4), (24, 16, 4, 8, 2), (32, 48, 16, 8, 5)]:
         yield lambda args=args: pins.test_sad_deviation_matches_sad_volume(v, *args)
     yield lambda: pins.test_acbm_full_search_set_shrinks_as_qp_rises(v)
+    yield lambda: pins.test_median_predictor_edge_rules(v)
+    for args in [(64, 48, 16, 16, 4), (40, 32, 8, 8, 3)]:
+        yield lambda args=args: pins.test_fsbm_pred_matches_brute_force(v, *args)
+    yield lambda: pins.test_fsbm_pred_reduces_to_fsbm_without_rate(v)
+    yield lambda: pins.test_fsbm_pred_follows_a_global_shift(v)
     yield lambda: pins.test_sad_deviation_closed_forms(v)
     yield lambda: pins.test_sad_deviation_of_a_known_global_shift(v, 3, -2)
 

@@ -620,3 +620,115 @@ def test_acbm_full_search_set_shrinks_as_qp_rises(orc):
     for lo, hi, llo, lhi in zip(masks, masks[1:], loads, loads[1:]):
         assert np.all(hi <= lo) and np.all(lhi <= llo)
     assert masks[0].sum() > masks[-1].sum()
+
+
+# ---------------------------------------------------------------------------
+# FSBM with R coded against the median predictor (Sec. 2.1 R, Sec. 2.2
+# differential coding; H.263-style median of left, upper, upper-right)
+# ---------------------------------------------------------------------------
+def brute_predictor(field, bx, by):
+    """H.263 rules restated: left edge -> MV1 = 0; top row -> the predictor is
+    MV1; right edge -> MV3 = 0; else the component-wise middle value."""
+    BW = field.shape[1]
+    mv1 = tuple(field[by, bx - 1]) if bx > 0 else (0, 0)
+    if by == 0:
+        return mv1
+    mv2 = tuple(field[by - 1, bx])
+    mv3 = tuple(field[by - 1, bx + 1]) if bx + 1 < BW else (0, 0)
+    return tuple(sorted([mv1[c], mv2[c], mv3[c]])[1] for c in range(2))
+
+
+def brute_fsbm_pred(cur, ref, N, M, p, lam):
+    H, W = cur.shape
+    BH, BW = H // M, W // N
+    vol = brute_sad_volume(cur, ref, N, M, p)
+    mvs = np.arange(-p, p + 1)
+    bits = {d: len(eg_encode_signed(int(d))) for d in range(-2 * p, 2 * p + 1)}
+    MY, MX = np.meshgrid(mvs, mvs, indexing="ij")
+    L1 = (np.abs(MY) + np.abs(MX)).ravel()
+    field = np.zeros((BH, BW, 2), np.int64)
+    Jb = np.zeros((BH, BW), np.int64)
+    Sb = np.zeros((BH, BW), np.int64)
+    for by in range(BH):
+        for bx in range(BW):
+            px, py = brute_predictor(field, bx, by)
+            R = np.array([[bits[int(x) - px] + bits[int(y) - py] for x in mvs] for y in mvs])
+            j = (256 * vol[:, :, by, bx] + lam * R).ravel()
+            k = np.lexsort((MX.ravel(), MY.ravel(), L1, j))[0]
+            field[by, bx] = (MX.ravel()[k], MY.ravel()[k])
+            Jb[by, bx] = j[k]
+            Sb[by, bx] = vol[:, :, by, bx].ravel()[k]
+    return field, Jb, Sb
+
+
+def test_median_predictor_edge_rules(orc):
+    """Hand-worked fields: interior median per component, the left-edge zero,
+    the right-edge zero and the top-row copy of the left vector."""
+    f = np.zeros((3, 3, 2), np.int16)
+    f[0] = [(5, -1), (-2, 4), (7, 7)]
+    f[1] = [(1, 1), (0, 0), (0, 0)]
+    assert orc.median_predictor(f, 0, 0) == (0, 0)          # top-left: nothing coded yet
+    assert orc.median_predictor(f, 1, 0) == (5, -1)         # top row: left vector
+    assert orc.median_predictor(f, 2, 0) == (-2, 4)
+    # (1,1): left (1,1), up (-2,4), up-right (7,7) -> (1, 4)
+    assert orc.median_predictor(f, 1, 1) == (1, 4)
+    # (0,1): left edge -> (0,0), up (5,-1), up-right (-2,4) -> (0, 0)
+    assert orc.median_predictor(f, 0, 1) == (0, 0)
+    # (2,1): left (0,0), up (7,7), right edge -> (0,0) -> (0, 0)
+    assert orc.median_predictor(f, 2, 1) == (0, 0)
+    f[1, 1] = (3, -6)
+    # (2,1) again: left (3,-6), up (7,7), up-right 0 -> (3, 0)
+    assert orc.median_predictor(f, 2, 1) == (3, 0)
+    # (0,2): left 0, up (1,1), up-right (3,-6) -> (1, 0)
+    assert orc.median_predictor(f, 0, 2) == (1, 0)
+
+
+def blockwise_motion(W, H, N, M, p, seed):
+    """cur: every block copied from the reference at its own random offset in
+    [-p, p]^2 (edge clamp), 30 % of blocks flat instead, plus U{-12..12}
+    noise: a field with many distinct vectors for the predictor to mix."""
+    rng = np.random.default_rng(seed)
+    ref = synth.texture(rng, W, H).astype(int)
+    cur = np.zeros((H, W), int)
+    for by in range(H // M):
+        for bx in range(W // N):
+            dx, dy = rng.integers(-p, p + 1, 2)
+            ys = np.clip(np.arange(by * M, by * M + M) + dy, 0, H - 1)
+            xs = np.clip(np.arange(bx * N, bx * N + N) + dx, 0, W - 1)
+            cur[by * M:by * M + M, bx * N:bx * N + N] = ref[np.ix_(ys, xs)]
+            if rng.random() < 0.3:
+                cur[by * M:by * M + M, bx * N:bx * N + N] = rng.integers(100, 110)
+    cur = np.clip(cur + rng.integers(-12, 13, cur.shape), 0, 255).astype(np.uint8)
+    return cur, ref.astype(np.uint8)
+
+
+@pytest.mark.parametrize("W,H,N,M,p", [(64, 48, 16, 16, 4), (40, 32, 8, 8, 3), (24, 32, 4, 8, 2)])
+def test_fsbm_pred_matches_brute_force(orc, W, H, N, M, p):
+    """Block-wise random motion (many distinct neighbour vectors), lambda from
+    0 to values where the rate decides most blocks."""
+    cur, ref = blockwise_motion(W, H, N, M, p, W + H)
+    for lam in (0, 3000, 6595, 20000, 60000, 1 << 20):
+        mv, J, sad = orc.fsbm_pred(cur, ref, N, M, p, lam)
+        bmv, bJ, bs = brute_fsbm_pred(cur, ref, N, M, p, lam)
+        assert np.array_equal(mv, bmv) and np.array_equal(J, bJ) and np.array_equal(sad, bs), lam
+
+
+def test_fsbm_pred_reduces_to_fsbm_without_rate(orc):
+    seq = synth.config_sequence("qcif", seed=3, n_frames=2)
+    mv, J, sad = orc.fsbm_pred(seq[1], seq[0], 16, 16, 7, 0)
+    fmv, fJ, fs = orc.fsbm(seq[1], seq[0], 16, 16, 7, 0)
+    assert np.array_equal(mv, fmv) and np.array_equal(J, fJ) and np.array_equal(sad, fs)
+
+
+def test_fsbm_pred_follows_a_global_shift(orc):
+    """Noise-free global shift g: SAD 0 at g in every block; once the first
+    block has g every predictor is g, so R is 2 bits there and the whole field
+    is g, J = 2*lambda after the first block."""
+    rng = np.random.default_rng(8)
+    ref = synth.texture(rng, 64, 64)
+    gx, gy = 3, -2
+    cur = synth.shifted_copy(ref, -gx, -gy)
+    lam = 6595
+    mv, J, sad = orc.fsbm_pred(cur, ref, 16, 16, 5, lam)
+    assert np.all(mv[..., 0] == gx) and np.all(mv[..., 1] == gy) and np.all(sad == 0)
+    assert np.all(J.ravel()[1:] == 2 * lam)
