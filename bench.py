@@ -581,6 +581,31 @@ def main():
                 acc.append(es0.elapsed_time(es1))
     ss_frame_ms = statistics.median(ss_ms)
     fs_single_ms = statistics.median(fs1_ms)
+    # FSBM with the rate coded against the median predictor (a wavefront):
+    # the whole sequence in two launches, and one pair alone
+    pr_out = (torch.empty_like(f_mv), torch.empty_like(f_J), torch.empty_like(f_sad))
+    for _ in range(2):
+        me.me_fsbm_pred_sequence(frames, N, M, P, lam, out=pr_out)
+        me.me_fsbm_pred(frames[1], frames[0], N, M, P, lam, out=(f_mv[0], f_J[0], f_sad[0]))
+    torch.cuda.synchronize()
+    pr_seq_ms, pr_one_ms = [], []
+    for i in range(5):
+        for fn, acc in ((lambda: me.me_fsbm_pred_sequence(frames, N, M, P, lam, out=pr_out), pr_seq_ms),
+                        (lambda: me.me_fsbm_pred(frames[1 + i], frames[i], N, M, P, lam,
+                                                 out=(pr_out[0][0], pr_out[1][0], pr_out[2][0])),
+                         pr_one_ms)):
+            flush.fill_(1)
+            ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ep0.record(stream)
+            fn()
+            ep1.record(stream)
+            torch.cuda.synchronize()
+            acc.append(ep0.elapsed_time(ep1))
+    pred_ok = me.me_fsbm_pred_status(W, H_PAD, N, M, P, pairs) == 0
+    pred_frame_ms = statistics.median(pr_seq_ms) / pairs
+    pred_pair_ms = statistics.median(pr_one_ms)
+
     # the known-motion experiment of Sec. 3.1 / Fig. 3 (CIF, nine moved
     # frames, 16x16, p = 16, lambda = 0): one launch, then its error classes
     st_frames, st_g = synth.global_motion_sequence(41, 352, 288)
@@ -685,6 +710,10 @@ def main():
                           "absdiff_per_s": ABSDIFF_PER_FRAME / (ss_frame_ms * 1e-3) / 1e12,
                           "frac_of_peak": ABSDIFF_PER_FRAME / (ss_frame_ms * 1e-3) / peak_absdiff,
                           "unit": "T absdiff/s"},
+        "fsbm_pred": {"form": "me_fsbm_pred_sequence: rate against the median predictor "
+                              "(SAD volume + persistent wavefront), all pairs in two launches",
+                      "ms_per_frame": pred_frame_ms, "frames_per_s": 1e3 / pred_frame_ms,
+                      "single_pair_ms": pred_pair_ms, "status_ok": pred_ok},
         "motion_study": {"form": "me_motion_study: CIF original + 9 frames moved by known global "
                                  "vectors, 16x16, p=16, lambda=0, one launch",
                          "ms": study_ms, "classes": study_classes},

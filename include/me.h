@@ -189,6 +189,39 @@ int me_halfpel_sequence(const uint8_t *const *frames, int K, int W, int H, int N
                         uint32_t lambda_q8, const int16_t *mv_int, int16_t *mv_half_out,
                         uint32_t *J_out, uint32_t *sad_out, me_stream_t stream);
 
+/* ------------------------------------- FSBM with a predicted vector rate */
+
+/* FSBM where the vector is coded against a predictor (Sec. 2.1: R is the
+ * bits that transmit the vector; Sec. 2.2: the standards code vectors
+ * differentially).  pm = the H.263-style median predictor: component-wise
+ * median of the final vectors of the left (MV1), upper (MV2) and upper-right
+ * (MV3) blocks; MV1 = (0,0) on the left edge, MV3 = (0,0) on the right edge,
+ * and in the top row the predictor is MV1.  R = L(mvx - pmx) + L(mvy - pmy)
+ * with L = me_mv_bits; J_q8 = 256*SAD + lambda_q8*R; ties as me_fsbm.
+ * Blocks depend on their neighbours' results, so the search is a wavefront:
+ * one launch computes every candidate's SAD (uint16 volume), a second,
+ * persistent one takes the blocks in anti-diagonal order with bounded waits.
+ * Outputs as me_fsbm (mv_out, J_out required; sad_out nullable).  Scratch:
+ * one cached plan per (device, W, H, N, M, p, K) holding the SAD volume
+ * (2*ceil8((2p+1)^2) bytes per block and pair) and per-block flags,
+ * allocated at the first call and kept until exit; runs with one plan are
+ * ordered on the GPU. */
+int me_fsbm_pred(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
+                 uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
+                 me_stream_t stream);
+
+/* me_fsbm_pred for K independent consecutive pairs (pair k: reference
+ * frames[k], current frames[k+1]; frames a host array of K+1 device
+ * pointers, 1 <= K <= 64) in the same two launches; outputs [K][BH][BW]. */
+int me_fsbm_pred_sequence(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
+                          uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
+                          me_stream_t stream);
+
+/* Waits for `stream` and reports ME_ERR_TIMEOUT if a bounded wait of the last
+ * me_fsbm_pred / me_fsbm_pred_sequence run with this shape gave up (its
+ * outputs are then incomplete), else ME_OK.  K = 1 for me_fsbm_pred. */
+int me_fsbm_pred_status(int W, int H, int N, int M, int p, int K, me_stream_t stream);
+
 /* ------------------------------------------------- SAD statistics (Sec. 3.1) */
 
 /* FSBM (as me_fsbm) plus, for every block, the two statistics of the full

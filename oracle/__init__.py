@@ -93,6 +93,10 @@ def _bind(lib):
     lib.oracle_fsbm_pred.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32, i16p,
                                      u32p, u32p]
     lib.oracle_fsbm_pred.restype = c_int
+    lib.oracle_fsbm_pred_blocks.argtypes = [u8p, u8p, c_int, c_int, c_int, c_int, c_int, c_u32,
+                                            i16p, ctypes.POINTER(ctypes.c_int32), c_int, i16p, u32p,
+                                            u32p]
+    lib.oracle_fsbm_pred_blocks.restype = c_int
     lib.oracle_median_predictor.argtypes = [i16p, c_int, c_int, c_int, ctypes.POINTER(c_int),
                                             ctypes.POINTER(c_int)]
     lib.oracle_median_predictor.restype = None
@@ -250,6 +254,24 @@ def fsbm_pred(cur, ref, N: int, M: int, p: int, lam_q8: int):
     _check(_load().oracle_fsbm_pred(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W, H, N,
                                     M, p, lam_q8, _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
                                     _ptr(sad, ctypes.c_uint32)), "oracle_fsbm_pred")
+    return mv, J, sad
+
+
+def fsbm_pred_blocks(cur, ref, N: int, M: int, p: int, lam_q8: int, field, blocks):
+    """The listed blocks of the predicted-rate FSBM, each with its predictor
+    from `field` [BH,BW,2].  Returns (mv [n,2], J [n], sad [n])."""
+    cur, ref = _frame(cur), _frame(ref)
+    H, W = cur.shape
+    field = np.ascontiguousarray(field, dtype=np.int16)
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    mv = np.zeros((len(blocks), 2), np.int16)
+    J = np.zeros(len(blocks), np.uint32)
+    sad = np.zeros(len(blocks), np.uint32)
+    _check(_load().oracle_fsbm_pred_blocks(_ptr(cur, ctypes.c_uint8), _ptr(ref, ctypes.c_uint8), W,
+                                           H, N, M, p, lam_q8, _ptr(field, ctypes.c_int16),
+                                           _ptr(blocks, ctypes.c_int32), len(blocks),
+                                           _ptr(mv, ctypes.c_int16), _ptr(J, ctypes.c_uint32),
+                                           _ptr(sad, ctypes.c_uint32)), "oracle_fsbm_pred_blocks")
     return mv, J, sad
 
 

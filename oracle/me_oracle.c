@@ -613,6 +613,25 @@ void oracle_median_predictor(const int16_t *mv, int BW, int bx, int by, int *pmx
     *pmy = median3(m1y, m2y, m3y);
 }
 
+/* Full search of one block with the rate coded against (pmx, pmy). */
+static void pred_search_block(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M,
+                              int p, uint32_t lambda_q8, int bx, int by, int pmx, int pmy,
+                              int *mvx_o, int *mvy_o, uint32_t *J_o, uint32_t *sad_o)
+{
+    int bmx = 0, bmy = 0, have = 0;
+    uint32_t bJ = 0, bS = 0;
+    for (int mvy = -p; mvy <= p; mvy++)
+        for (int mvx = -p; mvx <= p; mvx++) {
+            uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, mvx, mvy);
+            uint32_t J = 256u * s + lambda_q8 * (uint32_t)(oracle_mv_bits(mvx - pmx) +
+                                                           oracle_mv_bits(mvy - pmy));
+            if (!have || better(J, mvx, mvy, bJ, bmx, bmy)) {
+                have = 1; bJ = J; bS = s; bmx = mvx; bmy = mvy;
+            }
+        }
+    *mvx_o = bmx; *mvy_o = bmy; *J_o = bJ; *sad_o = bS;
+}
+
 int oracle_fsbm_pred(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
                      uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out)
 {
@@ -622,24 +641,40 @@ int oracle_fsbm_pred(const uint8_t *cur, const uint8_t *ref, int W, int H, int N
     int BW = W / N, BH = H / M;
     for (int by = 0; by < BH; by++)
         for (int bx = 0; bx < BW; bx++) {
-            int pmx, pmy;
+            int pmx, pmy, mx, my;
+            uint32_t J, s;
             oracle_median_predictor(mv_out, BW, bx, by, &pmx, &pmy);
-            int bmx = 0, bmy = 0, have = 0;
-            uint32_t bJ = 0, bS = 0;
-            for (int mvy = -p; mvy <= p; mvy++)
-                for (int mvx = -p; mvx <= p; mvx++) {
-                    uint32_t s = block_sad(cur, ref, W, H, N, M, bx * N, by * M, mvx, mvy);
-                    uint32_t J = 256u * s + lambda_q8 * (uint32_t)(oracle_mv_bits(mvx - pmx) +
-                                                                   oracle_mv_bits(mvy - pmy));
-                    if (!have || better(J, mvx, mvy, bJ, bmx, bmy)) {
-                        have = 1; bJ = J; bS = s; bmx = mvx; bmy = mvy;
-                    }
-                }
+            pred_search_block(cur, ref, W, H, N, M, p, lambda_q8, bx, by, pmx, pmy, &mx, &my, &J, &s);
             int b = by * BW + bx;
-            mv_out[2 * b] = (int16_t)bmx;
-            mv_out[2 * b + 1] = (int16_t)bmy;
-            J_out[b] = bJ;
-            if (sad_out) sad_out[b] = bS;
+            mv_out[2 * b] = (int16_t)mx;
+            mv_out[2 * b + 1] = (int16_t)my;
+            J_out[b] = J;
+            if (sad_out) sad_out[b] = s;
         }
+    return OR_OK;
+}
+
+/* The listed blocks only, each with its predictor taken from `field` (a
+ * whole [BH][BW][2] field, e.g. a result under test): checks every listed
+ * block's own step at frame sizes the sequential frame call is too slow for. */
+int oracle_fsbm_pred_blocks(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M,
+                            int p, uint32_t lambda_q8, const int16_t *field, const int32_t *blocks,
+                            int nblocks, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out)
+{
+    if (!cur || !ref || !field || !blocks || !mv_out || !J_out || !sad_out || nblocks < 0)
+        return OR_ERR_ARG;
+    int st = check_shape(W, H, N, M, p, lambda_q8);
+    if (st) return st;
+    int BW = W / N, BH = H / M;
+    for (int k = 0; k < nblocks; k++)
+        if (blocks[k] < 0 || blocks[k] >= BW * BH) return OR_ERR_ARG;
+    for (int k = 0; k < nblocks; k++) {
+        int bx = blocks[k] % BW, by = blocks[k] / BW, pmx, pmy, mx, my;
+        oracle_median_predictor(field, BW, bx, by, &pmx, &pmy);
+        pred_search_block(cur, ref, W, H, N, M, p, lambda_q8, bx, by, pmx, pmy, &mx, &my,
+                          &J_out[k], &sad_out[k]);
+        mv_out[2 * k] = (int16_t)mx;
+        mv_out[2 * k + 1] = (int16_t)my;
+    }
     return OR_OK;
 }

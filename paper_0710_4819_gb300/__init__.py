@@ -19,7 +19,7 @@ __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
     "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_deviation",
-    "me_motion_study", "me_sad_peak", "Batch", "Server", "STATUS",
+    "me_motion_study", "me_fsbm_pred", "me_fsbm_pred_sequence", "me_fsbm_pred_status", "me_sad_peak", "Batch", "Server", "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -103,6 +103,11 @@ def load_library(build_if_missing: bool = True):
                            c_int),
             "me_halfpel_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                      u32, vp, vp, vp, vp, vp], c_int),
+            "me_fsbm_pred": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp],
+                             c_int),
+            "me_fsbm_pred_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
+                                       u32, vp, vp, vp, vp], c_int),
+            "me_fsbm_pred_status": ([c_int, c_int, c_int, c_int, c_int, c_int, vp], c_int),
             "me_sad_deviation": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp,
                                   vp], c_int),
             "me_motion_study": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
@@ -337,6 +342,41 @@ def me_halfpel_sequence(frames, N: int, M: int, p: int, lambda_q8: int, mv_int, 
                                               _ptr(mv), _ptr(J), _ptr(sad), _stream_ptr(stream)),
            "me_halfpel_sequence")
     return FsbmResult(mv, J, sad)
+
+
+def me_fsbm_pred(cur, ref, N: int, M: int, p: int, lambda_q8: int, out=None,
+                 stream=None) -> FsbmResult:
+    """FSBM with R coded against the median predictor of the left, upper and
+    upper-right final vectors (a wavefront over the blocks)."""
+    W, H = _frame_args(cur, ref)
+    mv, J, sad = out if out is not None else _outs(H, W, N, M, cur.device)
+    _check(load_library().me_fsbm_pred(_ptr(cur), _ptr(ref), W, H, N, M, p, int(lambda_q8),
+                                        _ptr(mv), _ptr(J), _ptr(sad), _stream_ptr(stream)),
+           "me_fsbm_pred")
+    return FsbmResult(mv, J, sad)
+
+
+def me_fsbm_pred_sequence(frames, N: int, M: int, p: int, lambda_q8: int, out=None,
+                          stream=None) -> FsbmResult:
+    """me_fsbm_pred of K consecutive pairs in two launches; outputs [K, BH, BW, ...]."""
+    torch = _torch()
+    arr, K, W, H = _frame_ptrs(frames)
+    dev = frames[0].device
+    if out is None:
+        BH, BW = H // M, W // N
+        out = (torch.empty((K, BH, BW, 2), dtype=torch.int16, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev),
+               torch.empty((K, BH, BW), dtype=torch.int32, device=dev))
+    mv, J, sad = out
+    _check(load_library().me_fsbm_pred_sequence(arr, K, W, H, N, M, p, int(lambda_q8), _ptr(mv),
+                                                _ptr(J), _ptr(sad), _stream_ptr(stream)),
+           "me_fsbm_pred_sequence")
+    return FsbmResult(mv, J, sad)
+
+
+def me_fsbm_pred_status(W: int, H: int, N: int, M: int, p: int, K: int = 1, stream=None) -> int:
+    """Waits for the stream; the status of the last predicted-rate run of this shape."""
+    return load_library().me_fsbm_pred_status(W, H, N, M, p, K, _stream_ptr(stream))
 
 
 @dataclass

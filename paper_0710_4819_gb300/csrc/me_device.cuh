@@ -179,12 +179,16 @@ struct FsPad {
 // shifted-word pitch is SP (fixed at compile time), else g.sp.  STATS: also
 // the sum and the minimum of the SAD over the searched positions of every
 // block, to stats[2*blk] and stats[2*blk+1] (shared memory, 2*bpc words).
-template <int N, int M, int T, int SP = 0, bool STATS = false>
+// VOL: instead of keys, every candidate's SAD is stored to
+// vol[blk*vstride + (mvy+p)*n + (mvx+p)] (global memory, uint16: a SAD is at
+// most 255*N*M = 65280); keys_out then holds no result.
+template <int N, int M, int T, int SP = 0, bool STATS = false, bool VOL = false>
 __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restrict__ ref,
                          int W, int H, int x0, int y0, const FsGeom& g, uint32_t lam,
                          uint32_t* smem, unsigned long long* keys_out,
                          unsigned long long* tr = nullptr, FsPad pad = FsPad{nullptr, 0, 0, 0},
-                         uint32_t* stats = nullptr) {
+                         uint32_t* stats = nullptr, uint16_t* __restrict__ vol = nullptr,
+                         int vstride = 0) {
   constexpr int NW = N / 4;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
@@ -344,7 +348,14 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       const int mvx = wcol - p;
       const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
       const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
-      if (fast) {
+      if (VOL) {
+        uint16_t* vb = vol + (size_t)blk * vstride + wcol;
+#pragma unroll
+        for (int k = 0; k < T; k++) {
+          const int r = row0 + k;
+          if (r < n) vb[r * n] = (uint16_t)acc[k];
+        }
+      } else if (fast) {
         // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the
         // same for the whole run and is added after the minimum
         uint32_t m = 0xffffffffu;

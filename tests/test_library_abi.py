@@ -98,6 +98,15 @@ def test_argument_errors_before_launch(lib):
     frames = (vp * 3)(fake, None, fake)
     assert lib.me_halfpel_sequence(frames, 2, 64, 64, 16, 16, 4, 0, fake, fake, fake, None,
                                    None) == 1
+    # predicted-rate FSBM: frame checks as FSBM, K in 1..64
+    assert lib.me_fsbm_pred(fake, fake, 64, 64, 16, 16, 4, 0, None, fake, None, None) == 1
+    assert lib.me_fsbm_pred(fake, fake, 64, 48, 16, 32, 4, 0, fake, fake, None, None) == 1
+    assert lib.me_fsbm_pred(fake, fake, 64, 40, 16, 16, 4, 0, fake, fake, None, None) == 2
+    frames = (vp * 3)(fake, fake, fake)
+    assert lib.me_fsbm_pred_sequence(frames, 0, 64, 64, 16, 16, 4, 0, fake, fake, None, None) == 1
+    assert lib.me_fsbm_pred_sequence(frames, 65, 64, 64, 16, 16, 4, 0, fake, fake, None, None) == 1
+    assert lib.me_fsbm_pred_status(64, 64, 16, 16, 4, 0, None) == 1
+    assert lib.me_fsbm_pred_status(64, 64, 16, 16, 0, 1, None) == 1
     # SAD statistics: both statistic outputs required, frame checks as FSBM
     assert lib.me_sad_deviation(fake, fake, 64, 64, 16, 16, 4, 0, None, None, fake, None,
                                 None) == 1

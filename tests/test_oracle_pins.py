@@ -732,3 +732,14 @@ def test_fsbm_pred_follows_a_global_shift(orc):
     mv, J, sad = orc.fsbm_pred(cur, ref, 16, 16, 5, lam)
     assert np.all(mv[..., 0] == gx) and np.all(mv[..., 1] == gy) and np.all(sad == 0)
     assert np.all(J.ravel()[1:] == 2 * lam)
+
+
+def test_fsbm_pred_blocks_agree_with_the_frame_call(orc):
+    """Given the frame call's own field, every block's one-block step
+    reproduces it (the sampled check used at large frame sizes)."""
+    cur, ref = blockwise_motion(64, 48, 8, 8, 3, 77)
+    mv, J, sad = orc.fsbm_pred(cur, ref, 8, 8, 3, 6595)
+    blocks = np.arange(mv.shape[0] * mv.shape[1], dtype=np.int32)
+    bmv, bJ, bs = orc.fsbm_pred_blocks(cur, ref, 8, 8, 3, 6595, mv, blocks)
+    assert np.array_equal(bmv, mv.reshape(-1, 2)) and np.array_equal(bJ, J.ravel())
+    assert np.array_equal(bs, sad.ravel())
