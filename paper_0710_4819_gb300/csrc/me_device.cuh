@@ -21,6 +21,14 @@ __device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t c) {
   return c;
 }
 
+// The first step of an accumulation (accumulator zero): the zero can be the
+// zero register, so no register has to be cleared per candidate.
+__device__ __forceinline__ uint32_t sad4_first(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(0u));
+  return d;
+}
+
 // Bits of the signed Exp-Golomb code of one MV component: 1 for 0, else
 // 2*floor(log2|v|) + 3.  R(mv) of eq. J is mv_bits(mvx) + mv_bits(mvy).
 __host__ __device__ __forceinline__ int mv_bits(int v) {
@@ -319,8 +327,6 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       const uint32_t* shp = sh + row0 * sp + blk * N + col;
       uint32_t acc[T];
 #pragma unroll
-      for (int k = 0; k < T; k++) acc[k] = 0;
-#pragma unroll
       for (int r = 0; r < T + M - 1; r++) {
         uint32_t rw[NW];
 #pragma unroll
@@ -331,7 +337,10 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
 #pragma unroll
           for (int k = 0; k < T; k++) {
             const int j = r - k;
-            if (j >= 0 && j < M) acc[k] = sad4(c[j][w], rw[w], acc[k]);
+            if (j == 0 && w == 0)
+              acc[k] = sad4_first(c[0][0], rw[0]);
+            else if (j >= 0 && j < M)
+              acc[k] = sad4(c[j][w], rw[w], acc[k]);
           }
         }
       }
@@ -359,10 +368,22 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
         // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the
         // same for the whole run and is added after the minimum
         uint32_t m = 0xffffffffu;
+        if (row0 + T <= n) {
+          // a whole run inside the window: no per-candidate bounds, and a
+          // tree of three-input minima
+          uint32_t v[T];
 #pragma unroll
-        for (int k = 0; k < T; k++) {
-          const int r = row0 + k;
-          if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
+          for (int k = 0; k < T; k++) v[k] = acc[k] * (256u << rb) + tabQ[row0 + k];
+          m = v[0];
+#pragma unroll
+          for (int k = 1; k + 1 < T; k += 2) m = __vimin3_u32(m, v[k], v[k + 1]);
+          if ((T & 1) == 0) m = min(m, v[T - 1]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < T; k++) {
+            const int r = row0 + k;
+            if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
+          }
         }
         m += jx << rb;
         const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
