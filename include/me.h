@@ -144,6 +144,12 @@ int me_fsbm_sequence(const uint8_t *const *frames, int K, int W, int H, int N, i
                      uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
                      me_stream_t stream);
 
+/* Waits for `stream`; ME_ERR_TIMEOUT if a bounded wait inside a
+ * me_fsbm_sequence run since the last call gave up (the persistent form used
+ * for 16x16 blocks, whose staging and searching warps hand buffers to each
+ * other; its outputs are then incomplete), else ME_OK.  Clears the record. */
+int me_fsbm_sequence_status(me_stream_t stream);
+
 /* ACBM over K consecutive frame pairs in one persistent launch: pair k's
  * previous field is pair k-1's output (prev_mv_field for pair 0, NULL =
  * zeros), exactly as K chained me_acbm calls, with identical outputs.  The

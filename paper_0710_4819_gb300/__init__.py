@@ -19,7 +19,7 @@ __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
     "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_deviation",
-    "me_motion_study", "me_fsbm_pred", "me_fsbm_pred_sequence", "me_fsbm_pred_status", "me_sad_peak", "Batch", "Server", "STATUS",
+    "me_motion_study", "me_fsbm_sequence_status", "me_fsbm_pred", "me_fsbm_pred_sequence", "me_fsbm_pred_status", "me_sad_peak", "Batch", "Server", "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -103,6 +103,7 @@ def load_library(build_if_missing: bool = True):
                            c_int),
             "me_halfpel_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
                                      u32, vp, vp, vp, vp, vp], c_int),
+            "me_fsbm_sequence_status": ([vp], c_int),
             "me_fsbm_pred": ([vp, vp, c_int, c_int, c_int, c_int, c_int, u32, vp, vp, vp, vp],
                              c_int),
             "me_fsbm_pred_sequence": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, c_int, c_int,
@@ -342,6 +343,12 @@ def me_halfpel_sequence(frames, N: int, M: int, p: int, lambda_q8: int, mv_int, 
                                               _ptr(mv), _ptr(J), _ptr(sad), _stream_ptr(stream)),
            "me_halfpel_sequence")
     return FsbmResult(mv, J, sad)
+
+
+def me_fsbm_sequence_status(stream=None) -> int:
+    """Waits for the stream; ME_ERR_TIMEOUT (5) if a bounded wait of a
+    persistent FSBM sequence run gave up since the last call, else 0."""
+    return load_library().me_fsbm_sequence_status(_stream_ptr(stream))
 
 
 def me_fsbm_pred(cur, ref, N: int, M: int, p: int, lambda_q8: int, out=None,

@@ -171,6 +171,88 @@ __host__ __device__ inline size_t fs_smem_bytes(const FsGeom& g) {
   return words * 4 + 16 * 8 + 8;                    // per-block minima (+ alignment)
 }
 
+// The SADs of one run: T candidates of one mvx column, consecutive mvy,
+// against the shifted-word rows at shp (pitch sp words).  c holds the
+// block's current pixels as packed words.  Reference row r serves every
+// candidate k with j = r - k in [0, M); word-major order puts consecutive SAD
+// steps on different candidates.
+template <int N, int M, int T>
+__device__ __forceinline__ void fs_run_sads(const uint32_t (&c)[M][N / 4], const uint32_t* shp,
+                                            int sp, uint32_t (&acc)[T]) {
+  constexpr int NW = N / 4;
+#pragma unroll
+  for (int r = 0; r < T + M - 1; r++) {
+    uint32_t rw[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) rw[w] = shp[r * sp + 4 * w];
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+#pragma unroll
+      for (int k = 0; k < T; k++) {
+        const int j = r - k;
+        if (j == 0 && w == 0)
+          acc[k] = sad4_first(c[0][0], rw[0]);
+        else if (j >= 0 && j < M)
+          acc[k] = sad4(c[j][w], rw[w], acc[k]);
+      }
+    }
+  }
+}
+
+// The best key of one run (candidates row0 .. row0+T-1 of window column wcol,
+// those past row n-1 skipped).  fast: J_q8 << rb plus the in-run rank fits
+// 32 bits (fast32_ok), so the run is reduced with 32-bit minima using tabQ;
+// else 64-bit keys from tabJ / tabK.
+template <int T>
+__device__ __forceinline__ unsigned long long fs_run_key(const uint32_t (&acc)[T], int row0, int wcol,
+                                                         int p, int n, uint32_t lam, int rb, bool fast,
+                                                         const uint32_t* tabJ, const uint32_t* tabK,
+                                                         const uint32_t* tabQ) {
+  const int mvx = wcol - p;
+  const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
+  const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
+  unsigned long long best = kNoKey;
+  if (fast) {
+    // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the same
+    // for the whole run and is added after the minimum
+    uint32_t m = 0xffffffffu;
+    if (row0 + T <= n) {
+      // a whole run inside the window: no per-candidate bounds, and a tree
+      // of three-input minima
+      uint32_t v[T];
+#pragma unroll
+      for (int k = 0; k < T; k++) v[k] = acc[k] * (256u << rb) + tabQ[row0 + k];
+      m = v[0];
+#pragma unroll
+      for (int k = 1; k + 1 < T; k += 2) m = __vimin3_u32(m, v[k], v[k + 1]);
+      if ((T & 1) == 0) m = min(m, v[T - 1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < T; k++) {
+        const int r = row0 + k;
+        if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
+      }
+    }
+    m += jx << rb;
+    const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
+    const int mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
+    const uint32_t lo = ((amx + (uint32_t)(mvy < 0 ? -mvy : mvy)) << 17) +
+                        (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)wcol;
+    best = ((unsigned long long)J << 32) | lo;
+  } else {
+    const uint32_t kx = (amx << 17) + (uint32_t)wcol;
+#pragma unroll
+    for (int k = 0; k < T; k++) {
+      const int r = row0 + k;
+      if (r < n) {
+        const uint32_t J = acc[k] * 256u + jx + tabJ[r];
+        best = umin64(best, ((unsigned long long)J << 32) | (kx + tabK[r]));
+      }
+    }
+  }
+  return best;
+}
+
 // An edge-padded copy of the reference (margin P on every side, rows of
 // `pitch` bytes, 16-byte aligned; `rows` rows): when given, fs_group stages
 // its window from it with asynchronous 16-byte copies (one round trip, no
@@ -326,24 +408,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       const int row0 = seg * T;
       const uint32_t* shp = sh + row0 * sp + blk * N + col;
       uint32_t acc[T];
-#pragma unroll
-      for (int r = 0; r < T + M - 1; r++) {
-        uint32_t rw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) rw[w] = shp[r * sp + 4 * w];
-        // word-major order: consecutive SAD steps go to different candidates
-#pragma unroll
-        for (int w = 0; w < NW; w++) {
-#pragma unroll
-          for (int k = 0; k < T; k++) {
-            const int j = r - k;
-            if (j == 0 && w == 0)
-              acc[k] = sad4_first(c[0][0], rw[0]);
-            else if (j >= 0 && j < M)
-              acc[k] = sad4(c[j][w], rw[w], acc[k]);
-          }
-        }
-      }
+      fs_run_sads<N, M, T>(c, shp, sp, acc);
       if (STATS) {
 #pragma unroll
         for (int k = 0; k < T; k++)
@@ -354,9 +419,6 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
       }
       // cost and key of each candidate of the run (mvx = c0 + col - p)
       const int wcol = g.c0 + col;
-      const int mvx = wcol - p;
-      const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
-      const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
       if (VOL) {
         uint16_t* vb = vol + (size_t)blk * vstride + wcol;
 #pragma unroll
@@ -364,43 +426,8 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
           const int r = row0 + k;
           if (r < n) vb[r * n] = (uint16_t)acc[k];
         }
-      } else if (fast) {
-        // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the
-        // same for the whole run and is added after the minimum
-        uint32_t m = 0xffffffffu;
-        if (row0 + T <= n) {
-          // a whole run inside the window: no per-candidate bounds, and a
-          // tree of three-input minima
-          uint32_t v[T];
-#pragma unroll
-          for (int k = 0; k < T; k++) v[k] = acc[k] * (256u << rb) + tabQ[row0 + k];
-          m = v[0];
-#pragma unroll
-          for (int k = 1; k + 1 < T; k += 2) m = __vimin3_u32(m, v[k], v[k + 1]);
-          if ((T & 1) == 0) m = min(m, v[T - 1]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < T; k++) {
-            const int r = row0 + k;
-            if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
-          }
-        }
-        m += jx << rb;
-        const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
-        const int mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
-        const uint32_t lo = ((amx + (uint32_t)(mvy < 0 ? -mvy : mvy)) << 17) +
-                            (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)wcol;
-        best = umin64(best, ((unsigned long long)J << 32) | lo);
       } else {
-        const uint32_t kx = (amx << 17) + (uint32_t)wcol;
-#pragma unroll
-        for (int k = 0; k < T; k++) {
-          const int r = row0 + k;
-          if (r < n) {
-            const uint32_t J = acc[k] * 256u + jx + tabJ[r];
-            best = umin64(best, ((unsigned long long)J << 32) | (kx + tabK[r]));
-          }
-        }
+        best = umin64(best, fs_run_key<T>(acc, row0, wcol, p, n, lam, rb, fast, tabJ, tabK, tabQ));
       }
       seg += dseg;
       col += dcol;

@@ -390,7 +390,10 @@ static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* 
 int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
                 uint32_t lam, int16_t* mv, uint32_t* J, uint32_t* sad, cudaStream_t s) {
   FsPlan pl = fs_plan(N, M, p, W / N);
-  plan_override(N, M, &pl, p, W / N);
+  if (!plan_override(N, M, &pl, p, W / N) && fsbm_pipe_applies(N, M, p)) {
+    const uint8_t* frames[2] = {ref, cur};
+    return launch_fsbm_pipe(frames, 1, W, H, p, lam, mv, J, sad, s);
+  }
   ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
 }
 

@@ -426,6 +426,13 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max);
 FsPlan fs_plan_latency(int N, int M, int p);
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit);
 
+// The pipelined persistent full search (16x16 blocks, windows of 8 blocks
+// within the compile-time pitch): K frame pairs frames[k] -> frames[k+1]
+// (host array of device pointers) in one launch; outputs [K][BH][BW].
+bool fsbm_pipe_applies(int N, int M, int p);
+int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
+                     int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s);
+
 // Calls FN<N, M, T>(...) for the run lengths instantiated per block shape
 // (pl.T chooses among them for 16x16); expects N, M and pl in scope.
 #define ME_DISPATCH_FS(FN, ...)                                                      \

@@ -90,6 +90,271 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, i
   }
 }
 
+// ------------------------------------------------------------------ FSBM, pipelined
+//
+// The same full search as k_fsbm_seq as one persistent CTA per SM that
+// overlaps staging with searching.  Two producer warps stage the windows of
+// the CTA's groups (kPipeBpc adjacent blocks of one block row of one pair;
+// groups blockIdx.x, blockIdx.x + gridDim.x, ...) into two shared-memory
+// buffers in turn; fourteen consumer warps run the searches.  A group's runs
+// (block-major, then segment, then column) are dealt in rounds of 32, one
+// per lane, each consumer warp taking a fixed contiguous range of rounds, and
+// a warp moves on to the next group as soon as its own rounds are done --
+// the uneven shares of a group (2600 runs over 14 warps at p = 32) no longer
+// leave lanes or warps idle until the slowest finishes, and staging is off
+// the search's path.  The last consumer warp to finish a group writes its
+// results and frees the buffer.  Every wait is bounded (SM cycle count); a
+// wait that gives up records ME_ERR_TIMEOUT for me_fsbm_sequence_status.
+constexpr int kPipeThreads = 512;
+#ifndef ME_PIPE_PRODUCERS
+#define ME_PIPE_PRODUCERS 4
+#endif
+constexpr int kPipeProducers = ME_PIPE_PRODUCERS;               // warps
+constexpr int kPipeConsumers = kPipeThreads / 32 - kPipeProducers;
+constexpr int kPipeBpc = 8;
+
+__device__ int g_fsbm_pipe_error = 0;
+
+template <int N, int M, int T>
+__host__ __device__ inline size_t pipe_smem_bytes(int p) {
+  const FsGeom g = fs_geom<N, M, T>(p, kPipeBpc, 32, 0, 0, kSeqSP);
+  const size_t words = 3 * (size_t)g.rows + (size_t)g.rows * g.wbw +
+                       2 * ((size_t)kPipeBpc * M * (N / 4) + (size_t)g.rows * kSeqSP);
+  return 4 * words;
+}
+
+// Shared-memory barrier objects (mbarrier) hand the two buffers between the
+// roles: full[b] completes a phase when the producers have staged a group
+// into buffer b, empty[b] when every consumer thread is through it.  A
+// waiting thread sleeps in the barrier's try_wait (suspend-time hint), so
+// waiting costs no issue slots; the wait is bounded by the SM cycle count and
+// gives up early when another wait has (err).
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* err,
+                                          long long lim) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    if (*err) return false;
+    if (clock64() - t0 > lim) {
+      *err = 1;
+      atomicExch(&g_fsbm_pipe_error, (int)ME_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
+    SeqFrames fr, int W, int H, int p, uint32_t lam, int groups, long long lim,
+    int16_t* __restrict__ mv_out, uint32_t* __restrict__ J_out, uint32_t* __restrict__ sad_out) {
+  constexpr int NW = N / 4, B = kPipeBpc, SP = kSeqSP;
+  constexpr int PT = 32 * kPipeProducers, CT = 32 * kPipeConsumers;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long red[2][B];
+  __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
+  __shared__ int err_s, go_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const FsGeom g = fs_geom<N, M, T>(p, B, 32, 0, 0, SP);
+  const int n = g.n, nc = g.nc;
+  const int BW = W / N, BH = H / M, nbf = BW * BH;
+  const int gpr = (BW + B - 1) / B;
+  uint32_t* tabJ = smem;
+  uint32_t* tabK = tabJ + g.rows;
+  uint32_t* tabQ = tabK + g.rows;
+  uint32_t* raw = tabQ + g.rows;                        // [rows][wbw], producers only
+  // buffer b: current blocks [B][M][NW], then shifted words [rows][SP]
+  const int bstride = B * M * NW + g.rows * SP;
+  uint32_t* const buf0 = raw + g.rows * g.wbw;
+  const bool fast = fast32_ok(N, M, p, lam);
+  const int rb = rank_bits(p);
+  for (int r = tid; r < g.rows; r += kPipeThreads) {
+    const int mvy = r - p;
+    const int a = mvy < 0 ? -mvy : mvy;
+    tabJ[r] = lam * (uint32_t)mv_bits(mvy);
+    tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
+    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
+  }
+  if (tid < 2 * B) red[tid / B][tid % B] = kNoKey;
+  if (tid == 0) {
+    err_s = 0;
+    mbar_init(&full_bar[0], PT);
+    mbar_init(&full_bar[1], PT);
+    mbar_init(&empty_bar[0], CT);
+    mbar_init(&empty_bar[1], CT);
+  }
+  __syncthreads();
+  const int mine = groups > (int)blockIdx.x ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp < kPipeProducers) {
+    // ---------------- producers: stage group i into buffer i & 1; once its
+    // consumers are through group i - 2 in that buffer, write that group's
+    // results first
+    const int pt = tid;
+    // results of group j (its consumers done): the per-block minima -> outputs
+    auto finish = [&](int j) {
+      const int b = j & 1;
+      if (pt == 0) go_s = mbar_wait(&empty_bar[b], (unsigned)((j >> 1) & 1), &err_s, lim) ? 1 : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      const bool go = go_s != 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      if (!go) return false;
+      const int gj = (int)blockIdx.x + j * (int)gridDim.x;
+      const int k = gj / (BH * gpr), rem = gj - k * (BH * gpr);
+      const int by = rem / gpr, bx0 = (rem - by * gpr) * B;
+      if (pt < B) {
+        if (bx0 + pt < BW) {
+          const Decoded d = decode_key(red[b][pt], p, lam);
+          const size_t o = (size_t)k * nbf + (size_t)by * BW + bx0 + pt;
+          mv_out[2 * o] = (int16_t)d.mvx;
+          mv_out[2 * o + 1] = (int16_t)d.mvy;
+          J_out[o] = d.J;
+          if (sad_out) sad_out[o] = d.sad;
+        }
+        red[b][pt] = kNoKey;
+      }
+      return true;
+    };
+    bool ok = true;
+    for (int i = 0; i < mine && ok; i++) {
+      const int b = i & 1;
+      if (i >= 2 && !finish(i - 2)) { ok = false; break; }
+      const int gi = (int)blockIdx.x + i * (int)gridDim.x;
+      const int k = gi / (BH * gpr), rem = gi - k * (BH * gpr);
+      const int by = rem / gpr, bx0 = (rem - by * gpr) * B;
+      const int x0 = bx0 * N, y0 = by * M;
+      const uint8_t* __restrict__ cur = fr.f[k + 1];
+      const uint8_t* __restrict__ ref = fr.f[k];
+      uint32_t* cw = buf0 + b * bstride;
+      for (int e = pt; e < B * M * NW; e += PT) {
+        const int blk = e / (M * NW), rm = e % (M * NW), j = rm / NW, w = rm % NW;
+        cw[e] = bx0 + blk < BW
+                    ? *reinterpret_cast<const uint32_t*>(cur + (size_t)(y0 + j) * W + x0 + blk * N + 4 * w)
+                    : 0u;
+      }
+      // raw window rows from the aligned word at or left of column x0 - p:
+      // producer warp pw takes rows pw, pw + kPipeProducers, ...; its lanes
+      // the words of a row (wbw <= 64).  Windows inside the frame are copied
+      // asynchronously; the others are clamped byte by byte.
+      const int pw = warp;
+      const int wx0 = x0 - p;
+      const int A0 = (wx0 >> 2) << 2;
+      const int s0 = wx0 - A0;
+      const bool inside = A0 >= 0 && A0 + 4 * g.wbw <= W;
+      for (int r = pw; r < g.rows; r += kPipeProducers) {
+        const uint8_t* rowp = ref + (size_t)clampi(y0 - p + r, 0, H - 1) * W + A0;
+        uint32_t* dst = raw + r * g.wbw;
+        for (int q = lane; q < g.wbw; q += 32) {
+          if (inside) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(rowp + 4 * q)
+                         : "memory");
+          } else {
+            uint32_t v = 0;
+#pragma unroll
+            for (int bb = 0; bb < 4; bb++)
+              v |= (uint32_t)ref[(size_t)clampi(y0 - p + r, 0, H - 1) * W +
+                                 clampi(A0 + 4 * q + bb, 0, W - 1)] << (8 * bb);
+            dst[q] = v;
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      // shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3, four consecutive
+      // o per lane from the three raw words that hold them
+      uint32_t* sh = cw + B * M * NW;
+      const int quads = (g.pos + 3) >> 2;
+      for (int r = pw; r < g.rows; r += kPipeProducers) {
+        for (int qd = lane; qd < quads; qd += 32) {
+          const int o = 4 * qd;
+          // (the third word may lie past the row, and is then not used)
+          const uint32_t* row = raw + r * g.wbw + ((s0 + o) >> 2);
+          const uint32_t w0 = row[0], w1 = row[1], w2 = row[2];
+          const int t0 = (s0 + o) & 3;
+          uint32_t* dst = sh + r * SP + o;
+#pragma unroll
+          for (int d = 0; d < 4; d++) {
+            const int t = t0 + d;            // byte offset from w0, 0 .. 6
+            if (o + d < g.pos)
+              dst[d] = t < 4 ? __funnelshift_r(w0, w1, 8 * t) : __funnelshift_r(w1, w2, 8 * (t - 4));
+          }
+        }
+      }
+      // every producer's stores before its arrival (raw is rewritten only
+      // after the next group's first producer barrier)
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      mbar_arrive(&full_bar[b]);
+    }
+    // the last two groups' results
+    for (int j = mine - 2; ok && j < mine; j++)
+      if (j >= 0 && !finish(j)) ok = false;
+    return;
+  }
+
+  // ---------------- consumers
+  const int cw_id = warp - kPipeProducers;
+  const int F = B * g.tasks;
+  const int R = (F + 31) >> 5;
+  const int q0 = (cw_id * R) / kPipeConsumers, q1 = ((cw_id + 1) * R) / kPipeConsumers;
+  const int dseg = 32 / nc, dcol = 32 - (32 / nc) * nc;
+  uint32_t c[M][NW];
+  for (int i = 0; i < mine; i++) {
+    const int b = i & 1;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, lim) ? 1 : 0;
+    ok = __shfl_sync(FULL, ok, 0);
+    if (!ok) break;
+    __syncwarp();
+    // every lane acquires the producers' stores itself (the phase is complete)
+    mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, lim);
+    const int gi = (int)blockIdx.x + i * (int)gridDim.x;
+    const int rem = gi % (BH * gpr);
+    const int bx0 = (rem % gpr) * B;
+    const int nb = min(B, BW - bx0);
+    const uint32_t* cwb = buf0 + b * bstride;
+    const uint32_t* sh = cwb + B * M * NW;
+    int f = 32 * q0 + lane;
+    int blk = f / g.tasks;
+    const int t0 = f - blk * g.tasks;
+    int seg = t0 / nc, col = t0 - (t0 / nc) * nc;
+    for (int q = q0; q < q1; q++, f += 32) {
+      if (f < F && blk < nb) {
+#pragma unroll
+        for (int j = 0; j < M; j++)
+#pragma unroll
+          for (int w = 0; w < NW; w++) c[j][w] = cwb[(blk * M + j) * NW + w];
+        const int row0 = seg * T;
+        uint32_t acc[T];
+        fs_run_sads<N, M, T>(c, sh + row0 * SP + blk * N + col, SP, acc);
+        atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
+      }
+      seg += dseg;
+      col += dcol;
+      if (col >= nc) { col -= nc; seg++; }
+      while (seg >= g.nseg) { seg -= g.nseg; blk++; }
+    }
+    mbar_arrive(&empty_bar[b]);
+  }
+}
+
 // ------------------------------------------------------------------ ACBM
 
 
@@ -548,6 +813,44 @@ static int get_seq_plan(int W, int H, int N, int M, int p, int K, SeqPlan** out)
   return ME_OK;
 }
 
+bool fsbm_pipe_applies(int N, int M, int p) {
+  // 16x16 blocks with windows of kPipeBpc blocks within the kSeqSP pitch
+  // (ME_FSBM_PIPE=0 selects the one-launch-per-group kernels instead)
+  const char* pe = std::getenv("ME_FSBM_PIPE");
+  if (pe && pe[0] == '0') return false;
+  return N == 16 && M == 16 && (kPipeBpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP;
+}
+
+int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
+                     int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  if (K < 1 || K > kSeqMax) return ME_ERR_ARG;
+  SeqFrames fr;
+  std::memset(&fr, 0, sizeof(fr));
+  for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
+  const FsPlan pl = fs_plan(16, 16, p, W / 16);
+  int dev = 0, nsm = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int BW = W / 16, BH = H / 16;
+  const int groups = K * BH * ((BW + kPipeBpc - 1) / kPipeBpc);
+  const int pgrid = std::min(nsm, groups);
+  const long long lim = wait_cycles(1000000000ll);
+#define X(t_)                                                                                 \
+  if (pl.T == t_) {                                                                           \
+    auto kern = k_fsbm_pipe<16, 16, t_>;                                                      \
+    const size_t smem = pipe_smem_bytes<16, 16, t_>(p);                                       \
+    const int st = ensure_dynamic_smem((const void*)kern, smem);                              \
+    if (st) return st;                                                                        \
+    kern<<<pgrid, kPipeThreads, smem, s>>>(fr, W, H, p, lam, groups, lim, mv_out, J_out,      \
+                                           sad_out);                                          \
+    ME_CUDA(cudaGetLastError());                                                              \
+    return ME_OK;                                                                             \
+  }
+  X(8) X(11) X(13) X(16)
+#undef X
+  return ME_ERR_ARG;
+}
+
 static int check_seq_frames(const uint8_t* const* frames, int K) {
   if (!frames || K < 1 || K > kSeqMax) return ME_ERR_ARG;
   for (int k = 0; k <= K; k++)
@@ -576,6 +879,9 @@ int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
   const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (fsbm_pipe_applies(N, M, p)) {
+    return launch_fsbm_pipe(frames, K, W, H, p, lambda_q8, mv_out, J_out, sad_out, s);
+  }
   // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 34
   // at 8 blocks per CTA) uses the build with a compile-time row pitch
   if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP) {
@@ -662,6 +968,17 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   ME_CUDA(cudaEventRecord(pl->last, s));
   pl->ran = true;
   return ME_OK;
+}
+
+int me_fsbm_sequence_status(me_stream_t stream) {
+  ME_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  int e = 0;
+  ME_CUDA(cudaMemcpyFromSymbol(&e, g_fsbm_pipe_error, sizeof(int)));
+  if (e) {
+    const int zero = 0;
+    ME_CUDA(cudaMemcpyToSymbol(g_fsbm_pipe_error, &zero, sizeof(int)));
+  }
+  return e ? e : ME_OK;
 }
 
 int me_acbm_sequence_status(int W, int H, int N, int M, int p, int K, me_stream_t stream) {

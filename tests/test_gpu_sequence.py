@@ -38,6 +38,43 @@ def test_fsbm_sequence_matches_oracle(me, orc):
         assert np.array_equal(_u32(r.sad[k]), sad), k
 
 
+@pytest.mark.parametrize("w,h,p,K", [(176, 144, 16, 9), (352, 288, 16, 4), (352, 288, 34, 3),
+                                     (1280, 720, 32, 3), (208, 48, 9, 5), (16, 16, 12, 2)])
+def test_fsbm_sequence_pipelined_matches_oracle(me, orc, w, h, p, K, monkeypatch):
+    """The persistent staging/searching form (16x16, run length 13) against
+    the oracle pair by pair and against the one-launch-per-group form, on
+    grids whose last group of a row is short (11, 22, 13 and 1 blocks per row
+    against 8 per group) and on several pairs per CTA."""
+    import torch
+    seq = synth.scene_sequence(900 + w + p, w, h, K + 1, n_objects=4, vmax=5)
+    lam = orc.lambda_q8(30)
+    frames = torch.from_numpy(seq).cuda()
+    r = me.me_fsbm_sequence(frames, 16, 16, p, lam)
+    assert me.me_fsbm_sequence_status() == 0
+    monkeypatch.setenv("ME_FSBM_PIPE", "0")
+    r0 = me.me_fsbm_sequence(frames, 16, 16, p, lam)
+    torch.cuda.synchronize()
+    assert torch.equal(r.mv, r0.mv) and torch.equal(r.J, r0.J) and torch.equal(r.sad, r0.sad)
+    for k in range(K):
+        mv, J, sad = orc.fsbm(seq[k + 1], seq[k], 16, 16, p, lam, nthreads=8)
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), k
+        assert np.array_equal(_u32(r.J[k]), J), k
+        assert np.array_equal(_u32(r.sad[k]), sad), k
+
+
+def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me):
+    """1080p p = 32, 12 pairs (the bench's kernel): equal to me_fsbm per pair."""
+    import torch
+    seq = torch.from_numpy(synth.config_sequence("1080p", seed=7, n_frames=13)).cuda()
+    lam = me.me_lambda_q8(28)
+    r = me.me_fsbm_sequence(seq, 16, 16, 32, lam)
+    assert me.me_fsbm_sequence_status() == 0
+    for k in range(12):
+        f = me.me_fsbm(seq[k + 1], seq[k], 16, 16, 32, lam)
+        torch.cuda.synchronize()
+        assert torch.equal(r.mv[k], f.mv) and torch.equal(r.J[k], f.J) and torch.equal(r.sad[k], f.sad), k
+
+
 @pytest.mark.parametrize("name,n,p,qp", [("qcif", 10, 16, 28), ("cif", 5, 16, 40),
                                          ("1080p", 3, 32, 28)])
 def test_acbm_sequence_matches_chained_oracle(me, orc, name, n, p, qp):
