@@ -38,9 +38,9 @@ BW, BH = W // N, H_PAD // M
 NBLK = BW * BH
 NCAND = (2 * P + 1) ** 2
 ABSDIFF_PER_FRAME = NBLK * NCAND * N * M          # 8.83e9 for FSBM
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fsbm_seq<16,16,13,193>
-# on 8 frames (7 pairs): 16.760320 MB + 0 B, i.e. per frame of the sequence
-FSBM_SEQ_DRAM_BYTES_PER_FRAME = 16.760320e6 / 8
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fsbm_pipe<16,16,13>
+# on 13 frames (12 pairs): 27.201792 MB + 0 B, i.e. per frame of the sequence
+FSBM_SEQ_DRAM_BYTES_PER_FRAME = 27.201792e6 / 13
 WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
 
 
@@ -723,12 +723,12 @@ def main():
                      "p50_ms": pct(pair_ms, 0.5), "p99_ms": pct(pair_ms, 0.99),
                      "outputs_identical_to_sequence": identical},
         "p99_ms": pct(pair_ms, 0.99),
-        "roofline": {"bound": "alu", "kernel": "k_fsbm_seq", "achieved": achieved / 1e12,
+        "roofline": {"bound": "alu", "kernel": "k_fsbm_pipe", "achieved": achieved / 1e12,
                      "peak": peak_absdiff / 1e12, "unit": "T absdiff/s",
                      "frac": achieved / peak_absdiff,
                      # DRAM bytes of one launch over the whole sequence: ncu
-                     # dram__bytes_read+write of the same kernel on the 8-frame
-                     # case (16.76 MB, every frame read once), scaled by frames
+                     # dram__bytes_read+write of the same kernel on the 13-frame
+                     # case (27.20 MB, every frame read once), scaled by frames
                      "traffic": FSBM_SEQ_DRAM_BYTES_PER_FRAME * (pairs + 1),
                      "traffic_unit": "bytes/launch",
                      "algorithmic_bytes": (pairs + 1) * W * H_PAD,
@@ -736,7 +736,7 @@ def main():
                                     "(lane rate measured by me_sad_peak)"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,   # k_fsbm_seq; k_seq_begin, k_seq_prologue, k_acbm_seq
+        "gpu_launches": 4 * args.steps,   # k_fsbm_pipe; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
     }
