@@ -16,7 +16,8 @@
 //
 //   k_sad_volume : the FSBM engine (fs_group, VOL mode) stores every
 //                  candidate's SAD of every block as uint16 -- fully
-//                  parallel, the same ALU-bound packed-SAD work as FSBM;
+//                  parallel, the same ALU-bound packed-SAD work as FSBM
+//                  (16x16 blocks: the pipelined search in its volume mode);
 //   k_pred_wave  : a persistent kernel; each CTA claims blocks in (wave,
 //                  frame, row) order, stages the block's SAD volume into
 //                  shared memory and lists the candidates that can still win
@@ -412,6 +413,14 @@ static int launch_volume_t(const PredFrames& fr, int K, int W, int H, int p, int
 
 static int launch_volume(const PredFrames& fr, int K, int W, int H, int N, int M, int p,
                          int vstride, uint16_t* vol, cudaStream_t s) {
+  if (fsbm_pipe_applies(N, M, p)) {
+    // 16x16: the pipelined persistent search in its volume mode
+    PipeOut po;
+    std::memset(&po, 0, sizeof(po));
+    po.vol = vol;
+    po.vstride = vstride;
+    return launch_fsbm_pipe_mode(kPipeVolume, fr.f, K, W, H, p, 0u, po, s);
+  }
   const FsPlan pl = fs_plan(N, M, p, W / N);
   const int bpc = pl.threads / pl.G;
   if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kVolSP) {

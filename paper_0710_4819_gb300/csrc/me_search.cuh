@@ -433,6 +433,25 @@ bool fsbm_pipe_applies(int N, int M, int p);
 int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
                      int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s);
 
+// Outputs of the pipelined search in its three modes: kPipeKeys (mv, J, sad;
+// each nullable), kPipeStats (also smin, sdev: SAD_min and SAD_deviation,
+// required), kPipeVolume (every candidate's SAD: vol + block * vstride +
+// (mvy+p)*(2p+1) + (mvx+p), uint16).  ref_fixed: every pair k compares
+// frames[k+1] with frames[0] instead of frames[k].
+enum { kPipeKeys = 0, kPipeStats = 1, kPipeVolume = 2 };
+struct PipeOut {
+  int16_t* mv;
+  uint32_t* J;
+  uint32_t* sad;
+  uint32_t* smin;
+  uint32_t* sdev;
+  uint16_t* vol;
+  int vstride;
+  int ref_fixed;
+};
+int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, int H, int p,
+                          uint32_t lam, const PipeOut& out, cudaStream_t s);
+
 // Calls FN<N, M, T>(...) for the run lengths instantiated per block shape
 // (pl.T chooses among them for 16x16); expects N, M and pl in scope.
 #define ME_DISPATCH_FS(FN, ...)                                                      \

@@ -160,14 +160,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volati
   }
 }
 
-template <int N, int M, int T>
-__global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
-    SeqFrames fr, int W, int H, int p, uint32_t lam, int groups, long long lim,
-    int16_t* __restrict__ mv_out, uint32_t* __restrict__ J_out, uint32_t* __restrict__ sad_out) {
+// MODE: kPipeKeys (the search: best key per block), kPipeStats (also the sum
+// and the minimum of the SAD over the window per block: SAD_min and
+// SAD_deviation, Sec. 3.1), kPipeVolume (every candidate's SAD to a volume).
+template <int N, int M, int T, int MODE>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int W, int H, int p,
+                                                              uint32_t lam, int groups, long long lim,
+                                                              PipeOut out) {
   constexpr int NW = N / 4, B = kPipeBpc, SP = kSeqSP;
   constexpr int PT = 32 * kPipeProducers, CT = 32 * kPipeConsumers;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long red[2][B];
+  __shared__ uint32_t ssum_s[2][B], smin_s[2][B];
   __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
   __shared__ int err_s, go_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -192,7 +196,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
     tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
   }
-  if (tid < 2 * B) red[tid / B][tid % B] = kNoKey;
+  if (tid < 2 * B) {
+    red[tid / B][tid % B] = kNoKey;
+    ssum_s[tid / B][tid % B] = 0u;
+    smin_s[tid / B][tid % B] = 0xffffffffu;
+  }
   if (tid == 0) {
     err_s = 0;
     mbar_init(&full_bar[0], PT);
@@ -219,16 +227,25 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
       const int gj = (int)blockIdx.x + j * (int)gridDim.x;
       const int k = gj / (BH * gpr), rem = gj - k * (BH * gpr);
       const int by = rem / gpr, bx0 = (rem - by * gpr) * B;
-      if (pt < B) {
+      if (MODE != kPipeVolume && pt < B) {
         if (bx0 + pt < BW) {
           const Decoded d = decode_key(red[b][pt], p, lam);
           const size_t o = (size_t)k * nbf + (size_t)by * BW + bx0 + pt;
-          mv_out[2 * o] = (int16_t)d.mvx;
-          mv_out[2 * o + 1] = (int16_t)d.mvy;
-          J_out[o] = d.J;
-          if (sad_out) sad_out[o] = d.sad;
+          if (out.mv) {
+            out.mv[2 * o] = (int16_t)d.mvx;
+            out.mv[2 * o + 1] = (int16_t)d.mvy;
+          }
+          if (out.J) out.J[o] = d.J;
+          if (out.sad) out.sad[o] = d.sad;
+          if (MODE == kPipeStats) {
+            // every term of sum |SAD - SAD_min| is non-negative
+            out.smin[o] = smin_s[b][pt];
+            out.sdev[o] = ssum_s[b][pt] - (uint32_t)(n * n) * smin_s[b][pt];
+          }
         }
         red[b][pt] = kNoKey;
+        ssum_s[b][pt] = 0u;
+        smin_s[b][pt] = 0xffffffffu;
       }
       return true;
     };
@@ -241,7 +258,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
       const int by = rem / gpr, bx0 = (rem - by * gpr) * B;
       const int x0 = bx0 * N, y0 = by * M;
       const uint8_t* __restrict__ cur = fr.f[k + 1];
-      const uint8_t* __restrict__ ref = fr.f[k];
+      const uint8_t* __restrict__ ref = fr.f[out.ref_fixed ? 0 : k];
       uint32_t* cw = buf0 + b * bstride;
       for (int e = pt; e < B * M * NW; e += PT) {
         const int blk = e / (M * NW), rm = e % (M * NW), j = rm / NW, w = rm % NW;
@@ -326,9 +343,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
     // every lane acquires the producers' stores itself (the phase is complete)
     mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, lim);
     const int gi = (int)blockIdx.x + i * (int)gridDim.x;
-    const int rem = gi % (BH * gpr);
+    const int gk = gi / (BH * gpr), rem = gi - gk * (BH * gpr);
     const int bx0 = (rem % gpr) * B;
     const int nb = min(B, BW - bx0);
+    // MODE kPipeVolume: the group's first block in the volume
+    uint16_t* vg = MODE == kPipeVolume
+                       ? out.vol + ((size_t)gk * nbf + (size_t)(rem / gpr) * BW + bx0) * out.vstride
+                       : nullptr;
     const uint32_t* cwb = buf0 + b * bstride;
     const uint32_t* sh = cwb + B * M * NW;
     int f = 32 * q0 + lane;
@@ -344,7 +365,25 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(
         const int row0 = seg * T;
         uint32_t acc[T];
         fs_run_sads<N, M, T>(c, sh + row0 * SP + blk * N + col, SP, acc);
-        atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
+        if (MODE == kPipeVolume) {
+          uint16_t* vb = vg + (size_t)blk * out.vstride + col;
+#pragma unroll
+          for (int kk = 0; kk < T; kk++)
+            if (row0 + kk < n) vb[(row0 + kk) * n] = (uint16_t)acc[kk];
+        } else {
+          atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
+        }
+        if (MODE == kPipeStats) {
+          uint32_t sum = 0u, mn = 0xffffffffu;
+#pragma unroll
+          for (int kk = 0; kk < T; kk++)
+            if (row0 + kk < n) {
+              sum += acc[kk];
+              mn = min(mn, acc[kk]);
+            }
+          atomicAdd(&ssum_s[b][blk], sum);
+          atomicMin(&smin_s[b][blk], mn);
+        }
       }
       seg += dseg;
       col += dcol;
@@ -823,7 +862,19 @@ bool fsbm_pipe_applies(int N, int M, int p) {
 
 int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
                      int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  PipeOut o;
+  std::memset(&o, 0, sizeof(o));
+  o.mv = mv_out;
+  o.J = J_out;
+  o.sad = sad_out;
+  return launch_fsbm_pipe_mode(kPipeKeys, frames, K, W, H, p, lam, o, s);
+}
+
+int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, int H, int p,
+                          uint32_t lam, const PipeOut& out, cudaStream_t s) {
   if (K < 1 || K > kSeqMax) return ME_ERR_ARG;
+  if (mode == kPipeStats && (!out.smin || !out.sdev)) return ME_ERR_ARG;
+  if (mode == kPipeVolume && !out.vol) return ME_ERR_ARG;
   SeqFrames fr;
   std::memset(&fr, 0, sizeof(fr));
   for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
@@ -835,18 +886,19 @@ int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, u
   const int groups = K * BH * ((BW + kPipeBpc - 1) / kPipeBpc);
   const int pgrid = std::min(nsm, groups);
   const long long lim = wait_cycles(1000000000ll);
-#define X(t_)                                                                                 \
-  if (pl.T == t_) {                                                                           \
-    auto kern = k_fsbm_pipe<16, 16, t_>;                                                      \
+#define X(t_, m_)                                                                             \
+  if (pl.T == t_ && mode == m_) {                                                             \
+    auto kern = k_fsbm_pipe<16, 16, t_, m_>;                                                  \
     const size_t smem = pipe_smem_bytes<16, 16, t_>(p);                                       \
     const int st = ensure_dynamic_smem((const void*)kern, smem);                              \
     if (st) return st;                                                                        \
-    kern<<<pgrid, kPipeThreads, smem, s>>>(fr, W, H, p, lam, groups, lim, mv_out, J_out,      \
-                                           sad_out);                                          \
+    kern<<<pgrid, kPipeThreads, smem, s>>>(fr, W, H, p, lam, groups, lim, out);               \
     ME_CUDA(cudaGetLastError());                                                              \
     return ME_OK;                                                                             \
   }
-  X(8) X(11) X(13) X(16)
+#define Y(m_) X(8, m_) X(11, m_) X(13, m_) X(16, m_)
+  Y(kPipeKeys) Y(kPipeStats) Y(kPipeVolume)
+#undef Y
 #undef X
   return ME_ERR_ARG;
 }

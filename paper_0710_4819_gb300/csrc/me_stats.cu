@@ -11,7 +11,9 @@
 // candidate against N*M/4 packed SAD steps, so the kernel keeps the FSBM
 // kernel's SAD-rate roofline.
 //
-//   me_sad_deviation : one frame pair (K = 1, no vector error)
+//   me_sad_deviation : one frame pair (K = 1, no vector error); for 16x16
+//                      blocks the pipelined persistent search (statistics
+//                      mode) instead
 //   me_motion_study  : frames[1..K] each against frames[0] in one launch
 //                      (blockIdx.y = k), with Intra_SAD and the L1 error
 //                      against the known global vector of each frame
@@ -128,6 +130,17 @@ int me_sad_deviation(const uint8_t* cur, const uint8_t* ref, int W, int H, int N
   std::memset(&fr, 0, sizeof(fr));
   fr.f[0] = ref;
   fr.f[1] = cur;
+  if (fsbm_pipe_applies(N, M, p)) {
+    // 16x16: the pipelined persistent search in its statistics mode
+    PipeOut po;
+    std::memset(&po, 0, sizeof(po));
+    po.mv = mv_out;
+    po.J = J_out;
+    po.smin = sad_min_out;
+    po.sdev = sad_dev_out;
+    return launch_fsbm_pipe_mode(kPipeStats, fr.f, 1, W, H, p, lambda_q8, po,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  }
   const StatsOut o{nullptr, mv_out, J_out, nullptr, sad_min_out, sad_dev_out, nullptr};
   return launch_stats(fr, 1, W, H, N, M, p, lambda_q8, o, reinterpret_cast<cudaStream_t>(stream));
 }
