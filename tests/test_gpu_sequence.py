@@ -62,6 +62,25 @@ def test_fsbm_sequence_pipelined_matches_oracle(me, orc, w, h, p, K, monkeypatch
         assert np.array_equal(_u32(r.sad[k]), sad), k
 
 
+def test_fsbm_sequence_pipelined_64_pairs(me, orc, monkeypatch):
+    """The largest sequence a call takes (64 pairs, QCIF, p = 16): every pair
+    equal to the per-group kernel's, and the first and last to the oracle."""
+    import torch
+    seq = synth.config_sequence("qcif", seed=77, n_frames=65)
+    lam = orc.lambda_q8(28)
+    frames = torch.from_numpy(seq).cuda()
+    r = me.me_fsbm_sequence(frames, 16, 16, 16, lam)
+    assert me.me_fsbm_sequence_status() == 0
+    monkeypatch.setenv("ME_FSBM_PIPE", "0")
+    r0 = me.me_fsbm_sequence(frames, 16, 16, 16, lam)
+    torch.cuda.synchronize()
+    assert torch.equal(r.mv, r0.mv) and torch.equal(r.J, r0.J) and torch.equal(r.sad, r0.sad)
+    for k in (0, 63):
+        mv, J, sad = orc.fsbm(seq[k + 1], seq[k], 16, 16, 16, lam, nthreads=8)
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), k
+        assert np.array_equal(_u32(r.J[k]), J), k
+
+
 def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me):
     """1080p p = 32, 12 pairs (the bench's kernel): equal to me_fsbm per pair."""
     import torch
