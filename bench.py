@@ -643,19 +643,53 @@ def main():
     achieved = ABSDIFF_PER_FRAME / (seq_fsbm_ms * 1e-3)
 
     # end-to-end through the C ABI with host buffers: host frames copied in,
-    # the step's calls, results copied out, all inside the timed region
+    # the step's calls, results copied out, all inside the timed region.  The
+    # frames go up in four chunks on a copy stream and the full search of each
+    # chunk's pairs starts as soon as its frames are in (pairs are
+    # independent); ACBM, whose pairs chain, starts when all frames are in,
+    # and the full-search results go down while it runs.
     host_frames = torch.from_numpy(frames_np).pin_memory()
     h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in a_out + f_out]
     d_frames = torch.empty_like(frames)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d_frames.copy_(host_frames, non_blocking=True)
-    me.me_fsbm_sequence(d_frames, N, M, P, lam, out=f_out)
-    me.me_acbm_sequence(d_frames, N, M, P, lam, prm, out=a_out)
-    for h, d in zip(h_out, a_out + f_out):
-        h.copy_(d, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    copy_stream = torch.cuda.Stream()
+    n_chunks = 4
+    cuts = [round(c * pairs / n_chunks) for c in range(n_chunks + 1)]
+
+    def e2e_once():
+        arrived = []
+        with torch.cuda.stream(copy_stream):
+            for c in range(n_chunks):
+                f0 = 0 if c == 0 else cuts[c] + 1       # pairs cuts[c]..cuts[c+1]-1 need
+                f1 = cuts[c + 1] + 1                    # frames cuts[c]..cuts[c+1]
+                d_frames[f0:f1].copy_(host_frames[f0:f1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+                arrived.append(ev)
+        for c in range(n_chunks):
+            stream.wait_event(arrived[c])
+            lo, hi = cuts[c], cuts[c + 1]
+            me.me_fsbm_sequence(d_frames[lo:hi + 1], N, M, P, lam,
+                                out=(f_mv[lo:hi], f_J[lo:hi], f_sad[lo:hi]))
+        fs_done = torch.cuda.Event()
+        fs_done.record(stream)
+        me.me_acbm_sequence(d_frames, N, M, P, lam, prm, out=a_out)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(fs_done)
+            for h, d in zip(h_out[len(a_out):], f_out):
+                h.copy_(d, non_blocking=True)
+        for h, d in zip(h_out[:len(a_out)], a_out):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_once()                                      # warm-up (the chunk shapes' plans)
+    e2e_times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_once()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(pg, statistics.median(e2e_times))
+    same_e2e = all(torch.equal(h, d.cpu()) for h, d in zip(h_out, a_out + f_out))
     h2d = host_frames.numel()
     d2h = sum(x.numel() * x.element_size() for x in h_out)
     e2e_fps = pairs * world / e2e_s
@@ -735,7 +769,9 @@ def main():
                      "peak_source": "152 SMs x 64 packed-SAD lanes/clk x 4 bytes x 2070 MHz "
                                     "(lane rate measured by me_sad_peak)"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "outputs_identical": same_e2e,
+                "form": "frames up in 4 chunks on a copy stream, each chunk's full search "
+                        "as soon as it is in; median of 3"},
         "gpu_launches": 4 * args.steps,   # k_fsbm_pipe; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
