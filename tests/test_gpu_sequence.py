@@ -81,10 +81,14 @@ def test_fsbm_sequence_pipelined_64_pairs(me, orc, monkeypatch):
         assert np.array_equal(_u32(r.J[k]), J), k
 
 
-def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me):
-    """1080p p = 32, 12 pairs (the bench's kernel): equal to me_fsbm per pair."""
+def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me, orc, monkeypatch):
+    """1080p p = 32, 12 pairs in one launch (the bench's kernel): equal to
+    me_fsbm per pair, to the per-group kernel over the same sequence, and to
+    the oracle on sampled blocks (corners, edges, random) of the first and
+    last pair."""
     import torch
-    seq = torch.from_numpy(synth.config_sequence("1080p", seed=7, n_frames=13)).cuda()
+    seq_np = synth.config_sequence("1080p", seed=7, n_frames=13)
+    seq = torch.from_numpy(seq_np).cuda()
     lam = me.me_lambda_q8(28)
     r = me.me_fsbm_sequence(seq, 16, 16, 32, lam)
     assert me.me_fsbm_sequence_status() == 0
@@ -92,6 +96,19 @@ def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me):
         f = me.me_fsbm(seq[k + 1], seq[k], 16, 16, 32, lam)
         torch.cuda.synchronize()
         assert torch.equal(r.mv[k], f.mv) and torch.equal(r.J[k], f.J) and torch.equal(r.sad[k], f.sad), k
+    monkeypatch.setenv("ME_FSBM_PIPE", "0")
+    r0 = me.me_fsbm_sequence(seq, 16, 16, 32, lam)
+    torch.cuda.synchronize()
+    assert torch.equal(r.mv, r0.mv) and torch.equal(r.J, r0.J) and torch.equal(r.sad, r0.sad)
+    BW, BH = 120, 68
+    rng = np.random.default_rng(3)
+    blocks = np.unique(np.concatenate([[0, BW - 1, (BH - 1) * BW, BH * BW - 1, 7 * BW + 8, 8 * BW - 1],
+                                       rng.integers(0, BW * BH, 30)])).astype(np.int32)
+    for k in (0, 11):
+        mv, J, sad = orc.fsbm_blocks(seq_np[k + 1], seq_np[k], 16, 16, 32, lam, blocks, nthreads=8)
+        assert np.array_equal(r.mv[k].cpu().numpy().reshape(-1, 2)[blocks], mv), k
+        assert np.array_equal(_u32(r.J[k]).ravel()[blocks], J), k
+        assert np.array_equal(_u32(r.sad[k]).ravel()[blocks], sad), k
 
 
 @pytest.mark.parametrize("name,n,p,qp", [("qcif", 10, 16, 28), ("cif", 5, 16, 40),
