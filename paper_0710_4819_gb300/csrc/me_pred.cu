@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -103,11 +104,13 @@ __device__ __forceinline__ int med3(int a, int b, int c) {
 // has 256*SAD + 2*lambda <= UBmin.  The list is built before the wait; when
 // it is short, one warp evaluates it as soon as the predictor is known.
 constexpr int kPredList = 512;
+constexpr int kPredPruneMaxK = 8;   // pairs per call up to which the list is built
 
 __global__ void __launch_bounds__(kPredThreads) k_pred_wave(
     const int* __restrict__ items, int total, int BW, int nbf, int p, uint32_t lam,
     const uint16_t* __restrict__ vol, int vstride, unsigned long long* flags, PredCtrl* ctrl,
-    int16_t* __restrict__ mv_out, uint32_t* __restrict__ J_out, uint32_t* __restrict__ sad_out) {
+    int16_t* __restrict__ mv_out, uint32_t* __restrict__ J_out, uint32_t* __restrict__ sad_out,
+    int prune) {
   extern __shared__ __align__(16) uint16_t vs[];   // [vstride] SADs, then [vstride] list
   uint16_t* list = vs + vstride;
   __shared__ unsigned long long red[kPredThreads / 32];
@@ -143,15 +146,17 @@ __global__ void __launch_bounds__(kPredThreads) k_pred_wave(
       asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
-    // 2. UBmin, then the list of candidates that can still win (before the wait)
-    uint32_t rx[kCols], ax[kCols];
+    // 2. UBmin, then the list of candidates that can still win (before the
+    // wait; only when pruning: it shortens the wait-to-publish step of the
+    // dependency chain, which bounds one pair, at the price of two more
+    // passes over the volume, which bound many pairs)
+    uint32_t ax[kCols];
 #pragma unroll
-    for (int j = 0; j < kCols; j++) {
-      const int mvx = lane + 32 * j - p;
-      ax[j] = (uint32_t)abs(mvx);
-      rx[j] = lam * (uint32_t)mv_bits((int)ax[j] + p);
-    }
-    {
+    for (int j = 0; j < kCols; j++) ax[j] = (uint32_t)abs(lane + 32 * j - p);
+    if (prune) {
+      uint32_t rx[kCols];
+#pragma unroll
+      for (int j = 0; j < kCols; j++) rx[j] = lam * (uint32_t)mv_bits((int)ax[j] + p);
       uint32_t ub = 0xffffffffu;
       for (int r = warp; r < n; r += kPredThreads / 32) {
         const uint32_t ry = lam * (uint32_t)mv_bits(abs(r - p) + p);
@@ -165,9 +170,7 @@ __global__ void __launch_bounds__(kPredThreads) k_pred_wave(
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ub = min(ub, __shfl_xor_sync(FULL, ub, o));
       if (lane == 0) ured[warp] = ub;
-    }
-    __syncthreads();
-    {
+      __syncthreads();
       uint32_t ubmin = ured[0];
 #pragma unroll
       for (int i = 1; i < kPredThreads / 32; i++) ubmin = min(ubmin, ured[i]);
@@ -187,9 +190,9 @@ __global__ void __launch_bounds__(kPredThreads) k_pred_wave(
           }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const int cnt = s_cnt;
+    const int cnt = prune ? s_cnt : kPredList + 1;   // without the list: the whole CTA
     // 3. the three predecessors (warp 0; bounded), then the predictor
     if (warp == 0) {
       // lane 0: left, lane 1: upper, lane 2: upper-right (when inside the grid)
@@ -450,9 +453,13 @@ static int run_pred(const PredFrames& fr, int K, int W, int H, int N, int M, int
   st = launch_volume(fr, K, W, H, N, M, p, pl->vstride, pl->vol, s);
   if (st) return st;
   const int BW = W / N, nbf = BW * (H / M);
+  // prune (the pre-wait candidate list) for short runs, whose time is the
+  // dependency chain; long runs are bound by the work per block
+  int prune = K <= kPredPruneMaxK ? 1 : 0;
+  if (const char* e = std::getenv("ME_PRED_PRUNE")) prune = e[0] == '1' ? 1 : 0;
   k_pred_wave<<<pl->grid, kPredThreads, pl->smem, s>>>(pl->items, pl->total, BW, nbf, p, lam,
                                                        pl->vol, pl->vstride, pl->flags, pl->ctrl,
-                                                       mv, J, sad);
+                                                       mv, J, sad, prune);
   ME_CUDA(cudaGetLastError());
   ME_CUDA(cudaEventRecord(pl->last, s));
   pl->ran = true;
