@@ -118,3 +118,35 @@ def test_pred_flat_and_textured_regions(me, orc, lam):
     flat0 = (128 + rng.integers(-1, 2, (144, 176))).astype(np.uint8)
     flat1 = (128 + rng.integers(-1, 2, (144, 176))).astype(np.uint8)
     _check(me, orc, flat1, flat0, 16, 16, 6, lam, ("flat", lam))
+
+
+def test_pred_long_sequence_without_the_list(me, orc):
+    """More than 8 pairs per call: every candidate is evaluated after the
+    wait (no pre-wait list); each pair equals the oracle."""
+    import torch
+    seq = synth.config_sequence("cif", seed=620, n_frames=11)
+    lam = orc.lambda_q8(30)
+    r = me.me_fsbm_pred_sequence(torch.from_numpy(seq).cuda(), 16, 16, 16, lam)
+    assert me.me_fsbm_pred_status(352, 288, 16, 16, 16, 10) == 0
+    for k in range(10):
+        mv, J, sad = orc.fsbm_pred(seq[k + 1], seq[k], 16, 16, 16, lam)
+        assert np.array_equal(r.mv[k].cpu().numpy(), mv), k
+        assert np.array_equal(_u32(r.J[k]), J), k
+        assert np.array_equal(_u32(r.sad[k]), sad), k
+
+
+def test_pred_list_and_full_evaluation_agree(me, monkeypatch):
+    """The two evaluation forms (pre-wait list / every candidate) give the
+    same bytes for short and long calls."""
+    import torch
+    seq = torch.from_numpy(synth.config_sequence("cif", seed=621, n_frames=12)).cuda()
+    lam = me.me_lambda_q8(26)
+    for frames in (seq[:2], seq[:4], seq):
+        outs = []
+        for v in ("1", "0"):
+            monkeypatch.setenv("ME_PRED_PRUNE", v)
+            r = me.me_fsbm_pred_sequence(frames, 16, 16, 24, lam)
+            torch.cuda.synchronize()
+            outs.append(r)
+        assert torch.equal(outs[0].mv, outs[1].mv) and torch.equal(outs[0].J, outs[1].J)
+        assert torch.equal(outs[0].sad, outs[1].sad)
