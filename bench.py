@@ -39,8 +39,8 @@ NBLK = BW * BH
 NCAND = (2 * P + 1) ** 2
 ABSDIFF_PER_FRAME = NBLK * NCAND * N * M          # 8.83e9 for FSBM
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fsbm_pipe<16,16,13>
-# on 13 frames (12 pairs): 27.201792 MB + 0 B, i.e. per frame of the sequence
-FSBM_SEQ_DRAM_BYTES_PER_FRAME = 27.201792e6 / 13
+# on 13 frames (12 pairs): 27.202560 MB + 0 B, i.e. per frame of the sequence
+FSBM_SEQ_DRAM_BYTES_PER_FRAME = 27.202560e6 / 13
 WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
 
 
