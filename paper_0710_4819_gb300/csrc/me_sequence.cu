@@ -31,6 +31,12 @@ namespace me {
 constexpr int kSeqMax = 64;     // frame pairs per call
 constexpr int kSeqThreads = 256;
 constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
+// Every kSeqSearchEvery-th SM (by %smid) hosts two search CTAs instead of one
+// PBM and one search CTA.  Measured at 1080p p=32 (59 pairs): one of each on
+// every SM 0.1196 ms of ACBM per pair; two search CTAs on every 8th / 4th /
+// 3rd / 2nd SM 0.1159 / 0.1119 / 0.1097 / 0.1113 ms; without occlusions
+// (1.5 % of blocks searched) 0.0841 / - / 0.0834 / 0.0844 / 0.0911 ms.
+constexpr int kSeqSearchEvery = 3;
 constexpr int kSeqSP = 193;     // compile-time shifted-word pitch of the main FSBM build (odd:
                                 // rows of different runs start on different banks)
 
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
   const long long timeout = ctrl->timeout_ns;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
   const int n = 2 * p + 1;
-  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr);
+  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr, kSeqSearchEvery);
   __syncthreads();
 
   if (s_role == 0) {
