@@ -126,7 +126,8 @@ def contrast_texture(rng: np.random.Generator, w: int, h: int) -> np.ndarray:
     texture's deviation from 128 times c(x, y)^2, where c is U[0,1] noise
     blurred with sigma 12, replaced by its rank in the frame divided by the
     pixel count (uniform on [0, 1)), then mapped by max(0, (c - 0.3) / 0.7),
-    so that 30 % of the frame is flat whatever the seed."""
+    so that 30 % of the frame has zero contrast (flat at 128) whatever the
+    seed, and the low-contrast margin around it rounds to nearly flat."""
     t = texture(rng, w, h).astype(np.float64)
     c = rng.random((h, w))
     c = _blur_1d(_blur_1d(c, 1, 12.0, 36), 0, 12.0, 36)
