@@ -99,18 +99,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm_seq(SeqFrames fr, int W, i
 // ------------------------------------------------------------------ FSBM, pipelined
 //
 // The same full search as k_fsbm_seq as one persistent CTA per SM that
-// overlaps staging with searching.  Two producer warps stage the windows of
+// overlaps staging with searching.  Four producer warps stage the windows of
 // the CTA's groups (kPipeBpc adjacent blocks of one block row of one pair;
 // groups blockIdx.x, blockIdx.x + gridDim.x, ...) into two shared-memory
-// buffers in turn; fourteen consumer warps run the searches.  A group's runs
-// (block-major, then segment, then column) are dealt in rounds of 32, one
-// per lane, each consumer warp taking a fixed contiguous range of rounds, and
-// a warp moves on to the next group as soon as its own rounds are done --
-// the uneven shares of a group (2600 runs over 14 warps at p = 32) no longer
-// leave lanes or warps idle until the slowest finishes, and staging is off
-// the search's path.  The last consumer warp to finish a group writes its
-// results and frees the buffer.  Every wait is bounded (SM cycle count); a
-// wait that gives up records ME_ERR_TIMEOUT for me_fsbm_sequence_status.
+// buffers in turn; twelve consumer warps (three per scheduler) run the
+// searches.  A group's runs (block-major, then segment, then column) are
+// dealt in rounds of 32, one per lane, each consumer warp taking a fixed
+// contiguous range of rounds, and a warp moves on to the next group as soon
+// as its own rounds are done -- the uneven shares of a group (2600 runs over
+// 12 warps at p = 32) no longer leave lanes or warps idle until the slowest
+// finishes, and staging is off the search's path.  When every consumer
+// thread has arrived on a buffer's empty barrier, the producers write that
+// group's results (per-block minima kept in shared memory) and restage the
+// buffer.  Every wait is bounded (SM cycle count); a wait that gives up
+// records ME_ERR_TIMEOUT for me_fsbm_sequence_status.  The producer count is
+// a build-time setting (ME_PIPE_PRODUCERS) for sweeps.
 constexpr int kPipeThreads = 512;
 #ifndef ME_PIPE_PRODUCERS
 #define ME_PIPE_PRODUCERS 4
