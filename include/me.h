@@ -139,7 +139,10 @@ int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
 /* FSBM over K consecutive frame pairs in one launch (1 <= K <= 64).
  * frames is a HOST array of K+1 device frame pointers: pair k has reference
  * frames[k] and current frame frames[k+1].  Outputs are [K][BH][BW] (x2 for
- * mv), pair k at offset k*BW*BH.  No scratch memory. */
+ * mv), pair k at offset k*BW*BH.  No scratch memory.  For 16x16 blocks (and
+ * p <= 34) the launch is one persistent CTA per SM in which staging warps
+ * fill two shared-memory buffers while searching warps work on the other
+ * (me_fsbm uses the same kernel for one pair). */
 int me_fsbm_sequence(const uint8_t *const *frames, int K, int W, int H, int N, int M, int p,
                      uint32_t lambda_q8, int16_t *mv_out, uint32_t *J_out, uint32_t *sad_out,
                      me_stream_t stream);

@@ -1,7 +1,9 @@
 // me_frame.cu -- the per-frame C ABI: padding, Intra_SAD, FSBM and ACBM for
 // one frame pair, with their kernels.
 //
-//   me_fsbm : k_fsbm (one launch; full search of every block, Sec. 2.3)
+//   me_fsbm : one launch; full search of every block (Sec. 2.3): for 16x16
+//             blocks the pipelined persistent search of me_sequence.cu
+//             (k_fsbm_pipe), else k_fsbm
 //   me_acbm : k_pad_ref, k_intra_sad, then for each anti-diagonal wave
 //             w = x + 2y of the block grid: k_pbm_wave (PBM + the Sec. 3.2 test,
 //             compaction of the failing blocks) and k_fs_list (full search of
