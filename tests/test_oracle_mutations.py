@@ -96,6 +96,18 @@ MUTANTS = {
         "    if (by == 0) {\n        *pmx = m1x;", "    if (by < 0) {\n        *pmx = m1x;"),
     "right edge keeps a stale upper-right vector": (
         "    if (bx + 1 < BW) {\n        m3x", "    if (bx < BW) {\n        m3x"),
+    "block-list search takes the block index transposed": (
+        "lambda_q8, blocks[k] % BW, blocks[k] / BW,", "lambda_q8, blocks[k] / BH, blocks[k] % BH,"),
+    "block-list search scales the index by the grid height": (
+        "lambda_q8, blocks[k] % BW, blocks[k] / BW,", "lambda_q8, blocks[k] % BH, blocks[k] / BH,"),
+    "block-list search writes outputs by block index": (
+        "        J_out[k] = J;\n        if (sad_out) sad_out[k] = s;\n    }\n    return OR_OK;\n}\n\ntypedef",
+        "        J_out[blocks[k]] = J;\n        if (sad_out) sad_out[k] = s;\n    }\n    return OR_OK;\n}\n\ntypedef"),
+    "block-list ACBM takes the block index transposed": (
+        "prm, b % BW, b / BW,", "prm, b / BH, b % BH,"),
+    "block-list ACBM reads Intra_SAD by list position": (
+        "prm, b % BW, b / BW,\n                   intra[b], seen,",
+        "prm, b % BW, b / BW,\n                   intra[k], seen,"),
     "predicted rate coded against zero": (
         "(uint32_t)(oracle_mv_bits(mvx - pmx) +", "(uint32_t)(oracle_mv_bits(mvx) +"),
 }
@@ -138,6 +150,9 @@ def _pin_suite(v):
     yield lambda: pins.test_fsbm_pred_follows_a_global_shift(v)
     yield lambda: pins.test_sad_deviation_closed_forms(v)
     yield lambda: pins.test_sad_deviation_of_a_known_global_shift(v, 3, -2)
+    for args in [(48, 32, 16, 16, 3), (24, 48, 4, 16, 3)]:
+        yield lambda args=args: pins.test_fsbm_blocks_match_brute_force(v, *args)
+    yield lambda: pins.test_acbm_blocks_agree_with_the_frame_call(v, 8, 16, 3)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

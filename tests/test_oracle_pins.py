@@ -743,3 +743,54 @@ def test_fsbm_pred_blocks_agree_with_the_frame_call(orc):
     bmv, bJ, bs = orc.fsbm_pred_blocks(cur, ref, 8, 8, 3, 6595, mv, blocks)
     assert np.array_equal(bmv, mv.reshape(-1, 2)) and np.array_equal(bJ, J.ravel())
     assert np.array_equal(bs, sad.ravel())
+
+
+# ----------------------------------------------------------------- block-list entries
+@pytest.mark.parametrize("W,H,N,M,p", [(48, 32, 16, 16, 3), (40, 24, 8, 4, 2), (24, 48, 4, 16, 3)])
+def test_fsbm_blocks_match_brute_force(orc, W, H, N, M, p):
+    """The block-list full search (the oracle of the large-frame sampled
+    checks) against the numpy brute force of Sec. 2.3, on grids with BW != BH
+    so that a transposed or mis-scaled block index shows: every block once in
+    a shuffled order, plus repeats; outputs follow the list's order."""
+    rng = np.random.default_rng(W * H + N * M + p)
+    ref = synth.texture(rng, W, H)
+    cur = np.clip(np.roll(ref, (1, -2), (0, 1)).astype(int) + rng.integers(-9, 10, ref.shape),
+                  0, 255).astype(np.uint8)
+    BW, BH = W // N, H // M
+    assert BW != BH
+    lam = 6595
+    wmv, wJ, wS = brute_fsbm(cur, ref, N, M, p, lam)
+    blocks = np.concatenate([rng.permutation(BW * BH), rng.integers(0, BW * BH, 5)]).astype(np.int32)
+    mv, J, sad = orc.fsbm_blocks(cur, ref, N, M, p, lam, blocks, nthreads=2)
+    assert np.array_equal(mv, wmv.reshape(-1, 2)[blocks])
+    assert np.array_equal(J, wJ.ravel()[blocks])
+    assert np.array_equal(sad, wS.ravel()[blocks])
+    fmv, fJ, fS = orc.fsbm(cur, ref, N, M, p, lam)
+    assert np.array_equal(mv, fmv.reshape(-1, 2)[blocks]) and np.array_equal(J, fJ.ravel()[blocks])
+    with pytest.raises(Exception):
+        orc.fsbm_blocks(cur, ref, N, M, p, lam, np.array([BW * BH], np.int32))
+
+
+@pytest.mark.parametrize("N,M,p", [(16, 16, 4), (8, 16, 3), (16, 8, 5)])
+def test_acbm_blocks_agree_with_the_frame_call(orc, N, M, p):
+    """Given the frame call's own final field as the current-frame field (and
+    the same previous field), the block-list ACBM reproduces every block of
+    the frame call (Sec. 3.2: each block's result depends only on its
+    predictors' final vectors): vector, J, mask, SAD and load, with the blocks
+    listed in a shuffled order on a grid with BW != BH."""
+    seq = _acbm_inputs(5 * N + M + p, 112, 64)
+    lam = orc.lambda_q8(28)
+    prm = orc.params(alpha=300, beta=1)          # a mix of passing and full-searched blocks
+    prev = orc.acbm(seq[1], seq[0], N, M, p, lam, prm)[0]
+    mv, J, mask, sad, load = orc.acbm(seq[2], seq[1], N, M, p, lam, prm, prev)
+    BH, BW = J.shape
+    assert BW != BH and mask.any() and not mask.all()
+    rng = np.random.default_rng(N * M * p)
+    blocks = rng.permutation(BW * BH).astype(np.int32)
+    bmv, bJ, bmask, bsad, bload = orc.acbm_blocks(seq[2], seq[1], N, M, p, lam, prm, mv, blocks,
+                                                  prev_mv=prev)
+    assert np.array_equal(bmv, mv.reshape(-1, 2)[blocks])
+    assert np.array_equal(bJ, J.ravel()[blocks])
+    assert np.array_equal(bmask, mask.ravel()[blocks])
+    assert np.array_equal(bsad, sad.ravel()[blocks])
+    assert np.array_equal(bload, load.ravel()[blocks])
