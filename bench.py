@@ -42,6 +42,9 @@ ABSDIFF_PER_FRAME = NBLK * NCAND * N * M          # 8.83e9 for FSBM
 # on 13 frames (12 pairs): 27.202560 MB + 0 B, i.e. per frame of the sequence
 FSBM_SEQ_DRAM_BYTES_PER_FRAME = 27.202560e6 / 13
 WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
+# one metric string for both arms (the native step and the oracle's), so the
+# two lines can be divided; candidate-SADs/s, the roofline and p99 are keys
+METRIC = "1080p frames/s & candidate-SADs/s (FSBM, ACBM) vs int-pipe roofline; p99 ms"
 
 
 def parse():
@@ -52,11 +55,15 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=SEQ_FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the batch64 and serve legs of the default line")
     ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve", "loadtable"],
                     help="1080p: the default line; batch64 / serve: the multi-stream forms; "
                          "loadtable: ACBM load per block vs Qp on QCIF scenes (Table 1 layout)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
     ap.add_argument("--seconds", type=float, default=10.0, help="serve: arrival window")
+    ap.add_argument("--rate-sweep", action="store_true",
+                    help="serve: every rate of 2000..12000 req/s in turn (--seconds each)")
     return ap.parse_args()
 
 
@@ -173,6 +180,25 @@ def oracle_sample(frames, n_pairs: int, threads: int):
     return (time.perf_counter() - t0) / n_pairs
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -192,15 +218,16 @@ def _item(me, cur, ref, prev, out, lam, prm):
     return it
 
 
-def run_batch64(args):
+def batch64_measure(n_steps: int, gpu_index: int = 0):
     """The 64-stream mix (24 QCIF p16, 24 CIF p16, 12 720p p32, 4 2160p p64):
     one persistent launch per step (captured graph) against the plain per-frame
-    ACBM/FSBM calls on the same frames; outputs compared."""
+    ACBM/FSBM calls on the same frames; outputs compared.  Returns the
+    per-mode timings, the mix's FSBM absdiff rate and the clock record."""
     import torch
     import synth
     import paper_0710_4819_gb300 as me
     specs = synth.batch_mix()
-    n_frames = 1 + max(2, args.steps)
+    n_frames = 1 + max(2, n_steps)
     seqs = [torch.from_numpy(synth.stream_frames(s, n_frames)).cuda() for s in specs]
     lam = me.me_lambda_q8(QP)
     prm = me.params(qp=QP)
@@ -215,6 +242,8 @@ def run_batch64(args):
 
     res = {}
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
     for mode, name in ((0, "fsbm"), (1, "acbm")):
         b = me.Batch()
         for s in specs:
@@ -259,13 +288,24 @@ def run_batch64(args):
                      "batched_frames_per_s": len(specs) / (timings["batched"] * 1e-3),
                      "plain_frames_per_s": len(specs) / (timings["plain"] * 1e-3),
                      "speedup": timings["plain"] / timings["batched"], "outputs_identical": same}
+    res["clocks"] = clocks.stop()
     absd = sum((s.w // N) * (s.height // M) * (2 * s.p + 1) ** 2 * N * M for s in specs)
+    res["fsbm_absdiff_per_s_T"] = absd / (res["fsbm"]["batched_ms_per_step"] * 1e-3) / 1e12
+    res["steps"] = n_frames - 1
+    return res
+
+
+BATCH64_WORKLOAD = "batch64: 24 QCIF p16, 24 CIF p16, 12 720p p32, 4 2160p p64, 16x16, Qp 28"
+
+
+def run_batch64(args):
+    res = batch64_measure(args.steps)
     line = {"metric": "64-stream mix frames/s (one persistent launch per step vs plain per-frame calls)",
             "value": res["acbm"]["batched_frames_per_s"], "unit": "frames/s", "n_gpus": 1,
-            "steps": n_frames - 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "batch64: 24 QCIF p16, 24 CIF p16, 12 720p p32, 4 2160p p64, 16x16, Qp 28"},
+            "steps": res["steps"], "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": BATCH64_WORKLOAD},
             "fsbm": res["fsbm"], "acbm": res["acbm"],
-            "fsbm_absdiff_per_s_T": absd / (res["fsbm"]["batched_ms_per_step"] * 1e-3) / 1e12}
+            "fsbm_absdiff_per_s_T": res["fsbm_absdiff_per_s_T"], "clocks": res["clocks"]}
     print(json.dumps(line))
 
 
@@ -352,62 +392,102 @@ def run_load_table(args):
     print(json.dumps(line))
 
 
+class ServeRig:
+    """The serving mix: 200 streams (CIF p16 : 720p p32 : 1080p p32 =
+    50 : 35 : 15) opened on one continuous-batching server, each primed with
+    its first frame; a few distinct looping sequences per resolution are
+    shared round-robin."""
+
+    def __init__(self, n_streams: int = 200):
+        import numpy as np
+        import synth
+        import paper_0710_4819_gb300 as me
+        specs = synth.serving_mix(n_streams)
+        pool = {}
+        for kind in ("cif", "720p", "1080p"):
+            ex = [s for s in specs if s.name == kind][:4]
+            pool[kind] = [synth.stream_frames(s, 6)[:, :s.height] for s in ex]
+        self.specs = specs
+        self.srv = me.Server(40 << 30, max_inflight=2, mode=1)
+        self.ids = [self.srv.open_stream(s.w, s.height, s.p, qp=QP) for s in specs]
+        self.seq_of = [pool[s.name][i % len(pool[s.name])] for i, s in enumerate(specs)]
+        self.frame_no = [0] * len(specs)
+        self.rng = np.random.default_rng(11)
+        prime = [self.srv.submit(self.ids[i], self.seq_of[i][0]) for i in range(len(specs))]
+        for i, r in enumerate(prime):
+            self.srv.wait(r, self.ids[i], 60000)
+            self.frame_no[i] = 1
+
+    def run(self, rate: float, seconds: float, gpu_index: int = 0) -> dict:
+        """Poisson arrivals at `rate` requests/s for `seconds`, every result
+        waited for.  Latency = submit to results ready, per request.  The
+        server is saturated when it completes fewer frames per second than
+        are offered (its queue grows for the whole window)."""
+        n_req = max(1, int(rate * seconds))
+        gaps = self.rng.exponential(1.0 / rate, size=n_req)
+        which = self.rng.integers(0, len(self.specs), size=n_req)
+        reqs = []
+        clocks = ClockSampler(gpu_index)
+        clocks.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n_req):
+            t_next += gaps[k]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                if t_next - now > 0.0005:
+                    time.sleep(t_next - now - 0.0003)
+            i = int(which[k])
+            f = self.seq_of[i][self.frame_no[i] % self.seq_of[i].shape[0]]
+            self.frame_no[i] += 1
+            reqs.append((i, self.srv.submit(self.ids[i], f)))
+        t_sub = time.perf_counter() - t0
+        lat = []
+        for i, r in reqs:
+            has, ms, _ = self.srv.wait(r, self.ids[i], 120000)
+            lat.append(ms)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        lat.sort()
+        done = len(reqs) / wall
+        return {"offered_rate": rate, "requests": len(reqs), "seconds": seconds,
+                "submitted_per_s": len(reqs) / t_sub, "frames_per_s": done,
+                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "max_ms": lat[-1], "saturated": done < 0.95 * rate, "clocks": clk}
+
+    def close(self):
+        self.srv.close()
+
+
+SERVE_WORKLOAD = "serve: 200 streams CIF p16 50% / 720p p32 35% / 1080p p32 15%, Poisson arrivals, budget 40 GB"
+SERVE_SWEEP = (2000, 4000, 6000, 8000, 10000, 12000)
+
+
 def run_serve(args):
-    """Continuous-batching server over 200 streams (CIF p16 : 720p p32 :
-    1080p p32 = 50 : 35 : 15), Poisson arrivals at --rate for --seconds."""
-    import numpy as np
-    import torch
-    import synth
-    import paper_0710_4819_gb300 as me
-    specs = synth.serving_mix(200)
-    # a few distinct looping sequences per resolution, shared round-robin
-    pool = {}
-    for kind in ("cif", "720p", "1080p"):
-        ex = [s for s in specs if s.name == kind][:4]
-        pool[kind] = [synth.stream_frames(s, 6)[:, :s.height] for s in ex]
-    srv = me.Server(40 << 30, max_inflight=2, mode=1)
-    ids = [srv.open_stream(s.w, s.height, s.p, qp=QP) for s in specs]
-    seq_of = [pool[s.name][i % len(pool[s.name])] for i, s in enumerate(specs)]
-    frame_no = [0] * len(specs)
-    rng = np.random.default_rng(11)
-    # prime every stream with its first frame (no result), then the timed run
-    prime = [srv.submit(ids[i], seq_of[i][0]) for i in range(len(specs))]
-    for i, r in enumerate(prime):
-        srv.wait(r, ids[i], 60000)
-        frame_no[i] = 1
-    n_req = int(args.rate * args.seconds)
-    gaps = rng.exponential(1.0 / args.rate, size=n_req)
-    which = rng.integers(0, len(specs), size=n_req)
-    reqs = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for k in range(n_req):
-        t_next += gaps[k]
-        while True:
-            now = time.perf_counter()
-            if now >= t_next:
-                break
-            if t_next - now > 0.0005:
-                time.sleep(t_next - now - 0.0003)
-        i = int(which[k])
-        f = seq_of[i][frame_no[i] % seq_of[i].shape[0]]
-        frame_no[i] += 1
-        reqs.append((i, srv.submit(ids[i], f)))
-    lat = []
-    for i, r in reqs:
-        has, ms, _ = srv.wait(r, ids[i], 120000)
-        lat.append(ms)
-    wall = time.perf_counter() - t0
-    srv.close()
-    lat.sort()
-    line = {"metric": "serving: frames/s and latency (continuous batching, 200 streams)",
-            "value": len(reqs) / wall, "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "serve: 200 streams CIF p16 50% / 720p p32 35% / 1080p p32 15%, "
-                                   f"Poisson {args.rate:.0f} req/s for {args.seconds:.1f} s, budget 40 GB"},
-            "offered_rate": args.rate, "requests": len(reqs),
-            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "max_ms": lat[-1]}
+    """Continuous-batching server over the 200-stream mix: Poisson arrivals
+    at --rate for --seconds, or (--rate-sweep) at each rate of the configured
+    range 2000..12000 req/s in turn, reporting the curve and the highest rate
+    the server keeps up with."""
+    rig = ServeRig()
+    if args.rate_sweep:
+        curve = [rig.run(r, args.seconds) for r in SERVE_SWEEP]
+        rig.close()
+        kept = [c["offered_rate"] for c in curve if not c["saturated"]]
+        line = {"metric": "serving: frames/s and latency vs offered rate (continuous batching, 200 streams)",
+                "value": max(c["frames_per_s"] for c in curve), "unit": "frames/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+                "config": {"workload": SERVE_WORKLOAD + f", {args.seconds:.1f} s per rate"},
+                "highest_rate_kept_up": max(kept) if kept else None, "curve": curve}
+    else:
+        r = rig.run(args.rate, args.seconds)
+        rig.close()
+        line = {"metric": "serving: frames/s and latency (continuous batching, 200 streams)",
+                "value": r["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
+                "dtype": "u8", "data": "synthetic",
+                "config": {"workload": SERVE_WORKLOAD + f", {args.rate:.0f} req/s for {args.seconds:.1f} s"},
+                **{k: v for k, v in r.items() if k != "frames_per_s"}}
     print(json.dumps(line))
 
 
@@ -438,12 +518,13 @@ def main():
                 sec.append(s)
         fps = 1.0 / statistics.mean(sec)
         line = {
-            "impl": "reference", "metric": "1080p frames/s (FSBM + ACBM per frame pair)",
+            "impl": "reference", "metric": METRIC,
             "value": fps, "unit": "frames/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(sec),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 frame pair per step"},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": thr, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": "1 frame pair per step: FSBM on all cores + ACBM on one"},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -485,8 +566,9 @@ def main():
         step()
     me.me_acbm_sequence_status(W, H_PAD, N, M, P, pairs)
 
-    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    gpu_index = (int(os.environ["CUDA_VISIBLE_DEVICES"])
+                 if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks = ClockSampler(gpu_index)
     step_ms, fsbm_ms, acbm_ms = [], [], []
     clocks.start()
     for _ in range(args.steps):
@@ -638,7 +720,13 @@ def main():
     ek1.record(stream)
     torch.cuda.synchronize()
     fsbm_kernel_ms = ek0.elapsed_time(ek1) / reps
-    peak_absdiff = 152 * 256 * 2.07e9          # SMs x absdiff/clk/SM x max SM clock
+    # peak: this device's SMs x the packed-SAD lane rate per SM per clock
+    # measured by the library's probe (4 absdiffs per lane-op) x the median
+    # SM clock sampled during the timed steps
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    lanes_per_clk = me.me_sad_peak(0)[1]
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak_absdiff = n_sm * 4 * lanes_per_clk * sm_mhz * 1e6
     seq_fsbm_ms = statistics.mean(fsbm_ms) / pairs
     achieved = ABSDIFF_PER_FRAME / (seq_fsbm_ms * 1e-3)
 
@@ -694,11 +782,25 @@ def main():
     d2h = sum(x.numel() * x.element_size() for x in h_out)
     e2e_fps = pairs * world / e2e_s
 
+    # the batched and served forms, compact legs beside the step: the 64-stream
+    # mix (one persistent launch per step against per-frame plain calls,
+    # outputs compared) and a Poisson serve run, each with its clock record
+    legs = {}
+    if rank == 0 and world == 1 and not args.no_extra_legs:
+        b64 = batch64_measure(4, gpu_index)
+        legs["batch64"] = {"workload": BATCH64_WORKLOAD, "steps": b64["steps"],
+                           "acbm": b64["acbm"], "fsbm": b64["fsbm"],
+                           "fsbm_absdiff_per_s_T": b64["fsbm_absdiff_per_s_T"], "clocks": b64["clocks"]}
+        rig = ServeRig()
+        legs["serve"] = dict(rig.run(4000.0, 3.0, gpu_index), workload=SERVE_WORKLOAD)
+        rig.close()
+
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         thr = cpu_threads()
         sec = oracle_sample(frames_np, 2, thr)
         cpu_base = {"value": 1.0 / sec, "unit": "frames/s", "cores": thr, "kind": "oracle",
+                    "cpu_model": cpu_model(),
                     "sample": "frame pairs 1-2 of the sequence: oracle FSBM (OpenMP over "
                               f"blocks, {thr} threads) + oracle ACBM (one thread)"}
 
@@ -713,7 +815,7 @@ def main():
 
     pair_ms = [f + a for f, a in zip(pair_fsbm_ms, pair_acbm_ms)]
     line = {
-        "metric": "1080p frames/s (FSBM + ACBM per frame pair), candidate-SADs/s, p99 ms",
+        "metric": METRIC,
         "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
@@ -766,8 +868,9 @@ def main():
                      "traffic": FSBM_SEQ_DRAM_BYTES_PER_FRAME * (pairs + 1),
                      "traffic_unit": "bytes/launch",
                      "algorithmic_bytes": (pairs + 1) * W * H_PAD,
-                     "peak_source": "152 SMs x 64 packed-SAD lanes/clk x 4 bytes x 2070 MHz "
-                                    "(lane rate measured by me_sad_peak)"},
+                     "peak_source": f"{n_sm} SMs x {lanes_per_clk:.2f} packed-SAD lanes/clk/SM "
+                                    f"(measured by me_sad_peak) x 4 absdiffs x {sm_mhz:.0f} MHz "
+                                    "(median SM clock sampled during the timed steps)"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "outputs_identical": same_e2e,
                 "form": "frames up in 4 chunks on a copy stream, each chunk's full search "
@@ -775,6 +878,7 @@ def main():
         "gpu_launches": 4 * args.steps,   # k_fsbm_pipe; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
+        **legs,
     }
     print(json.dumps(line))
 

@@ -16,11 +16,13 @@ def test_reference_arm_prints_one_json_line():
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     line = json.loads(lines[-1])
     assert line["impl"] == "reference"
-    assert line["metric"].startswith("1080p frames/s") and line["unit"] == "frames/s"
+    import bench
+    assert line["metric"] == bench.METRIC and line["unit"] == "frames/s"    # the native arm's string
     assert line["higher_is_better"] is True and line["value"] > 0
     assert line["steps"] == 1 and line["warmup"] == 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["cpu_model"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

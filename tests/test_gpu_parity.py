@@ -173,6 +173,20 @@ def test_fsbm_1080p_sampled(me, orc):
     _eq("sad", sad.ravel()[blocks], ws)
 
 
+def test_fsbm_1080p_whole_frame(me, orc):
+    """One whole 1920x1088 frame pair at p = 32 (the headline workload's
+    shape, 8160 blocks, the pipelined search behind me_fsbm): every block's
+    vector, J and SAD against the oracle's full search of Sec. 2.3."""
+    import os
+    seq = synth.config_sequence("1080p", seed=17, n_frames=2)
+    lam = orc.lambda_q8(28)
+    mv, J, sad = _fsbm_gpu(me, seq[1], seq[0], 16, 16, 32, lam)
+    wmv, wJ, ws = orc.fsbm(seq[1], seq[0], 16, 16, 32, lam, nthreads=os.cpu_count() or 8)
+    _eq("mv", mv, wmv)
+    _eq("J", J, wJ)
+    _eq("sad", sad, ws)
+
+
 def test_fsbm_2160p_p64_sampled(me, orc):
     spec = synth.batch_mix()[-1]
     seq = synth.stream_frames(spec, 2)

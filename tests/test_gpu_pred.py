@@ -2,8 +2,7 @@
 (SAD volume, then the persistent wavefront): bit-exact against the oracle
 for every block shape and several search ranges on fields with many distinct
 vectors, at CIF for a range of p (every run length of the 16x16 plans), the
-sequence form against the per-pair oracle, 1080p p=32 by sampled blocks
-(each block's step checked with its predictor taken from the GPU field) plus
+sequence form against the per-pair oracle, one whole 1080p p=32 frame plus
 the lambda = 0 reduction to plain FSBM, and repeated runs of one plan."""
 import numpy as np
 import pytest
@@ -81,26 +80,22 @@ def test_pred_repeated_runs_of_one_plan(me, orc):
             assert np.array_equal(g, w), lam
 
 
-def test_pred_1080p_sampled(me, orc):
-    """1920x1088, 16x16, p = 32: 60 sampled blocks (corners, edges, first row
-    and column, random) each checked against the oracle's one-block step with
-    its predictor taken from the GPU field; lambda = 0 equals me_fsbm."""
+def test_pred_1080p_whole_frame(me, orc):
+    """1920x1088, 16x16, p = 32: every block of one pair against the oracle's
+    predictor-coded search run over the whole frame in raster order (each
+    block's predictor from the oracle's own field); lambda = 0 equals
+    me_fsbm."""
     import torch
     seq = synth.config_sequence("1080p", seed=91, n_frames=2)
     cur, ref = np.ascontiguousarray(seq[1]), np.ascontiguousarray(seq[0])
     N = M = 16
     p = 32
-    BW, BH = cur.shape[1] // N, cur.shape[0] // M
     lam = orc.lambda_q8(28)
     mv, J, sad = _run(me, cur, ref, N, M, p, lam)
-    rng = np.random.default_rng(2)
-    blocks = np.unique(np.concatenate([
-        [0, 1, BW - 1, BW, 2 * BW - 1, (BH - 1) * BW, BH * BW - 1, 5 * BW + 7],
-        rng.integers(0, BW * BH, 52)])).astype(np.int32)
-    bmv, bJ, bs = orc.fsbm_pred_blocks(cur, ref, N, M, p, lam, mv, blocks)
-    assert np.array_equal(mv.reshape(-1, 2)[blocks], bmv)
-    assert np.array_equal(J.ravel()[blocks], bJ)
-    assert np.array_equal(sad.ravel()[blocks], bs)
+    wmv, wJ, ws = orc.fsbm_pred(cur, ref, N, M, p, lam)
+    assert np.array_equal(mv, wmv)
+    assert np.array_equal(J, wJ)
+    assert np.array_equal(sad, ws)
     mv0, J0, _ = _run(me, cur, ref, N, M, p, 0)
     f = me.me_fsbm(torch.from_numpy(cur).cuda(), torch.from_numpy(ref).cuda(), N, M, p, 0)
     torch.cuda.synchronize()

@@ -111,6 +111,54 @@ def test_fsbm_sequence_pipelined_1080p_equals_per_pair(me, orc, monkeypatch):
         assert np.array_equal(_u32(r.sad[k]).ravel()[blocks], sad), k
 
 
+def test_bench_step_matches_chained_oracle(me, orc):
+    """The benchmark's own step: 1080p p = 32, Qp 28, the 60-frame sequence of
+    seed 2026 with all 59 pairs in one me_fsbm_sequence and one
+    me_acbm_sequence launch.  ACBM: the first 8 pairs equal the oracle chained
+    pair by pair (mv, J, mask, SAD, load); every pair keeps the properties
+    that hold at any length (a full-searched block equals FSBM with load
+    (2p+1)^2, FSBM J <= ACBM J, other loads within the PBM bound).  FSBM:
+    whole frames of pairs 0, 29 and 58 and sampled blocks of every pair
+    against the oracle."""
+    import os
+    import torch
+    nthr = os.cpu_count() or 8
+    seq_np = synth.config_sequence("1080p", seed=2026, n_frames=60)
+    frames = torch.from_numpy(seq_np).cuda()
+    lam = orc.lambda_q8(28)
+    fs = me.me_fsbm_sequence(frames, 16, 16, 32, lam)
+    ac = me.me_acbm_sequence(frames, 16, 16, 32, lam, me.params(qp=28))
+    torch.cuda.synchronize()
+    assert me.me_fsbm_sequence_status() == 0
+    me.me_acbm_sequence_status(1920, 1088, 16, 16, 32, 59)     # raises on a timed-out wait
+    f_mv, f_J, f_sad = fs.mv.cpu().numpy(), _u32(fs.J), _u32(fs.sad)
+    a_mv, a_J, a_mask = ac.mv.cpu().numpy(), _u32(ac.J), ac.mask.cpu().numpy()
+    a_sad, a_load = _u32(ac.sad), _u32(ac.load)
+    prev = None
+    for k in range(8):
+        mv, J, mask, sad, load = orc.acbm(seq_np[k + 1], seq_np[k], 16, 16, 32, lam,
+                                          orc.params(qp=28), prev)
+        prev = mv
+        for nm, g, w in (("mv", a_mv[k], mv), ("J", a_J[k], J), ("mask", a_mask[k], mask),
+                         ("sad", a_sad[k], sad), ("load", a_load[k], load)):
+            assert np.array_equal(g, w), (k, nm)
+    BW, BH = 120, 68
+    rng = np.random.default_rng(11)
+    for k in range(59):
+        fsb = a_mask[k] == 1
+        assert fsb.any() and not fsb.all(), k
+        assert np.array_equal(a_mv[k][fsb], f_mv[k][fsb]) and np.array_equal(a_J[k][fsb], f_J[k][fsb]), k
+        assert np.all(a_load[k][fsb] == 65 * 65) and np.all(a_load[k][~fsb] <= 22), k
+        assert np.all(f_J[k] <= a_J[k]), k
+        blocks = rng.choice(BW * BH, 24, replace=False).astype(np.int32)
+        mv, J, sad = orc.fsbm_blocks(seq_np[k + 1], seq_np[k], 16, 16, 32, lam, blocks, nthreads=nthr)
+        assert np.array_equal(f_mv[k].reshape(-1, 2)[blocks], mv), k
+        assert np.array_equal(f_J[k].ravel()[blocks], J) and np.array_equal(f_sad[k].ravel()[blocks], sad), k
+    for k in (0, 29, 58):
+        mv, J, sad = orc.fsbm(seq_np[k + 1], seq_np[k], 16, 16, 32, lam, nthreads=nthr)
+        assert np.array_equal(f_mv[k], mv) and np.array_equal(f_J[k], J) and np.array_equal(f_sad[k], sad), k
+
+
 @pytest.mark.parametrize("name,n,p,qp", [("qcif", 10, 16, 28), ("cif", 5, 16, 40),
                                          ("1080p", 3, 32, 28)])
 def test_acbm_sequence_matches_chained_oracle(me, orc, name, n, p, qp):
