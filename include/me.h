@@ -373,11 +373,14 @@ void me_server_destroy(me_server *s);
  * fixed budget, a plugin loaded into another process's CUDA context, or code
  * that must not allocate after start-up.  The paper has no counterpart; this
  * is a deployment variant.  It allocates nothing: its scratch memory is one
- * fixed device array of 4 MiB inside the library (enough for frames up to
- * about 1920x1088 at any p), which every GPU that loads the library holds
- * until the process exits.  Arguments, outputs and errors are those of
- * me_acbm; a frame whose scratch would exceed the array returns ME_ERR_NOMEM
- * before anything is enqueued.
+ * fixed device array of 4 MiB inside the library, which every GPU that loads
+ * the library holds until the process exits.  A call needs the padded
+ * reference, (16*ceil(W/16) + 2P + 16) x (H + 2P) bytes with
+ * P = 16*ceil(p/16), plus 20 bytes per block: frames up to 1920x1088 fit at
+ * any p for every block shape of 4x8 / 8x4 pixels or larger; 4x4 blocks fit
+ * frames up to 1280x720 (not 1920x1088).  Arguments, outputs and errors are
+ * those of me_acbm; a frame whose scratch would exceed the array returns
+ * ME_ERR_NOMEM before anything is enqueued.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
  * Every call on a device shares the one array, and a call leaves its contents
@@ -401,6 +404,25 @@ int me_acbm_noalloc(const uint8_t *cur, const uint8_t *ref, int W, int H, int N,
  * SM (from the SM cycle counter).  Synchronous. */
 int me_sad_peak(int variant, double *absdiff_per_s, double *lane_ops_per_clk_per_sm,
                 me_stream_t stream);
+
+/* ----------------------------------------------------------------- autotuner */
+
+/* The library tunes its launch forms by measurement (not a paper item; the
+ * paper has no implementation): on the first call of a shape, me_fsbm,
+ * me_fsbm_sequence and me_acbm_sequence time every candidate launch form
+ * (run length of the full searches, per-group or pipelined full-search
+ * kernel, the CTA roles of the ACBM sequence kernel) with CUDA events on the
+ * caller's stream, synchronising it, and keep the fastest for the rest of the
+ * process.  Every candidate computes the same outputs.  A first call made
+ * while the stream is being captured into a CUDA graph, or with the
+ * environment variable ME_TUNE=0, takes the cost model's choice without
+ * timing; ME_TUNE_FORCE=<i> runs candidate i of every tuned call (tests).
+ *
+ * me_tune_log writes one text line per tuned shape -- the shape, the model's
+ * and the chosen candidate and every candidate's best time in ms (-1: not
+ * timed) -- NUL-terminated into buf (at most len bytes, truncated), and
+ * returns the bytes the whole text needs including the NUL. */
+int me_tune_log(char *buf, int len);
 
 #ifdef __cplusplus
 }

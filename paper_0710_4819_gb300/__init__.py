@@ -19,7 +19,7 @@ __all__ = [
     "load_library", "MeError", "AcbmParams", "me_lambda_q8", "me_mv_bits",
     "me_acbm_default_params", "me_padded_geometry", "me_pad_ref", "me_intra_sad",
     "me_fsbm", "me_acbm", "me_halfpel", "me_halfpel_sequence", "me_sad_deviation",
-    "me_motion_study", "me_fsbm_sequence_status", "me_fsbm_pred", "me_fsbm_pred_sequence", "me_fsbm_pred_status", "me_sad_peak", "Batch", "Server", "STATUS",
+    "me_motion_study", "me_fsbm_sequence_status", "me_fsbm_pred", "me_fsbm_pred_sequence", "me_fsbm_pred_status", "me_sad_peak", "me_tune_log", "Batch", "Server", "STATUS",
 ]
 
 _lock = threading.Lock()
@@ -117,6 +117,7 @@ def load_library(build_if_missing: bool = True):
                                   u32, vp, ctypes.POINTER(AcbmParams), vp, vp, vp, vp, vp, vp],
                                  c_int),
             "me_acbm_sequence_status": ([c_int, c_int, c_int, c_int, c_int, c_int, vp], c_int),
+            "me_tune_log": ([ctypes.c_char_p, c_int], c_int),
             "me_sad_peak": ([c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), vp], c_int),
             "me_batch_create": ([ctypes.POINTER(vp)], c_int),
@@ -461,6 +462,16 @@ def me_sad_peak(variant: int = 0, stream=None):
     _check(load_library().me_sad_peak(variant, ctypes.byref(a), ctypes.byref(b),
                                       _stream_ptr(stream)), "me_sad_peak")
     return a.value, b.value
+
+
+def me_tune_log() -> str:
+    """The autotuner's record: one line per tuned shape (model's and chosen
+    candidate, every candidate's best time in ms)."""
+    lib = load_library()
+    need = lib.me_tune_log(None, 0)
+    buf = ctypes.create_string_buffer(max(1, need))
+    lib.me_tune_log(buf, need)
+    return buf.value.decode()
 
 
 class Batch:

@@ -113,17 +113,19 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
                      unsigned long long* items, unsigned long long* q, cudaStream_t s) {
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
   k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
   if (total_items > 0) {
-    const int gt = std::max(1, std::min((total_items + 255) / 256, 152 * 8));
+    const int gt = std::max(1, std::min((total_items + 255) / 256, nsm * 8));
     k_batch_items<<<gt, 256, 0, s>>>(segs, nseg, total_items, shapes, N, items);
     ME_CUDA(cudaGetLastError());
   }
-  const int gp = (int)std::max<long long>(1, std::min<long long>((total_pad + 255) / 256, 152 * 16));
+  const int gp = (int)std::max<long long>(1, std::min<long long>((total_pad + 255) / 256, nsm * 16LL));
   k_batch_pad<<<gp, 256, 0, s>>>(shapes, streams, nstreams, total_pad);
   ME_CUDA(cudaGetLastError());
-  const int gi = std::max(1, std::min((total_blocks + 7) / 8, 152 * 16));
+  const int gi = std::max(1, std::min((total_blocks + 7) / 8, nsm * 16));
   int st = ME_ERR_ARG;
 #define X(n_, m_)                                                                              \
   if (N == n_ && M == m_) {                                                                    \
@@ -135,9 +137,6 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
   if (st) return st;
   ME_CUDA(cudaGetLastError());
   // half the CTAs run PBM warps, half the full searches: two per SM
-  int dev = 0, nsm = 0;
-  ME_CUDA(cudaGetDevice(&dev));
-  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int pw = batch_pbm_warps(N, M, p_max);
   const int ww = pbm_win_words(N, M, p_max);
   st = ME_ERR_ARG;

@@ -282,6 +282,50 @@ FsPlan fs_plan(int N, int M, int p, int bpc_max) {
   return best;
 }
 
+// The k plans of lowest modelled cost with distinct (T, G, threads), best
+// first (the first equals fs_plan's): the candidates the autotuner times.
+std::vector<FsPlan> fs_plans_ranked(int N, int M, int p, int bpc_max, int k) {
+  const int n = 2 * p + 1;
+  const int* Ts = (N == 16 && M == 16) ? kT16 : kTOther;
+  const int nT = (N == 16 && M == 16) ? 4 : 1;
+  std::vector<std::pair<double, FsPlan>> all;
+  static const int kG[] = {8, 16, 32, 64, 128, 256, 512};
+  static const int kThr[] = {64, 128, 256, 512};
+  for (int ti = 0; ti < nT; ti++) {
+    const int T = Ts[ti];
+    const int tasks = n * ((n + T - 1) / T);
+    for (int G : kG) {
+      const int rounds = (tasks + G - 1) / G;
+      for (int thr : kThr) {
+        if (thr < G || thr % G) continue;
+        const int bpc = thr / G;
+        if (bpc > std::min(bpc_max, 16)) continue;
+        const size_t smem = smem_dispatch(N, M, T, p, bpc);
+        if (smem > 110 * 1024) continue;
+        const double per_thread = rounds * task_cost(N, M, T) + stage_cost(N, M, T, p, bpc) / thr;
+        const int warps = thr / 32;
+        int ctas = std::min(64 / warps, 65536 / (thr * 128));
+        ctas = std::min(ctas, (int)((228 * 1024) / (smem + 1024)));
+        if (ctas < 1) continue;
+        const double occ = std::min(1.0, (double)(ctas * warps) / 16.0);
+        all.push_back({per_thread * thr / ((double)bpc * n * n) / occ, FsPlan{T, G, thr, smem, 1}});
+      }
+    }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const std::pair<double, FsPlan>& x,
+                                              const std::pair<double, FsPlan>& y) {
+    return x.first < y.first * 0.999;
+  });
+  std::vector<FsPlan> out{fs_plan(N, M, p, bpc_max)};
+  for (const auto& e : all) {
+    if ((int)out.size() >= k) break;
+    bool dup = false;
+    for (const FsPlan& o : out) dup |= o.T == e.second.T && o.G == e.second.G && o.threads == e.second.threads;
+    if (!dup) out.push_back(e.second);
+  }
+  return out;
+}
+
 // Threads per block for a fixed run length and CTA size (persistent kernels,
 // whose launch fixes both): the G with the lowest modelled cost per candidate.
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit) {
@@ -392,9 +436,9 @@ static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* 
 int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
                 uint32_t lam, int16_t* mv, uint32_t* J, uint32_t* sad, cudaStream_t s) {
   FsPlan pl = fs_plan(N, M, p, W / N);
-  if (!plan_override(N, M, &pl, p, W / N) && fsbm_pipe_applies(N, M, p)) {
+  if (!plan_override(N, M, &pl, p, W / N)) {
     const uint8_t* frames[2] = {ref, cur};
-    return launch_fsbm_pipe(frames, 1, W, H, p, lam, mv, J, sad, s);
+    return fsbm_tuned(frames, 1, W, H, N, M, p, lam, mv, J, sad, s);
   }
   ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
 }
@@ -467,7 +511,9 @@ static int launch_prologue_t(const AcbmArgs& a, AcbmArgs* slot, const PadGeom& p
                              unsigned long long* bkeys, int* bdone, cudaStream_t s) {
   const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16),
                                              32LL * (W / N) * (H / M));
-  const int grid = (int)std::min<long long>((work + 255) / 256, 152 * 8);
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
+  const int grid = (int)std::min<long long>((work + 255) / 256, nsm * 8LL);
   k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, cnt, nwaves, bkeys,
                                              bdone);
   ME_CUDA(cudaGetLastError());

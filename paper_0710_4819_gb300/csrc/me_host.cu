@@ -77,6 +77,42 @@ int ensure_dynamic_smem(const void* kernel, size_t bytes) {
 
 bool aligned4(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0; }
 
+// Per-device SM count and peak SM clock (kHz), read once per device.
+struct DevInfo {
+  int sms = 0, clock_khz = 0;
+};
+static std::mutex g_dev_mu;
+static std::vector<DevInfo> g_dev;
+
+static int dev_info(DevInfo* out) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+  DevInfo& d = g_dev[dev];
+  if (d.sms == 0) {
+    ME_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    ME_CUDA(cudaDeviceGetAttribute(&d.clock_khz, cudaDevAttrClockRate, dev));
+  }
+  *out = d;
+  return ME_OK;
+}
+
+int sm_count(int* out) {
+  DevInfo d;
+  const int st = dev_info(&d);
+  *out = st == ME_OK && d.sms > 0 ? d.sms : 1;
+  return st;
+}
+
+long long wait_cycles(long long timeout_ns) {
+  DevInfo d;
+  // without the clock rate, assume 3 GHz (above any GB300 clock: the bound
+  // stays at least the timeout)
+  const long long khz = dev_info(&d) == ME_OK && d.clock_khz > 0 ? d.clock_khz : 3000000;
+  return timeout_ns / 1000000 * khz + timeout_ns % 1000000 * khz / 1000000;
+}
+
 // One pool per device, created on first use, that keeps freed blocks cached
 // (release threshold = max) so steady-state calls do not return memory to the
 // driver between frames.

@@ -5,6 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
 
 #include "../../include/me.h"
 
@@ -38,6 +41,25 @@ int scratch_alloc(void** ptr, size_t bytes, cudaStream_t s);
 int scratch_free(void* ptr, cudaStream_t s);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// SM count of the current device (cached per device).
+int sm_count(int* out);
+// A spin-wait bound in SM clock cycles for `timeout_ns` at the current
+// device's peak SM clock (cached per device): at lower clocks the wait lasts
+// longer than the timeout, never shorter.
+long long wait_cycles(long long timeout_ns);
+
+// The autotuner (me_tune.cu).  tune_select times run(c) for every candidate
+// c (names[c] describes it) on stream s with CUDA events -- one untimed run,
+// then the best of two timed runs -- and sets *chosen to the fastest.  When
+// tuning is off (ME_TUNE=0), the stream is being captured, or there is one
+// candidate, it runs nothing and chooses `model` (the cost model's pick).
+// Every call is recorded for me_tune_log.  tune_forced(n): a candidate index
+// forced by ME_TUNE_FORCE (tests of every candidate), else -1.
+bool tune_enabled();
+int tune_forced(int n);
+int tune_select(const std::string& what, const std::vector<std::string>& names, int model,
+                cudaStream_t s, const std::function<int(int)>& run, int* chosen);
 
 // Geometry of the anti-diagonal waves x + 2y = w of a BW x BH block grid.
 struct Waves {

@@ -51,7 +51,7 @@ struct PredFrames {
 
 struct PredCtrl {
   int epoch, error, err_item;
-  long long timeout_ns;
+  long long timeout_cycles;  // bound of every spin-wait (SM clock cycles)
   alignas(128) int next;  // claims
 };
 
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kPredThreads) k_pred_wave(
   constexpr int kCols = (2 * kMaxP + 1 + 31) / 32;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
   const volatile int* verr = &ctrl->error;
-  const long long lim = wait_cycles(ctrl->timeout_ns);
+  const long long lim = ctrl->timeout_cycles;
   for (;;) {
     if (tid == 0) {
       s_item = atomicAdd(&ctrl->next, 1);
@@ -359,7 +359,7 @@ static int build_pred_plan(PredPlan* pl) {
   ME_CUDA(cudaMemcpy(pl->items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice));
   PredCtrl c;
   std::memset(&c, 0, sizeof(c));
-  c.timeout_ns = 1000000000ll;
+  c.timeout_cycles = wait_cycles(1000000000ll);     // 1 s
   ME_CUDA(cudaMemcpy(pl->ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
   pl->smem = 4 * (size_t)pl->vstride;   // SAD volume + candidate list
   {

@@ -3,6 +3,7 @@
 // ACBM for one block (one warp), and the full-search plan (tile choice).
 #pragma once
 #include <cstdio>
+#include <vector>
 
 #include "../../include/me.h"
 #include "me_device.cuh"
@@ -246,10 +247,10 @@ __device__ __forceinline__ unsigned long long warp_wait_flags(const unsigned lon
   return w;
 }
 
-// Spin-wait bound in SM clock cycles (the SM-local cycle counter is cheap to
-// read, unlike the global timer): timeout_ns * 2, about the timeout at 2 GHz
-// and longer at lower clocks.
-__host__ __device__ __forceinline__ long long wait_cycles(long long timeout_ns) { return 2 * timeout_ns; }
+// Spin-wait bounds are counted in SM clock cycles (the SM-local cycle counter
+// is cheap to read, unlike the global timer); the host converts a timeout to
+// cycles at the device's peak SM clock (wait_cycles in me_host.h), so a wait
+// lasts at least the timeout at any clock.
 
 // ---------------------------------------------------------------------------
 // PBM of one block by one warp, in two parts so that the memory traffic that
@@ -427,6 +428,7 @@ struct FsPlan {
 // (SAD, load and epilogue instructions per useful candidate, lanes idle in the
 // last round, shared-memory staging).  bpc_max = 1 forces one block per CTA.
 FsPlan fs_plan(int N, int M, int p, int bpc_max);
+std::vector<FsPlan> fs_plans_ranked(int N, int M, int p, int bpc_max, int k);
 FsPlan fs_plan_latency(int N, int M, int p);
 FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t smem_limit);
 
@@ -454,7 +456,13 @@ struct PipeOut {
   int ref_fixed;
 };
 int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, int H, int p,
-                          uint32_t lam, const PipeOut& out, cudaStream_t s);
+                          uint32_t lam, const PipeOut& out, cudaStream_t s, int T = 0);
+
+// The full search of K pairs (frames[k] -> frames[k+1], outputs [K][BH][BW])
+// in the launch form the autotuner picked for the shape (timed on the first
+// call; every form gives the same outputs).
+int fsbm_tuned(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+               uint32_t lam, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s);
 
 // Calls FN<N, M, T>(...) for the run lengths instantiated per block shape
 // (pl.T chooses among them for 16x16); expects N, M and pl in scope.

@@ -31,11 +31,13 @@ namespace me {
 constexpr int kSeqMax = 64;     // frame pairs per call
 constexpr int kSeqThreads = 256;
 constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
-// Every kSeqSearchEvery-th SM (by %smid) hosts two search CTAs instead of one
-// PBM and one search CTA.  Measured at 1080p p=32 (59 pairs): one of each on
-// every SM 0.1196 ms of ACBM per pair; two search CTAs on every 8th / 4th /
-// 3rd / 2nd SM 0.1159 / 0.1119 / 0.1097 / 0.1113 ms; without occlusions
-// (1.5 % of blocks searched) 0.0841 / - / 0.0834 / 0.0844 / 0.0911 ms.
+// The model's role split of k_acbm_seq: every kSeqSearchEvery-th SM (by
+// %smid) hosts two search CTAs instead of one PBM and one search CTA.
+// Measured at 1080p p=32 (59 pairs): one of each on every SM 0.1196 ms of
+// ACBM per pair; two search CTAs on every 8th / 4th / 3rd / 2nd SM 0.1159 /
+// 0.1119 / 0.1097 / 0.1113 ms; without occlusions (1.5 % of blocks searched)
+// 0.0841 / - / 0.0834 / 0.0844 / 0.0911 ms.  The autotuner also times the
+// 2nd and 4th SM splits.
 constexpr int kSeqSearchEvery = 3;
 constexpr int kSeqSP = 193;     // compile-time shifted-word pitch of the main FSBM build (odd:
                                 // rows of different runs start on different banks)
@@ -60,7 +62,7 @@ struct SeqArgs {
 // reading waits behind those reads for microseconds.
 struct SeqCtrl {
   int epoch, error, err_item;   // read-mostly (error is written only on failure)
-  long long timeout_ns;
+  long long timeout_cycles;     // bound of every spin-wait (SM clock cycles)
   alignas(128) int next;        // PBM claims
   alignas(128) int fs_head;     // search-CTA claims
   alignas(128) int fs_tail;     // queue appends
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              unsigned long long* __restrict__ q,
                                                              unsigned long long* __restrict__ bkey,
                                                              int* __restrict__ bdone, int S,
-                                                             int pbm_warps, int nsm) {
+                                                             int pbm_warps, int search_every) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_item, s_role, s_slice;
@@ -508,10 +510,10 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int BW = W / N, BH = H / M, nbf = BW * BH;
   const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
-  const long long timeout = ctrl->timeout_ns;
+  const long long timeout = ctrl->timeout_cycles;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
   const int n = 2 * p + 1;
-  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr, kSeqSearchEvery);
+  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr, search_every);
   __syncthreads();
 
   if (s_role == 0) {
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       {
         const unsigned long long w = warp_wait_flags(nidx >= 0 ? flags + nidx : nullptr, epoch,
                                                      &ctrl->error, &ctrl->err_item,
-                                                     wait_cycles(timeout), i);
+                                                     timeout, i);
         if (nidx >= 0) {
           cx = pub_mvx(w);
           cy = pub_mvy(w);
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         const volatile int* done = &ctrl->pbm_done;
         const volatile int* tail = &ctrl->fs_tail;
         const volatile int* err = &ctrl->error;
-        const long long t0 = clock64(), lim = wait_cycles(timeout);
+        const long long t0 = clock64(), lim = timeout;
         int got = -1;
         unsigned ns = 32;
         for (int it = 0;; it++) {
@@ -708,10 +710,330 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
   }
 }
 
+// ------------------------------------------------------------------ ACBM, one CTA per SM
+//
+// The same ACBM over K pairs with both roles in one CTA per SM (512 threads):
+// warps 0..pw-1 run PBM exactly as the PBM CTAs of k_acbm_seq; the other
+// warps form the SM's search group.  A PBM warp whose block fails both
+// conditions has the block's whole search window and current pixels in its
+// shared memory already (staged for PBM), so it copies them into a free
+// hand-off slot of its own CTA and goes on to its next block; the search
+// group builds its shifted words from that slot (no second trip to global
+// memory) and searches the block with all its threads.  When both slots are
+// taken the block goes to the global queue instead, which every search group
+// drains when its own slots are empty (staging that window from the padded
+// reference itself).  The search group synchronises with a named barrier, so
+// the PBM warps never wait for it.
+//
+// Progress: a PBM warp only waits for blocks claimed before its own; such a
+// block is either published, in some CTA's slot (that CTA's search group
+// runs and takes its slots first), or in the global queue (whose entries a
+// running PBM warp writes right after reserving them).  A search group exits
+// once every block has been through PBM, the global queue is drained and its
+// own slots are empty.  Every wait is also bounded in time.
+constexpr int kSeq2Threads = 512;
+constexpr int kSeq2Slots = 2;   // hand-off slots per CTA; slot kSeq2Slots: global jobs
+
+__device__ __forceinline__ void seq2_bar(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(kSeq2Threads, 1) k_acbm_seq2(
+    SeqFrames fr, SeqArgs a, int W, int H, int p, PadGeom pg, const uint8_t* __restrict__ refpad,
+    const uint32_t* __restrict__ intra, unsigned long long* __restrict__ flags,
+    const int* __restrict__ items, int total, SeqCtrl* ctrl, unsigned long long* __restrict__ q,
+    int pbm_warps) {
+  constexpr int NW = N / 4;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_state[kSeq2Slots];    // 0 free, 1 being filled, 2 full
+  __shared__ int s_seq[kSeq2Slots];      // claim index (age) of the block in each full slot
+  __shared__ int s_blk[kSeq2Slots + 1];  // block of each slot
+  __shared__ int s_job;
+  __shared__ unsigned long long s_red;
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int BW = W / N, BH = H / M, nbf = BW * BH;
+  const int epoch = *reinterpret_cast<volatile int*>(&ctrl->epoch);
+  const long long timeout = ctrl->timeout_cycles;
+  const size_t padsz = (size_t)pg.pitch * pg.rows;
+  const int n = 2 * p + 1;
+  const int wwin = pbm_win_words(N, M, p);   // window words of a PBM warp / slot
+  const int wwords = wwin + M * NW;          // + the current block
+  uint32_t* slots = smem + pbm_warps * wwords;               // [kSeq2Slots + 1][wwords]
+  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x - 32 * pbm_warps);
+  uint32_t* sh = slots + (kSeq2Slots + 1) * wwords;          // [g.rows][g.sp]
+  uint32_t* tabJ = sh + g.rows * g.sp;
+  uint32_t* tabK = tabJ + g.rows;
+  uint32_t* tabQ = tabK + g.rows;
+  if (tid < kSeq2Slots) s_state[tid] = 0;
+  if (tid == 0) s_red = kNoKey;
+  __syncthreads();
+
+  if (warp < pbm_warps) {
+    // ---------------------------------------------------------------- PBM warps
+    uint32_t* win = smem + warp * wwords;
+    uint32_t* curs = win + wwin;
+    int nxt = 0, onxt = 0;
+    if (lane == 0) {
+      nxt = atomicAdd(&ctrl->next, 1);
+      if (nxt < total) onxt = items[nxt];
+    }
+    for (;;) {
+      const int i = __shfl_sync(FULL, nxt, 0);
+      if (i >= total) break;
+      const int o = __shfl_sync(FULL, onxt, 0);
+      const int k = o / nbf, b = o - k * nbf;
+      const int bx = b % BW, by = b / BW;
+      const PbmWin wg = pbm_stage<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, p, bx * N,
+                                        by * M, curs, win);
+      const uint32_t ix = intra[o];
+      int cx = 0, cy = 0, nidx = -1;
+      bool valid = false;
+      if (lane < 4) {
+        const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
+        const int dy = (lane == 0) ? 0 : -1;
+        const int nx = bx + dx, ny = by + dy;
+        if (nx >= 0 && nx < BW && ny >= 0) {
+          nidx = k * nbf + ny * BW + nx;
+          valid = true;
+        }
+      } else if (lane < 13) {
+        const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
+        if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+          valid = true;
+          if (k > 0) {
+            nidx = (k - 1) * nbf + ny * BW + nx;
+          } else if (a.prev0) {
+            cx = a.prev0[2 * (ny * BW + nx)];
+            cy = a.prev0[2 * (ny * BW + nx) + 1];
+          }
+        }
+      } else if (lane == 13) {
+        valid = true;
+      }
+      {
+        const unsigned long long w = warp_wait_flags(nidx >= 0 ? flags + nidx : nullptr, epoch,
+                                                     &ctrl->error, &ctrl->err_item, timeout, i);
+        if (nidx >= 0) {
+          cx = pub_mvx(w);
+          cy = pub_mvy(w);
+        }
+      }
+      const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, p, a.lam, ix, a.alpha, a.beta, a.gnum,
+                                         a.gden, a.qp, a.refine, curs, win);
+      if (r.pass) {
+        if (lane == 0) {
+          const Decoded d = decode_key(r.key, p, a.lam);
+          atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
+          int16_t* field = a.mv + (size_t)k * nbf * 2;
+          field[2 * b] = (int16_t)d.mvx;
+          field[2 * b + 1] = (int16_t)d.mvy;
+          a.J[o] = d.J;
+          a.mask[o] = 0;
+          if (a.sad) a.sad[o] = d.sad;
+          if (a.load) a.load[o] = (uint32_t)r.load;
+        }
+      } else {
+        // hand the staged window to this SM's search group, or queue it
+        int got = -1;
+        if (lane == 0) {
+          for (int s = 0; s < kSeq2Slots && got < 0; s++)
+            if (atomicCAS(&s_state[s], 0, 1) == 0) got = s;
+        }
+        got = __shfl_sync(FULL, got, 0);
+        if (got >= 0) {
+          uint32_t* dst = slots + got * wwords;
+          const int nw = wg.rows * wg.wp;
+          for (int j = lane; j < nw; j += 32) dst[j] = win[j];
+          for (int j = lane; j < M * NW; j += 32) dst[wwin + j] = curs[j];
+          __syncwarp();
+          if (lane == 0) {
+            s_blk[got] = o;
+            s_seq[got] = i;
+            __threadfence_block();
+            atomicExch(&s_state[got], 2);
+          }
+        } else if (lane == 0) {
+          const int slot = atomicAdd(&ctrl->fs_tail, 1);
+          atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)i);
+        }
+      }
+      if (lane == 0) {
+        // the hand-off (slot state or queue entry) is ordered before the count
+        __threadfence();
+        atomicAdd(&ctrl->pbm_done, 1);
+        nxt = atomicAdd(&ctrl->next, 1);
+        onxt = nxt < total ? items[nxt] : 0;
+      }
+      __syncwarp();
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- search group
+  const int ns = blockDim.x - 32 * pbm_warps;   // search threads
+  const int st = tid - 32 * pbm_warps;          // index within the group
+  const bool fast = fast32_ok(N, M, p, a.lam);
+  const int rb = rank_bits(p);
+  for (int r = st; r < g.rows; r += ns) {
+    const int mvy = r - p;
+    const int am = mvy < 0 ? -mvy : mvy;
+    tabJ[r] = a.lam * (uint32_t)mv_bits(mvy);
+    tabK[r] = ((uint32_t)am << 17) + (uint32_t)r * (uint32_t)n;
+    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * am - (mvy < 0 ? 1 : 0));
+  }
+  const volatile int* vstate = s_state;
+  for (;;) {
+    if (st == 0) {
+      // next job: the oldest block (smallest claim index) in this CTA's full
+      // slots, else the head of the global queue, else wait (bounded) for
+      // either or for the end of the run.  (Serving an older global entry
+      // before a full local slot measured twice as slow: the slots stay
+      // taken, more blocks go to the queue and each costs a staging trip.)
+      int job = -1;
+      const long long t0 = clock64();
+      unsigned nsl = 32;
+      for (int it = 0;; it++) {
+        int best = -1, bseq = 0;
+        bool busy = false;
+        for (int s = 0; s < kSeq2Slots; s++) {
+          const int v = vstate[s];
+          busy |= v != 0;
+          if (v == 2) {
+            __threadfence_block();
+            const int sq = *reinterpret_cast<volatile int*>(&s_seq[s]);
+            if (best < 0 || sq < bseq) { best = s; bseq = sq; }
+          }
+        }
+        const int h = *reinterpret_cast<volatile int*>(&ctrl->fs_head);
+        const int tl = *reinterpret_cast<volatile int*>(&ctrl->fs_tail);
+        // this CTA's slots first (no staging); the global queue when they are empty
+        const bool take_global = best < 0 && h < tl && h < total;
+        if (!take_global && best >= 0) { job = best; break; }
+        if (take_global) {
+          if (atomicCAS(&ctrl->fs_head, h, h + 1) == h) {
+            // reserved entry h: its writer has already counted it in fs_tail
+            const volatile unsigned long long* rd = q + h;
+            int ci = -1;
+            for (;;) {
+              const unsigned long long e = *rd;
+              if (pub_epoch(e) == epoch) { ci = (int)(uint32_t)e; break; }
+              if (*reinterpret_cast<volatile int*>(&ctrl->error) != 0) break;
+              if (clock64() - t0 > timeout) {
+                atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+                break;
+              }
+              __nanosleep(32);
+            }
+            if (ci >= 0 && ci < total) {
+              s_blk[kSeq2Slots] = items[ci];
+              job = kSeq2Slots;
+            } else if (ci >= total) {
+              atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
+            }
+            break;
+          }
+          continue;
+        }
+        if (!busy && *reinterpret_cast<volatile int*>(&ctrl->pbm_done) == total &&
+            *reinterpret_cast<volatile int*>(&ctrl->fs_head) >=
+                *reinterpret_cast<volatile int*>(&ctrl->fs_tail))
+          break;   // every block through PBM, the queue drained, no slot of ours in use
+        if ((it & 7) == 7) {
+          if (*reinterpret_cast<volatile int*>(&ctrl->error) != 0) break;
+          if (clock64() - t0 > timeout) {
+            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+            break;
+          }
+        }
+        __nanosleep(nsl);
+        if (nsl < 256) nsl *= 2;
+      }
+      s_job = job;
+    }
+    seq2_bar(ns);
+    const int job = s_job;
+    if (job < 0) break;
+    const int o = s_blk[job];
+    const int k = o / nbf, b = o - k * nbf;
+    const int x0 = (b % BW) * N, y0 = (b / BW) * M;
+    uint32_t* raw = slots + job * wwords;
+    const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
+    if (job == kSeq2Slots) {
+      // a queued block: stage its window and current pixels as pbm_stage does
+      const uint8_t* cur = fr.f[k + 1];
+      for (int i = st; i < M * NW; i += ns) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + wwin + i);
+        const void* src = cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+      }
+      const uint8_t* base = refpad + (size_t)k * padsz + (size_t)(y0 + pg.P - p) * pg.pitch +
+                            ((x0 + pg.P - p) & ~15);
+      for (int i = st; i < wg.rows * wg.chunks; i += ns) {
+        const int r = i / wg.chunks, c = i - r * wg.chunks;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + r * wg.wp + 4 * c);
+        const void* src = base + (size_t)r * pg.pitch + 16 * c;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      seq2_bar(ns);
+    }
+    // shifted words: sh[r][o] = window bytes s0+o .. s0+o+3 of row r (rows
+    // past the window's last row only feed candidates beyond 2p: any row)
+    for (int i = st; i < g.rows * g.pos; i += ns) {
+      const int r = i / g.pos, oo = i - r * g.pos;
+      const int rr = r < wg.rows ? r : wg.rows - 1;
+      const int kk = wg.s0 + oo;
+      const uint32_t* row = raw + rr * wg.wp;
+      sh[r * g.sp + oo] = __funnelshift_r(row[kk >> 2], row[(kk >> 2) + 1], 8 * (kk & 3));
+    }
+    uint32_t c[M][NW];
+#pragma unroll
+    for (int j = 0; j < M; j++)
+#pragma unroll
+      for (int w = 0; w < NW; w++) c[j][w] = raw[wwin + j * NW + w];
+    seq2_bar(ns);
+    if (st == 0 && job < kSeq2Slots) atomicExch(&s_state[job], 0);   // slot read in full
+    unsigned long long best = kNoKey;
+    {
+      const int nc = g.nc;
+      int seg = st / nc, col = st - (st / nc) * nc;
+      const int dseg = ns / nc, dcol = ns - (ns / nc) * nc;
+      for (int t = st; t < g.tasks; t += ns) {
+        const int row0 = seg * T;
+        uint32_t acc[T];
+        fs_run_sads<N, M, T>(c, sh + row0 * g.sp + col, g.sp, acc);
+        best = umin64(best, fs_run_key<T>(acc, row0, col, p, n, a.lam, rb, fast, tabJ, tabK, tabQ));
+        seg += dseg;
+        col += dcol;
+        if (col >= nc) { col -= nc; seg++; }
+      }
+    }
+    best = warp_min64(best);
+    if (lane == 0 && best != kNoKey) atomicMin(&s_red, best);
+    seq2_bar(ns);
+    if (st == 0) {
+      const unsigned long long key = s_red;
+      s_red = kNoKey;
+      const Decoded d = decode_key(key, p, a.lam);
+      atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
+      int16_t* field = a.mv + (size_t)k * nbf * 2;
+      field[2 * b] = (int16_t)d.mvx;
+      field[2 * b + 1] = (int16_t)d.mvy;
+      a.J[o] = d.J;
+      a.mask[o] = 1;
+      if (a.sad) a.sad[o] = d.sad;
+      if (a.load) a.load[o] = (uint32_t)(n * n);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ plans
 
 struct SeqPlan {
-  int dev, W, H, N, M, p, K, T;
+  int dev, W, H, N, M, p, K;
   void* mem = nullptr;
   uint8_t* refpad = nullptr;
   uint32_t* intra = nullptr;
@@ -723,11 +1045,23 @@ struct SeqPlan {
   int* items = nullptr;                  // claim order -> block (pair * blocks + block)
   SeqCtrl* ctrl = nullptr;
   int total = 0;
-  size_t smem = 0;
-  int grid = 0;
   cudaEvent_t last = nullptr;   // end of the previous run (runs of one plan never overlap)
   bool ran = false;
   std::mutex mu;
+  // launch candidates (same scratch, same results): the autotuner times them
+  // on the plan's first call and keeps the fastest
+  struct Cand {
+    int ver;      // 1: k_acbm_seq (two CTA roles); 2: k_acbm_seq2 (one CTA per SM)
+    int T;        // run length of the full searches
+    int split;    // ver 1: every split-th SM hosts two search CTAs (0: none)
+    int pw;       // ver 1: PBM warps per PBM CTA; ver 2: PBM warps per CTA
+    size_t smem;
+    int grid;
+    std::string name;
+  };
+  std::vector<Cand> cands;
+  int model = 0;                // the cost model's candidate
+  int chosen = -1;              // -1: not tuned yet
 };
 
 static std::mutex g_seq_mu;
@@ -745,26 +1079,87 @@ static size_t seq_smem(int p) {
   return std::max(fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads)), pbm);
 }
 
+// Shared memory of k_acbm_seq2 with pw PBM warps.
+template <int N, int M, int T>
+static size_t seq2_smem(int p, int pw) {
+  const size_t wwords = (size_t)pbm_win_words(N, M, p) + M * (N / 4);
+  const FsGeom g = fs_geom<N, M, T>(p, 1, kSeq2Threads - 32 * pw);
+  return 4 * ((pw + kSeq2Slots + 1) * wwords + (size_t)g.rows * g.sp + 3 * (size_t)g.rows);
+}
+
 #define ME_SEQ_NMT(X)                                                                          \
   X(16, 16, 8) X(16, 16, 11) X(16, 16, 13) X(16, 16, 16) X(16, 8, 8) X(16, 4, 8) X(8, 16, 8)   \
   X(8, 8, 8) X(8, 4, 8) X(4, 16, 8) X(4, 8, 8) X(4, 4, 8)
 
-static int seq_T(int N, int M, int p) {
-  if (!(N == 16 && M == 16)) return 8;
-  // optional override of the run length (tile sweeps): ME_SEQ_T=8|11|13|16
+// Modelled cost of a run length: staged rows per column and the per-run
+// epilogue (16x16 has four instantiated run lengths, the other shapes one).
+static double seq_T_cost(int M, int p, int T) {
+  const int n = 2 * p + 1, nseg = (n + T - 1) / T;
+  return (double)(nseg * T + M - 1) * (1.0 + 4.0 / T);
+}
+
+// Run lengths worth timing: the model's best and those within 10 % of it
+// (model first).  ME_SEQ_T=8|11|13|16 fixes one (tile sweeps and tests).
+static std::vector<int> seq_Ts(int N, int M, int p) {
+  if (!(N == 16 && M == 16)) return {8};
   if (const char* e = std::getenv("ME_SEQ_T")) {
     const int t = std::atoi(e);
-    if (t == 8 || t == 11 || t == 13 || t == 16) return t;
+    if (t == 8 || t == 11 || t == 13 || t == 16) return {t};
   }
   static const int Ts[] = {8, 11, 13, 16};
   int bestT = 13;
   double best = 1e300;
-  for (int T : Ts) {
-    const int n = 2 * p + 1, nseg = (n + T - 1) / T;
-    const double waste = (double)(nseg * T + M - 1) * (1.0 + 4.0 / T);
-    if (waste < best * 0.999) { best = waste; bestT = T; }
+  for (int T : Ts)
+    if (seq_T_cost(M, p, T) < best * 0.999) { best = seq_T_cost(M, p, T); bestT = T; }
+  std::vector<int> out{bestT};
+  for (int T : Ts)
+    if (T != bestT && seq_T_cost(M, p, T) <= 1.10 * best) out.push_back(T);
+  return out;
+}
+
+// Adds the launch candidates of run length T to the plan: k_acbm_seq with
+// two search CTAs on every 3rd (the model), 2nd or 4th SM, and k_acbm_seq2
+// with 4 or 5 PBM warps per CTA when its shared memory allows (single-slice
+// searches only).
+template <int N, int M, int T>
+static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
+  const int p = pl->p;
+  int per_sm = 0;
+  const size_t sm1 = seq_smem<N, M, T>(p);
+  {
+    const int e = ensure_dynamic_smem((const void*)k_acbm_seq<N, M, T>, sm1);
+    if (e) return e;
   }
-  return bestT;
+  ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<N, M, T>, kSeqThreads,
+                                                        sm1));
+  // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
+  // the 8-row build at 85 registers measured 30 % slower.)
+  if (per_sm >= 2) {
+    static const int splits[] = {kSeqSearchEvery, 2, 4};
+    for (int sp : splits) {
+      if (pl->S > 1 && sp != kSeqSearchEvery) continue;
+      char nm[64];
+      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d", T, sp);
+      if (model_T && sp == kSeqSearchEvery) pl->model = (int)pl->cands.size();
+      pl->cands.push_back(SeqPlan::Cand{1, T, sp, seq_pbm_warps(N, M, p), sm1, 2 * nsm, nm});
+    }
+  }
+  if (pl->S == 1) {
+    for (int pw = 4; pw <= 5; pw++) {
+      const size_t sm2 = seq2_smem<N, M, T>(p, pw);
+      if (sm2 > 220 * 1024) continue;
+      const int e = ensure_dynamic_smem((const void*)k_acbm_seq2<N, M, T>, sm2);
+      if (e) return e;
+      int per2 = 0;
+      ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_acbm_seq2<N, M, T>,
+                                                            kSeq2Threads, sm2));
+      if (per2 < 1) continue;
+      char nm[64];
+      std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, sm2, nsm, nm});
+    }
+  }
+  return ME_OK;
 }
 
 static int build_seq_plan(SeqPlan* pl) {
@@ -790,7 +1185,6 @@ static int build_seq_plan(SeqPlan* pl) {
   const size_t o_intra = take(4 * (size_t)nbf * pl->K);
   const size_t o_flags = take(8 * (size_t)nbf * pl->K);
   // column slices per full search
-  pl->T = seq_T(N, M, pl->p);
   // One slice by default: splitting a block's full search over CTAs (S > 1,
   // merged by an atomic minimum) measured slower at 1080p p=32 (a slice of
   // half the columns took 7 us against 10 us for the whole search, and the
@@ -815,27 +1209,26 @@ static int build_seq_plan(SeqPlan* pl) {
   ME_CUDA(cudaMemcpy(pl->items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice));
   SeqCtrl c;
   std::memset(&c, 0, sizeof(c));
-  c.timeout_ns = 1000000000ll;
+  c.timeout_cycles = wait_cycles(1000000000ll);     // 1 s
   ME_CUDA(cudaMemcpy(pl->ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
-  int nsm = 0, per_sm = 0, st = ME_ERR_ARG;
-  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->dev));
-#define X(n_, m_, t_)                                                                          \
-  if (N == n_ && M == m_ && pl->T == t_) {                                                     \
-    pl->smem = seq_smem<n_, m_, t_>(pl->p);                                                    \
-    { const int e_ = ensure_dynamic_smem((const void*)k_acbm_seq<n_, m_, t_>, pl->smem);        \
-      if (e_) return e_; }                                                                     \
-    ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<n_, m_, t_>,     \
-                                                          kSeqThreads, pl->smem));             \
-    st = ME_OK;                                                                                \
+  int nsm = 1;
+  {
+    const int e = sm_count(&nsm);
+    if (e) return e;
   }
-  ME_SEQ_NMT(X)
+  const std::vector<int> Ts = seq_Ts(N, M, pl->p);
+  for (size_t ti = 0; ti < Ts.size(); ti++) {
+    int st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+    if (N == n_ && M == m_ && Ts[ti] == t_) st = seq_add_cands<n_, m_, t_>(pl, nsm, ti == 0);
+    ME_SEQ_NMT(X)
 #undef X
-  // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
-  // the 8-row build at 85 registers measured 30 % slower.)
-  if (per_sm < 2) st = ME_ERR_CUDA;
-  pl->grid = 2 * nsm;
+    if (st) return st;
+  }
+  if (pl->cands.empty()) return ME_ERR_CUDA;
+  if (pl->cands[pl->model].ver != 1) pl->model = 0;
   ME_CUDA(cudaEventCreateWithFlags(&pl->last, cudaEventDisableTiming));
-  return st;
+  return ME_OK;
 }
 
 static int get_seq_plan(int W, int H, int N, int M, int p, int K, SeqPlan** out) {
@@ -880,17 +1273,16 @@ int launch_fsbm_pipe(const uint8_t* const* frames, int K, int W, int H, int p, u
 }
 
 int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, int H, int p,
-                          uint32_t lam, const PipeOut& out, cudaStream_t s) {
+                          uint32_t lam, const PipeOut& out, cudaStream_t s, int T) {
   if (K < 1 || K > kSeqMax) return ME_ERR_ARG;
   if (mode == kPipeStats && (!out.smin || !out.sdev)) return ME_ERR_ARG;
   if (mode == kPipeVolume && !out.vol) return ME_ERR_ARG;
   SeqFrames fr;
   std::memset(&fr, 0, sizeof(fr));
   for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
-  const FsPlan pl = fs_plan(16, 16, p, W / 16);
-  int dev = 0, nsm = 0;
-  ME_CUDA(cudaGetDevice(&dev));
-  ME_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const FsPlan pl{T > 0 ? T : fs_plan(16, 16, p, W / 16).T, 0, 0, 0, 1};
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
   const int BW = W / 16, BH = H / 16;
   const int groups = K * BH * ((BW + kPipeBpc - 1) / kPipeBpc);
   const int pgrid = std::min(nsm, groups);
@@ -912,6 +1304,126 @@ int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, 
   return ME_ERR_ARG;
 }
 
+// ------------------------------------------------------------------ tuned full search
+// Full search of K pairs (frames[k] -> frames[k+1]) in one launch, with the
+// launch form chosen by the autotuner on the first call of each shape: the
+// pipelined kernel at each run length within 10 % of the model's best (16x16
+// blocks, windows within its compile-time pitch), and the per-group kernel
+// with the two or three plans of lowest modelled cost.
+struct FsTune {
+  int dev, W, H, N, M, p, K;
+  bool pipe;
+  struct Cand {
+    int pipeT;    // > 0: k_fsbm_pipe with this run length; 0: k_fsbm_seq with pl
+    FsPlan pl;
+    std::string name;
+  };
+  std::vector<Cand> cands;
+  int model = 0, chosen = -1;
+  std::mutex mu;
+};
+static std::mutex g_fst_mu;
+static std::vector<FsTune*> g_fst;
+
+static FsTune* fs_tune_entry(int dev, int W, int H, int N, int M, int p, int K) {
+  const bool pipe = fsbm_pipe_applies(N, M, p);
+  std::lock_guard<std::mutex> lk(g_fst_mu);
+  for (FsTune* t : g_fst)
+    if (t->dev == dev && t->W == W && t->H == H && t->N == N && t->M == M && t->p == p &&
+        t->K == K && t->pipe == pipe)
+      return t;
+  FsTune* t = new FsTune();
+  t->dev = dev; t->W = W; t->H = H; t->N = N; t->M = M; t->p = p; t->K = K; t->pipe = pipe;
+  char nm[64];
+  if (pipe) {
+    const int T0 = fs_plan(16, 16, p, W / 16).T;
+    static const int Ts[] = {8, 11, 13, 16};
+    std::snprintf(nm, sizeof(nm), "pipe T=%d", T0);
+    t->cands.push_back(FsTune::Cand{T0, FsPlan{T0, 0, 0, 0, 1}, nm});
+    for (int T : Ts)
+      if (T != T0 && seq_T_cost(16, p, T) <= 1.10 * seq_T_cost(16, p, T0)) {
+        std::snprintf(nm, sizeof(nm), "pipe T=%d", T);
+        t->cands.push_back(FsTune::Cand{T, FsPlan{T, 0, 0, 0, 1}, nm});
+      }
+  }
+  for (const FsPlan& pl : fs_plans_ranked(N, M, p, W / N, pipe ? 2 : 3)) {
+    std::snprintf(nm, sizeof(nm), "group T=%d G=%d thr=%d", pl.T, pl.G, pl.threads);
+    t->cands.push_back(FsTune::Cand{0, pl, nm});
+  }
+  g_fst.push_back(t);
+  return t;
+}
+
+static int fs_seq_enqueue(const FsTune::Cand& cd, const uint8_t* const* frames, int K, int W,
+                          int H, int N, int M, int p, uint32_t lam, int16_t* mv_out,
+                          uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  if (cd.pipeT > 0) {
+    PipeOut o;
+    std::memset(&o, 0, sizeof(o));
+    o.mv = mv_out;
+    o.J = J_out;
+    o.sad = sad_out;
+    return launch_fsbm_pipe_mode(kPipeKeys, frames, K, W, H, p, lam, o, s, cd.pipeT);
+  }
+  const FsPlan& pl = cd.pl;
+  SeqFrames fr;
+  std::memset(&fr, 0, sizeof(fr));
+  for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
+  const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
+  const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
+  // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 34
+  // at 8 blocks per CTA) uses the build with a compile-time row pitch
+  if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP) {
+    auto kern = k_fsbm_seq<16, 16, 13, kSeqSP>;
+    const size_t smem = fs_smem_bytes<16, 16, 13>(fs_geom<16, 16, 13>(p, bpc, pl.G, 0, 0, kSeqSP));
+    const int st = ensure_dynamic_smem((const void*)kern, smem);
+    if (st) return st;
+    kern<<<grid, pl.threads, smem, s>>>(fr, W, H, p, pl.G, lam, mv_out, J_out, sad_out);
+    ME_CUDA(cudaGetLastError());
+    return ME_OK;
+  }
+  int st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && pl.T == t_) {                                                      \
+    { const int e_ = ensure_dynamic_smem((const void*)k_fsbm_seq<n_, m_, t_>, pl.smem);         \
+      if (e_) return e_; }                                                                     \
+    k_fsbm_seq<n_, m_, t_><<<grid, pl.threads, pl.smem, s>>>(fr, W, H, p, pl.G, lam, mv_out,   \
+                                                            J_out, sad_out);                   \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+int fsbm_tuned(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+               uint32_t lam, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  FsTune* t = fs_tune_entry(dev, W, H, N, M, p, K);
+  std::lock_guard<std::mutex> lk(t->mu);
+  auto run = [&](int c) {
+    return fs_seq_enqueue(t->cands[c], frames, K, W, H, N, M, p, lam, mv_out, J_out, sad_out, s);
+  };
+  int c = tune_forced((int)t->cands.size());
+  if (c < 0) {
+    if (t->chosen < 0) {
+      char what[96];
+      std::snprintf(what, sizeof(what), "fsbm %dx%d %dx%d p=%d K=%d", W, H, N, M, p, K);
+      std::vector<std::string> names;
+      for (const FsTune::Cand& cd : t->cands) names.push_back(cd.name);
+      int ch = t->model;
+      const int st = tune_select(what, names, t->model, s, run, &ch);
+      if (st) return st;
+      t->chosen = ch;
+    }
+    c = t->chosen;
+  }
+  return run(c);
+}
+
 static int check_seq_frames(const uint8_t* const* frames, int K) {
   if (!frames || K < 1 || K > kSeqMax) return ME_ERR_ARG;
   for (int k = 0; k <= K; k++)
@@ -923,6 +1435,54 @@ static int check_seq_frames(const uint8_t* const* frames, int K) {
 
 using namespace me;
 
+// Enqueues one whole ACBM sequence run of plan candidate c on s: the run's
+// control reset, the padded references and Intra_SAD of all pairs, and the
+// persistent search kernel.  Called with the plan's lock held.
+static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a, cudaStream_t s) {
+  const int W = pl->W, H = pl->H, N = pl->N, M = pl->M, p = pl->p, K = pl->K;
+  const SeqPlan::Cand& cd = pl->cands[c];
+  const PadGeom pg = pad_geom(W, H, p);
+  if (pl->ran) ME_CUDA(cudaStreamWaitEvent(s, pl->last, 0));
+  k_seq_begin<<<1, 256, 0, s>>>(pl->ctrl);
+  ME_CUDA(cudaGetLastError());
+  const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16) * K,
+                                             32LL * (W / N) * (H / M) * K);
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
+  const int gp = (int)std::min<long long>((work + 255) / 256, nsm * 8LL);
+  int st = ME_ERR_ARG;
+#define X(n_, m_)                                                                              \
+  if (N == n_ && M == m_) {                                                                    \
+    k_seq_prologue<n_, m_><<<gp, 256, 0, s>>>(fr, K, pg, W, H, pl->refpad, pl->intra, pl->bkey, \
+                                               pl->bdone);                                     \
+    st = ME_OK;                                                                                \
+  }
+  X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && cd.T == t_) {                                                      \
+    if (cd.ver == 2)                                                                           \
+      k_acbm_seq2<n_, m_, t_><<<cd.grid, kSeq2Threads, cd.smem, s>>>(                          \
+          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total, pl->ctrl,\
+          pl->q, cd.pw);                                                                       \
+    else                                                                                       \
+      k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
+          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total,          \
+          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split);                       \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ_NMT(X)
+#undef X
+  if (st) return st;
+  ME_CUDA(cudaGetLastError());
+  ME_CUDA(cudaEventRecord(pl->last, s));
+  pl->ran = true;
+  return ME_OK;
+}
+
 extern "C" {
 
 int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
@@ -933,41 +1493,8 @@ int me_fsbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   if (!mv_out || !J_out) return ME_ERR_ARG;
   st = check_frame_args(W, H, N, M, p, lambda_q8);
   if (st) return st;
-  SeqFrames fr;
-  std::memset(&fr, 0, sizeof(fr));
-  for (int k = 0; k <= K; k++) fr.f[k] = frames[k];
-  FsPlan pl = fs_plan(N, M, p, W / N);
-  const int BW = W / N, BH = H / M, bpc = pl.threads / pl.G;
-  const dim3 grid(((BW + bpc - 1) / bpc) * BH, K);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (fsbm_pipe_applies(N, M, p)) {
-    return launch_fsbm_pipe(frames, K, W, H, p, lambda_q8, mv_out, J_out, sad_out, s);
-  }
-  // the 16x16 run length 13 with shifted rows of at most kSeqSP words (p <= 34
-  // at 8 blocks per CTA) uses the build with a compile-time row pitch
-  if (N == 16 && M == 16 && pl.T == 13 && (bpc - 1) * N + 2 * p + 1 + N - 4 <= kSeqSP) {
-    auto kern = k_fsbm_seq<16, 16, 13, kSeqSP>;
-    const size_t smem = fs_smem_bytes<16, 16, 13>(fs_geom<16, 16, 13>(p, bpc, pl.G, 0, 0, kSeqSP));
-    st = ensure_dynamic_smem((const void*)kern, smem);
-    if (st) return st;
-    kern<<<grid, pl.threads, smem, s>>>(fr, W, H, p, pl.G, lambda_q8, mv_out, J_out, sad_out);
-    ME_CUDA(cudaGetLastError());
-    return ME_OK;
-  }
-  st = ME_ERR_ARG;
-#define X(n_, m_, t_)                                                                          \
-  if (N == n_ && M == m_ && pl.T == t_) {                                                      \
-    { const int e_ = ensure_dynamic_smem((const void*)k_fsbm_seq<n_, m_, t_>, pl.smem);         \
-      if (e_) return e_; }                                                                     \
-    k_fsbm_seq<n_, m_, t_><<<grid, pl.threads, pl.smem, s>>>(fr, W, H, p, pl.G, lambda_q8,     \
-                                                            mv_out, J_out, sad_out);           \
-    st = ME_OK;                                                                                \
-  }
-  ME_SEQ_NMT(X)
-#undef X
-  if (st) return st;
-  ME_CUDA(cudaGetLastError());
-  return ME_OK;
+  return fsbm_tuned(frames, K, W, H, N, M, p, lambda_q8, mv_out, J_out, sad_out,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
@@ -993,42 +1520,25 @@ int me_acbm_sequence(const uint8_t* const* frames, int K, int W, int H, int N, i
   a.lam = lambda_q8;
   a.alpha = prm->alpha; a.beta = prm->beta; a.gnum = prm->gamma_num; a.gden = prm->gamma_den;
   a.qp = prm->qp; a.refine = prm->refine;
-  const PadGeom pg = pad_geom(W, H, p);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // runs that share a plan's scratch are ordered on the GPU, whatever their streams
   std::lock_guard<std::mutex> lk(pl->mu);
-  if (pl->ran) ME_CUDA(cudaStreamWaitEvent(s, pl->last, 0));
-  k_seq_begin<<<1, 256, 0, s>>>(pl->ctrl);
-  ME_CUDA(cudaGetLastError());
-  const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16) * K,
-                                             32LL * (W / N) * (H / M) * K);
-  const int gp = (int)std::min<long long>((work + 255) / 256, 152 * 8);
-  st = ME_ERR_ARG;
-#define X(n_, m_)                                                                              \
-  if (N == n_ && M == m_) {                                                                    \
-    k_seq_prologue<n_, m_><<<gp, 256, 0, s>>>(fr, K, pg, W, H, pl->refpad, pl->intra, pl->bkey, \
-                                               pl->bdone);                                     \
-    st = ME_OK;                                                                                \
+  auto run = [&](int c) { return seq_enqueue(pl, c, fr, a, s); };
+  int c = tune_forced((int)pl->cands.size());
+  if (c < 0) {
+    if (pl->chosen < 0) {
+      char what[96];
+      std::snprintf(what, sizeof(what), "acbm_sequence %dx%d %dx%d p=%d K=%d", W, H, N, M, p, K);
+      std::vector<std::string> names;
+      for (const SeqPlan::Cand& cd : pl->cands) names.push_back(cd.name);
+      int ch = pl->model;
+      st = tune_select(what, names, pl->model, s, run, &ch);
+      if (st) return st;
+      pl->chosen = ch;
+    }
+    c = pl->chosen;
   }
-  X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
-#undef X
-  if (st) return st;
-  ME_CUDA(cudaGetLastError());
-  st = ME_ERR_ARG;
-#define X(n_, m_, t_)                                                                          \
-  if (N == n_ && M == m_ && pl->T == t_) {                                                     \
-    k_acbm_seq<n_, m_, t_><<<pl->grid, kSeqThreads, pl->smem, s>>>(                            \
-        fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total, pl->ctrl,  \
-        pl->q, pl->bkey, pl->bdone, pl->S, seq_pbm_warps(N, M, p), pl->grid / 2);              \
-    st = ME_OK;                                                                                \
-  }
-  ME_SEQ_NMT(X)
-#undef X
-  if (st) return st;
-  ME_CUDA(cudaGetLastError());
-  ME_CUDA(cudaEventRecord(pl->last, s));
-  pl->ran = true;
-  return ME_OK;
+  return run(c);
 }
 
 int me_fsbm_sequence_status(me_stream_t stream) {

@@ -1,0 +1,141 @@
+"""The autotuner: every launch form it may pick gives the same bytes, and it
+picks by measurement.
+
+For each tuned entry point (me_fsbm_sequence / me_fsbm through the tuned
+full search, me_acbm_sequence) every candidate is forced in turn
+(ME_TUNE_FORCE) on a small case and compared with the oracle; the number of
+candidates comes from the tuner's own record, so a candidate list that grows
+is covered too."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def me():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_0710_4819_gb300 as me
+    me.load_library(build_if_missing=True)
+    return me
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _candidates(me, prefix):
+    """Candidate names of the tuner's line for a shape (prefix: 'fsbm 352x288 16x16 p=16 K=3')."""
+    for ln in me.me_tune_log().splitlines():
+        if ln.startswith(prefix + " "):
+            return [c.strip().rsplit(" ", 2)[0] for c in ln.split("|")[1:]]
+    return None
+
+
+def _line(me, prefix):
+    for ln in me.me_tune_log().splitlines():
+        if ln.startswith(prefix + " "):
+            return ln
+    return None
+
+
+class _Force:
+    def __init__(self, c):
+        self.c = c
+
+    def __enter__(self):
+        self.old = os.environ.get("ME_TUNE_FORCE")
+        os.environ["ME_TUNE_FORCE"] = str(self.c)
+
+    def __exit__(self, *a):
+        if self.old is None:
+            os.environ.pop("ME_TUNE_FORCE", None)
+        else:
+            os.environ["ME_TUNE_FORCE"] = self.old
+
+
+@pytest.mark.parametrize("w,h,N,M,p,K", [(352, 288, 16, 16, 16, 3), (208, 96, 8, 8, 7, 2),
+                                         (176, 144, 16, 8, 12, 1)])
+def test_every_fsbm_candidate_gives_the_oracle(me, orc, w, h, N, M, p, K):
+    import torch
+    seq = synth.scene_sequence(300 + w + N + p, w, h, K + 1, n_objects=4, vmax=5)
+    frames = torch.from_numpy(seq).cuda()
+    lam = orc.lambda_q8(28)
+    r = me.me_fsbm_sequence(frames, N, M, p, lam)          # the tuned first call
+    torch.cuda.synchronize()
+    prefix = f"fsbm {w}x{h} {N}x{M} p={p} K={K}"
+    names = _candidates(me, prefix)
+    assert names and len(names) >= 2, me.me_tune_log()
+    want = [orc.fsbm(seq[k + 1], seq[k], N, M, p, lam, nthreads=8) for k in range(K)]
+    for c in range(len(names)):
+        with _Force(c):
+            r = me.me_fsbm_sequence(frames, N, M, p, lam)
+            torch.cuda.synchronize()
+        assert me.me_fsbm_sequence_status() == 0
+        for k, (mv, J, sad) in enumerate(want):
+            assert np.array_equal(r.mv[k].cpu().numpy(), mv), (names[c], k)
+            assert np.array_equal(_u32(r.J[k]), J), (names[c], k)
+            assert np.array_equal(_u32(r.sad[k]), sad), (names[c], k)
+    if K == 1:
+        # the single-pair call goes through the same tuned forms
+        for c in range(len(names)):
+            with _Force(c):
+                f = me.me_fsbm(frames[1], frames[0], N, M, p, lam)
+                torch.cuda.synchronize()
+            assert np.array_equal(f.mv.cpu().numpy(), want[0][0]), names[c]
+            assert np.array_equal(_u32(f.J), want[0][1]), names[c]
+
+
+@pytest.mark.parametrize("name,N,M,p,K", [("cif", 16, 16, 16, 4), ("cif", 8, 8, 8, 3),
+                                          ("qcif", 16, 16, 32, 3)])
+def test_every_acbm_sequence_candidate_gives_the_chained_oracle(me, orc, name, N, M, p, K):
+    import torch
+    seq = synth.config_sequence(name, seed=71 + N + p, n_frames=K + 1)
+    H, W = seq.shape[1:]
+    frames = torch.from_numpy(seq).cuda()
+    lam = orc.lambda_q8(30)
+    prm = me.params(qp=30)
+    me.me_acbm_sequence(frames, N, M, p, lam, prm)        # the tuned first call
+    torch.cuda.synchronize()
+    prefix = f"acbm_sequence {W}x{H} {N}x{M} p={p} K={K}"
+    names = _candidates(me, prefix)
+    assert names and len(names) >= 2, me.me_tune_log()
+    want, prev = [], None
+    for k in range(K):
+        out = orc.acbm(seq[k + 1], seq[k], N, M, p, lam, orc.params(qp=30), prev)
+        prev = out[0]
+        want.append(out)
+    for c in range(len(names)):
+        with _Force(c):
+            r = me.me_acbm_sequence(frames, N, M, p, lam, prm)
+            torch.cuda.synchronize()
+        me.me_acbm_sequence_status(W, H, N, M, p, K)
+        for k, (mv, J, mask, sad, load) in enumerate(want):
+            for nm, g, w_ in (("mv", r.mv[k].cpu().numpy(), mv), ("J", _u32(r.J[k]), J),
+                              ("mask", r.mask[k].cpu().numpy(), mask), ("sad", _u32(r.sad[k]), sad),
+                              ("load", _u32(r.load[k]), load)):
+                assert np.array_equal(g, w_), (names[c], k, nm)
+
+
+def test_tuner_times_every_candidate_and_keeps_the_fastest(me):
+    import torch
+    seq = synth.config_sequence("cif", seed=5, n_frames=6)
+    frames = torch.from_numpy(seq).cuda()
+    lam = me.me_lambda_q8(28)
+    me.me_acbm_sequence(frames, 16, 16, 16, lam, me.params(qp=28))
+    me.me_fsbm_sequence(frames, 16, 16, 16, lam)
+    torch.cuda.synchronize()
+    for prefix in ("acbm_sequence 352x288 16x16 p=16 K=5", "fsbm 352x288 16x16 p=16 K=5"):
+        ln = _line(me, prefix)
+        assert ln is not None and " tuned:" in ln, me.me_tune_log()
+        chosen = re.search(r"chosen=(.+?) \|", ln).group(1)
+        times = {c.strip().rsplit(" ", 2)[0]: float(c.strip().rsplit(" ", 2)[1])
+                 for c in ln.split("|")[1:]}
+        assert all(t > 0 for t in times.values()), ln
+        assert times[chosen] == min(times.values()), ln

@@ -128,3 +128,13 @@ def test_argument_errors_before_launch(lib):
     assert lib.me_motion_study(frames, 2, 64, 64, 16, 16, 4, 0, fake, None, None, fake, fake,
                                None, None) == 1
     assert lib.me_status_string(2).decode().startswith("frame size")
+
+
+def test_tune_log_before_any_call(lib):
+    """No shape tuned yet in this process: the record is empty text (one NUL
+    byte needed), and a short buffer is truncated, not overrun."""
+    need = lib.me_tune_log(None, 0)
+    assert need >= 1
+    buf = ctypes.create_string_buffer(4)
+    got = lib.me_tune_log(buf, 4)
+    assert got == need and len(buf.value) <= 3

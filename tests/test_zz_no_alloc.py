@@ -38,8 +38,9 @@ def _run(lib, fn, cur, ref, N, M, p, lam, prm, prev):
     return mv, [t.cpu().numpy() for t in (mv, J, mask, sad, load)]
 
 
-@pytest.mark.parametrize("name,p,qp", [("cif", 16, 28), ("1080p", 32, 28)])
-def test_noalloc_matches_acbm_on_consecutive_calls(name, p, qp):
+@pytest.mark.parametrize("name,p,qp,N,M", [("cif", 16, 28, 16, 16), ("1080p", 32, 28, 16, 16),
+                                           ("1080p", 64, 28, 8, 8)])
+def test_noalloc_matches_acbm_on_consecutive_calls(name, p, qp, N, M):
     import torch
     import paper_0710_4819_gb300 as me
     lib = me.load_library(build_if_missing=True)
@@ -49,23 +50,26 @@ def test_noalloc_matches_acbm_on_consecutive_calls(name, p, qp):
     prm = me.params(qp=qp)
     prev_a = prev_n = None
     for t in (1, 2):          # two calls in a row, the second chained on the first
-        mv_a, want = _run(lib, "me_acbm", frames[t], frames[t - 1], 16, 16, p, lam, prm, prev_a)
-        mv_n, got = _run(lib, "me_acbm_noalloc", frames[t], frames[t - 1], 16, 16, p, lam, prm,
+        mv_a, want = _run(lib, "me_acbm", frames[t], frames[t - 1], N, M, p, lam, prm, prev_a)
+        mv_n, got = _run(lib, "me_acbm_noalloc", frames[t], frames[t - 1], N, M, p, lam, prm,
                          prev_n)
         for nm, g, w in zip(("mv", "J", "mask", "sad", "load"), got, want):
             assert np.array_equal(g, w), f"{name} t={t}: {nm} differs"
         prev_a, prev_n = mv_a, mv_n
 
 
-def test_noalloc_rejects_frames_beyond_its_array():
+@pytest.mark.parametrize("W,H,N,M,p", [(3840, 2160, 16, 16, 64), (1920, 1088, 4, 4, 16)])
+def test_noalloc_rejects_frames_beyond_its_array(W, H, N, M, p):
+    """2160p at 16x16 and 1080p at 4x4 blocks need more than the 4 MiB array
+    (9.3 and 4.6 MB): refused with ME_ERR_NOMEM, nothing enqueued."""
     import torch
     import paper_0710_4819_gb300 as me
     lib = me.load_library(build_if_missing=True)
-    x = torch.zeros((2160, 3840), dtype=torch.uint8, device="cuda")
-    out = torch.zeros((135, 240, 2), dtype=torch.int16, device="cuda")
+    x = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((H // M, W // N, 2), dtype=torch.int32, device="cuda")
     vp = ctypes.c_void_p
     prm = me.params(qp=28)
-    st = lib.me_acbm_noalloc(vp(x.data_ptr()), vp(x.data_ptr()), 3840, 2160, 16, 16, 64, 6595,
+    st = lib.me_acbm_noalloc(vp(x.data_ptr()), vp(x.data_ptr()), W, H, N, M, p, 6595,
                              None, ctypes.byref(prm), vp(out.data_ptr()), vp(out.data_ptr()),
                              vp(out.data_ptr()), None, None,
                              vp(torch.cuda.current_stream().cuda_stream))
