@@ -32,6 +32,11 @@ struct me_batch {
   std::vector<me::BShape> shapes;       // host copy (device pointers inside)
   std::vector<me::BSegment> segs;
   std::vector<me::BFsEntry> fsent;
+  std::vector<me::BFsEntry> fsent_tab;  // groups of the pipelined search (16x16 only)
+  // step forms the autotuner chooses among, per mode (0 FSBM, 1 ACBM)
+  std::vector<int> acbm_Ts;             // ACBM: run lengths
+  std::vector<size_t> acbm_smem;        //   and their shared memory
+  int form[2] = {-1, -1};               // chosen candidate, -1: not yet
   int total_items = 0, total_blocks = 0;
   long long total_pad = 0;
   size_t smem_fs = 0, smem_acbm = 0;
@@ -41,6 +46,7 @@ struct me_batch {
   me::BStream* d_streams = nullptr;
   me::BSegment* d_segs = nullptr;
   me::BFsEntry* d_fsent = nullptr;
+  me::BFsEntry* d_fsent_tab = nullptr;
   me::BCtrl* d_ctrl = nullptr;
   unsigned long long* d_items = nullptr;   // claim order of the ACBM step
   unsigned long long* d_q = nullptr;       // full-search queue of the ACBM step
@@ -86,21 +92,37 @@ static int persistent_grid(const void* fn, size_t smem, int* grid) {
   return ME_OK;
 }
 
+static double batch_T_waste(int N, int M, const std::vector<BShape>& shapes, int T) {
+  double waste = 0;
+  for (const BShape& s : shapes) {
+    const int n = 2 * s.p + 1, nseg = (n + T - 1) / T;
+    const double blocks = (double)(s.W / N) * (s.H / M);
+    waste += blocks * n * (nseg * T + M - 1) * (1.0 + 4.0 / T);
+  }
+  return waste;
+}
+
 int batch_choose_T(int N, int M, const std::vector<BShape>& shapes) {
   static const int kT16b[] = {8, 11, 13, 16};
   if (!(N == 16 && M == 16)) return 8;
   int bestT = 13;
   double best = 1e300;
   for (int T : kT16b) {
-    double waste = 0;
-    for (const BShape& s : shapes) {
-      const int n = 2 * s.p + 1, nseg = (n + T - 1) / T;
-      const double blocks = (double)(s.W / N) * (s.H / M);
-      waste += blocks * n * (nseg * T + M - 1) * (1.0 + 4.0 / T);
-    }
+    const double waste = batch_T_waste(N, M, shapes, T);
     if (waste < best * 0.999) { best = waste; bestT = T; }
   }
   return bestT;
+}
+
+std::vector<int> batch_Ts(int N, int M, const std::vector<BShape>& shapes) {
+  const int T0 = batch_choose_T(N, M, shapes);
+  std::vector<int> out{T0};
+  if (!(N == 16 && M == 16)) return out;
+  static const int kT16b[] = {8, 11, 13, 16};
+  const double w0 = batch_T_waste(N, M, shapes, T0);
+  for (int T : kT16b)
+    if (T != T0 && batch_T_waste(N, M, shapes, T) <= 1.10 * w0) out.push_back(T);
+  return out;
 }
 
 size_t acbm_step_smem(int N, int M, int T, int p_max) {
@@ -177,6 +199,13 @@ int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
   return ME_OK;
 }
 
+int launch_fsbm_tab_step(BCtrl* ctrl, int epoch, const BShape* shapes, const BStream* streams,
+                         const BFsEntry* ent, int nent, cudaStream_t s) {
+  k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
+  ME_CUDA(cudaGetLastError());
+  return launch_pipe_tab_batch(shapes, streams, ent, nent, &ctrl->next, &ctrl->error, s);
+}
+
 static int batch_finalize(me_batch* b) {
   b->T = batch_choose_T(b->N, b->M, b->shapes);
   // FSBM work entries: threads per block (and so blocks per CTA) per stream
@@ -198,6 +227,23 @@ static int batch_finalize(me_batch* b) {
     return (long long)px * px * x.nb > (long long)py * py * y.nb;
   });
   b->smem_fs = smem_fs;
+  // groups of the pipelined search, largest work first
+  b->fsent_tab.clear();
+  if (b->N == 16 && b->M == 16 && pipe_tab_applies(16, 16, 1)) {
+    for (int si = 0; si < (int)b->shapes.size(); si++) {
+      const BShape& s = b->shapes[si];
+      const int BW = s.W / 16, BH = s.H / 16, bpc = pipe_tab_bpc(s.p);
+      for (int by = 0; by < BH; by++)
+        for (int bx0 = 0; bx0 < BW; bx0 += bpc)
+          b->fsent_tab.push_back(BFsEntry{si, by, bx0, std::min(bpc, BW - bx0), 0});
+    }
+    std::stable_sort(b->fsent_tab.begin(), b->fsent_tab.end(),
+                     [&](const BFsEntry& x, const BFsEntry& y) {
+                       const long long nx = 2 * b->shapes[x.stream].p + 1;
+                       const long long ny = 2 * b->shapes[y.stream].p + 1;
+                       return nx * nx * x.nb > ny * ny * y.nb;
+                     });
+  }
   // ACBM segments: wave-major across streams
   b->segs.clear();
   int maxw = 0;
@@ -218,6 +264,9 @@ static int batch_finalize(me_batch* b) {
   b->p_max = 1;
   for (const BShape& s : b->shapes) b->p_max = std::max(b->p_max, s.p);
   b->smem_acbm = acbm_step_smem(b->N, b->M, b->T, b->p_max);
+  b->acbm_Ts = batch_Ts(b->N, b->M, b->shapes);
+  b->acbm_smem.clear();
+  for (int T : b->acbm_Ts) b->acbm_smem.push_back(acbm_step_smem(b->N, b->M, T, b->p_max));
   // device memory: control, tables, per-stream scratch
   const size_t n = b->shapes.size();
   size_t off = 0;
@@ -227,6 +276,7 @@ static int batch_finalize(me_batch* b) {
   const size_t o_streams = take(sizeof(BStream) * n);
   const size_t o_segs = take(sizeof(BSegment) * b->segs.size());
   const size_t o_fsent = take(sizeof(BFsEntry) * b->fsent.size());
+  const size_t o_fsent_tab = take(sizeof(BFsEntry) * std::max<size_t>(1, b->fsent_tab.size()));
   const size_t o_items = take(8 * (size_t)std::max(1, b->total_items));
   const size_t o_q = take(8 * (size_t)std::max(1, b->total_items));
   std::vector<size_t> o_pad(n), o_intra(n), o_flags(n);
@@ -256,6 +306,7 @@ static int batch_finalize(me_batch* b) {
   b->d_streams = reinterpret_cast<BStream*>(base8 + o_streams);
   b->d_segs = reinterpret_cast<BSegment*>(base8 + o_segs);
   b->d_fsent = reinterpret_cast<BFsEntry*>(base8 + o_fsent);
+  b->d_fsent_tab = reinterpret_cast<BFsEntry*>(base8 + o_fsent_tab);
   b->d_items = reinterpret_cast<unsigned long long*>(base8 + o_items);
   b->d_q = reinterpret_cast<unsigned long long*>(base8 + o_q);
   ME_CUDA(cudaMemcpy(b->d_shapes, b->shapes.data(), sizeof(BShape) * n, cudaMemcpyHostToDevice));
@@ -265,6 +316,9 @@ static int batch_finalize(me_batch* b) {
   if (!b->fsent.empty())
     ME_CUDA(cudaMemcpy(b->d_fsent, b->fsent.data(), sizeof(BFsEntry) * b->fsent.size(),
                        cudaMemcpyHostToDevice));
+  if (!b->fsent_tab.empty())
+    ME_CUDA(cudaMemcpy(b->d_fsent_tab, b->fsent_tab.data(),
+                       sizeof(BFsEntry) * b->fsent_tab.size(), cudaMemcpyHostToDevice));
   BCtrl c;
   std::memset(&c, 0, sizeof(c));
   c.timeout_ns = b->timeout_ns;
@@ -281,24 +335,52 @@ static int batch_finalize(me_batch* b) {
   // size the persistent grids now, outside any capture
   int st = ME_ERR_ARG, grid = 0;
 #define X(n_, m_, t_)                                                                          \
-  if (b->N == n_ && b->M == m_ && b->T == t_) {                                                \
-    st = persistent_grid((const void*)k_fsbm_persist<n_, m_, t_>, b->smem_fs, &grid);          \
-    if (st == ME_OK)                                                                           \
-      st = persistent_grid((const void*)k_acbm_persist<n_, m_, t_>, b->smem_acbm, &grid);      \
-  }
+  if (b->N == n_ && b->M == m_ && b->T == t_)                                                  \
+    st = persistent_grid((const void*)k_fsbm_persist<n_, m_, t_>, b->smem_fs, &grid);
   ME_BATCH_NMT(X)
 #undef X
+  for (size_t i = 0; i < b->acbm_Ts.size() && st == ME_OK; i++) {
+    st = ME_ERR_ARG;
+#define X(n_, m_, t_)                                                                          \
+    if (b->N == n_ && b->M == m_ && b->acbm_Ts[i] == t_)                                       \
+      st = persistent_grid((const void*)k_acbm_persist<n_, m_, t_>, b->acbm_smem[i], &grid);
+    ME_BATCH_NMT(X)
+#undef X
+  }
   return st;
 }
 
-// Enqueues one step of `mode` (no argument staging).
-static int batch_enqueue(me_batch* b, int mode, cudaStream_t s) {
-  if (mode == ME_MODE_FSBM)
+// Candidate step forms of a mode: FSBM -- the per-group persistent kernel at
+// the model's run length, then (16x16) the pipelined search; ACBM -- the
+// persistent kernel at each run length of acbm_Ts.
+static std::vector<std::string> batch_forms(const me_batch* b, int mode) {
+  std::vector<std::string> names;
+  char nm[64];
+  if (mode == ME_MODE_FSBM) {
+    std::snprintf(nm, sizeof(nm), "persist T=%d", b->T);
+    names.push_back(nm);
+    if (!b->fsent_tab.empty()) names.push_back("pipetab");
+  } else {
+    for (int T : b->acbm_Ts) {
+      std::snprintf(nm, sizeof(nm), "persist T=%d", T);
+      names.push_back(nm);
+    }
+  }
+  return names;
+}
+
+// Enqueues one step of `mode` in candidate form c (no argument staging).
+static int batch_enqueue(me_batch* b, int mode, int c, cudaStream_t s) {
+  if (mode == ME_MODE_FSBM) {
+    if (c == 1)
+      return launch_fsbm_tab_step(b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent_tab,
+                                  (int)b->fsent_tab.size(), s);
     return launch_fsbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent,
                             (int)b->fsent.size(), b->smem_fs, s);
-  return launch_acbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams,
+  }
+  return launch_acbm_step(b->N, b->M, b->acbm_Ts[c], b->d_ctrl, 0, b->d_shapes, b->d_streams,
                           (int)b->shapes.size(), b->total_pad, b->total_blocks, b->d_segs,
-                          (int)b->segs.size(), b->total_items, b->smem_acbm, b->p_max,
+                          (int)b->segs.size(), b->total_items, b->acbm_smem[c], b->p_max,
                           b->d_items, b->d_q, s);
 }
 
@@ -374,11 +456,22 @@ int me_batch_run(me_batch* b, int mode, const me_batch_item* items, int n_items,
   ME_CUDA(cudaEventRecord(b->staged[slot], s));
   const int gi = mode == ME_MODE_ACBM ? 1 : 0;
   if (!b->exec[gi]) {
+    // the step's form: forced (tests), else timed on this step's inputs
+    const std::vector<std::string> names = batch_forms(b, mode);
+    int c = tune_forced((int)names.size());
+    if (c < 0) {
+      char what[64];
+      std::snprintf(what, sizeof(what), "batch %s %d streams", mode == ME_MODE_FSBM ? "fsbm" : "acbm",
+                    (int)b->shapes.size());
+      int st = tune_select(what, names, 0, s, [&](int k) { return batch_enqueue(b, mode, k, s); }, &c);
+      if (st) return st;
+    }
+    b->form[gi] = c;
     // capture the step once on a private stream, then replay it
     cudaStream_t cs;
     ME_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     ME_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int st = batch_enqueue(b, mode, cs);
+    int st = batch_enqueue(b, mode, c, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);

@@ -9,40 +9,14 @@
 #include "me_device.cuh"
 #include "me_host.h"
 #include "me_search.cuh"
+#include "me_batch_types.h"
 
 namespace me {
 
 constexpr int kBatchThreads = 256;
 
-struct BStream {  // per-run arguments of one stream (copied to the device each run)
-  const uint8_t* cur;
-  const uint8_t* ref;
-  const int16_t* prev;
-  int16_t* mv;
-  uint32_t* J;
-  uint8_t* mask;
-  uint32_t* sad;
-  uint32_t* load;
-  uint32_t lam;
-  int32_t alpha, beta, gnum, gden, qp, refine;
-};
-
-struct BShape {  // fixed per stream
-  int W, H, p;
-  PadGeom pg;
-  uint8_t* refpad;
-  uint32_t* intra;
-  unsigned long long* flags;  // per block: epoch + final vector (pub_word)
-  long long pad_base;  // first 16-byte chunk of this stream in the flat pad index
-  int blk_base;        // first block of this stream in the flat block index
-};
-
 struct BSegment {  // ACBM: the blocks of one wave of one stream
   int stream, wave, ylo, count, item_base;
-};
-
-struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block
-  int stream, by, bx0, nb, G;
 };
 
 // Control block of a step.  Counters that many warps update or poll each sit
@@ -421,5 +395,15 @@ size_t acbm_step_smem(int N, int M, int T, int p_max);
 int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, const BFsEntry* ent, int nent, size_t smem,
                      cudaStream_t s);
+
+// Enqueues one FSBM step of 16x16 streams through the pipelined search at
+// any p (begin kernel + k_fsbm_pipe_tab over the group table `ent`, groups of
+// at most pipe_tab_bpc(p) blocks, claimed from ctrl->next).
+int launch_fsbm_tab_step(BCtrl* ctrl, int epoch, const BShape* shapes, const BStream* streams,
+                         const BFsEntry* ent, int nent, cudaStream_t s);
+
+// Run lengths worth timing for a set of streams: batch_choose_T's and those
+// whose modelled waste is within 10 % of it (model first).
+std::vector<int> batch_Ts(int N, int M, const std::vector<BShape>& shapes);
 
 }  // namespace me

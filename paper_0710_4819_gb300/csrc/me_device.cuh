@@ -133,6 +133,36 @@ __host__ __device__ inline bool fast32_ok(int N, int M, int p, uint32_t lam) {
   return ((jmax << rb) | ((1ull << rb) - 1)) < (1ull << 32);
 }
 
+// Bits that hold |mvy| <= p.
+__host__ __device__ inline int abs_bits(int p) {
+  int b = 0;
+  while ((1 << b) <= p) b++;
+  return b;
+}
+
+// How the runs are reduced to their best key:
+//   1: 32-bit minima of (J_q8 << rank_bits) + rank for every run (fast32_ok);
+//   2: 32-bit minima of (J_q8 << abs_bits) + |mvy| for the runs whose
+//      candidates lie on one side of mvy = 0 (within such a run the tie
+//      order is by |mvy| alone), 64-bit keys for the one run per column that
+//      holds both signs -- when the |mvy| form fits 32 bits (large p);
+//   0: 64-bit keys for every run.
+__host__ __device__ inline int key_mode(int N, int M, int p, uint32_t lam) {
+  if (fast32_ok(N, M, p, lam)) return 1;
+  const unsigned long long jmax =
+      256ull * 255ull * (unsigned long long)(N * M) + (unsigned long long)lam * (2ull * mv_bits(p));
+  const int ab = abs_bits(p);
+  return ((jmax << ab) | ((1ull << ab) - 1)) < (1ull << 32) ? 2 : 0;
+}
+
+// Per-row entry of the 32-bit run key table for key mode `mode` (tabJ =
+// lambda * L(mvy) of the row).
+__host__ __device__ inline uint32_t tabq_value(int mode, uint32_t tabJ, int mvy, int p) {
+  const int a = mvy < 0 ? -mvy : mvy;
+  if (mode == 2) return (tabJ << abs_bits(p)) + (uint32_t)a;
+  return (tabJ << rank_bits(p)) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
+}
+
 // Geometry of a search over columns c0 .. c0+nc-1 of the (2p+1)-wide window
 // (nc = 0: all columns); a slice lets several CTAs share one block's search.
 // sp_min > 0 widens the shifted-word rows to a fixed pitch (a kernel compiled
@@ -200,28 +230,31 @@ __device__ __forceinline__ void fs_run_sads(const uint32_t (&c)[M][N / 4], const
 }
 
 // The best key of one run (candidates row0 .. row0+T-1 of window column wcol,
-// those past row n-1 skipped).  fast: J_q8 << rb plus the in-run rank fits
-// 32 bits (fast32_ok), so the run is reduced with 32-bit minima using tabQ;
-// else 64-bit keys from tabJ / tabK.
+// those past row n-1 skipped), reduced as key mode `mode` says (key_mode):
+// 32-bit minima using tabQ where the mode allows it for this run, else
+// 64-bit keys from tabJ / tabK.
 template <int T>
 __device__ __forceinline__ unsigned long long fs_run_key(const uint32_t (&acc)[T], int row0, int wcol,
-                                                         int p, int n, uint32_t lam, int rb, bool fast,
+                                                         int p, int n, uint32_t lam, int rb, int mode,
                                                          const uint32_t* tabJ, const uint32_t* tabK,
                                                          const uint32_t* tabQ) {
   const int mvx = wcol - p;
   const uint32_t amx = (uint32_t)(mvx < 0 ? -mvx : mvx);
   const uint32_t jx = lam * (uint32_t)mv_bits(mvx);
   unsigned long long best = kNoKey;
-  if (fast) {
-    // 32-bit run minimum of (J << rb) + rank; the mvx part of J is the same
-    // for the whole run and is added after the minimum
+  // mode 2 applies to runs on one side of mvy = 0
+  const bool one_side = row0 >= p || row0 + T - 1 <= p;
+  if (mode == 1 || (mode == 2 && one_side)) {
+    // 32-bit run minimum of (J << sb) + tie bits; the mvx part of J is the
+    // same for the whole run and is added after the minimum
+    const int sb = mode == 1 ? rb : 32 - __clz(p);
     uint32_t m = 0xffffffffu;
     if (row0 + T <= n) {
       // a whole run inside the window: no per-candidate bounds, and a tree
       // of three-input minima
       uint32_t v[T];
 #pragma unroll
-      for (int k = 0; k < T; k++) v[k] = acc[k] * (256u << rb) + tabQ[row0 + k];
+      for (int k = 0; k < T; k++) v[k] = acc[k] * (256u << sb) + tabQ[row0 + k];
       m = v[0];
 #pragma unroll
       for (int k = 1; k + 1 < T; k += 2) m = __vimin3_u32(m, v[k], v[k + 1]);
@@ -230,12 +263,16 @@ __device__ __forceinline__ unsigned long long fs_run_key(const uint32_t (&acc)[T
 #pragma unroll
       for (int k = 0; k < T; k++) {
         const int r = row0 + k;
-        if (r < n) m = min(m, acc[k] * (256u << rb) + tabQ[r]);
+        if (r < n) m = min(m, acc[k] * (256u << sb) + tabQ[r]);
       }
     }
-    m += jx << rb;
-    const uint32_t J = m >> rb, rk = m & ((1u << rb) - 1u);
-    const int mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
+    m += jx << sb;
+    const uint32_t J = m >> sb, rk = m & ((1u << sb) - 1u);
+    int mvy;
+    if (mode == 1)
+      mvy = (rk & 1u) ? -(int)((rk + 1u) >> 1) : (int)(rk >> 1);
+    else
+      mvy = row0 >= p ? (int)rk : -(int)rk;
     const uint32_t lo = ((amx + (uint32_t)(mvy < 0 ? -mvy : mvy)) << 17) +
                         (uint32_t)(mvy + p) * (uint32_t)n + (uint32_t)wcol;
     best = ((unsigned long long)J << 32) | lo;
@@ -293,7 +330,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
   uint32_t* tabQ = tabK + g.rows;                          // [rows] 32-bit run key of mvy
   unsigned long long* red = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(tabQ + g.rows) + 7) & ~uintptr_t(7));
-  const bool fast = fast32_ok(N, M, p, lam);
+  const int fast = key_mode(N, M, p, lam);
   const int rb = rank_bits(p);
 
   if (tid < g.bpc) red[tid] = kNoKey;
@@ -370,7 +407,7 @@ __device__ void fs_group(const uint8_t* __restrict__ cur, const uint8_t* __restr
     const int a = mvy < 0 ? -mvy : mvy;
     tabJ[r] = lam * (uint32_t)mv_bits(mvy);
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
-    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
+    tabQ[r] = tabq_value(fast, tabJ[r], mvy, p);
   }
   if (pad.base) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();

@@ -25,6 +25,7 @@
 #include "me_device.cuh"
 #include "me_host.h"
 #include "me_search.cuh"
+#include "me_batch_types.h"
 
 namespace me {
 
@@ -198,14 +199,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
   // buffer b: current blocks [B][M][NW], then shifted words [rows][SP]
   const int bstride = B * M * NW + g.rows * SP;
   uint32_t* const buf0 = raw + g.rows * g.wbw;
-  const bool fast = fast32_ok(N, M, p, lam);
+  const int fast = key_mode(N, M, p, lam);
   const int rb = rank_bits(p);
   for (int r = tid; r < g.rows; r += kPipeThreads) {
     const int mvy = r - p;
     const int a = mvy < 0 ? -mvy : mvy;
     tabJ[r] = lam * (uint32_t)mv_bits(mvy);
     tabK[r] = ((uint32_t)a << 17) + (uint32_t)r * (uint32_t)n;
-    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * a - (mvy < 0 ? 1 : 0));
+    tabQ[r] = tabq_value(fast, tabJ[r], mvy, p);
   }
   if (tid < 2 * B) {
     red[tid / B][tid % B] = kNoKey;
@@ -400,6 +401,310 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
       col += dcol;
       if (col >= nc) { col -= nc; seg++; }
       while (seg >= g.nseg) { seg -= g.nseg; blk++; }
+    }
+    mbar_arrive(&empty_bar[b]);
+  }
+}
+
+// ------------------------------------------------------------------ pipelined search, any p
+//
+// The pipelined full search for 16x16 blocks at every search range p <= 64,
+// driven by a table of block groups: the same producer/consumer pipeline as
+// k_fsbm_pipe (4 producer warps stage a group into one of two shared buffers
+// while 12 consumer warps search the other), with a fixed shifted-word pitch
+// of kTabSP = 157 words and buffers of kTabRows = 145 rows, enough for a
+// group of tab_bpc(p) blocks (8 at p <= 16, 6 at p <= 32, 4 at p <= 48, 2 at
+// p <= 64) with the 13-row runs.  Groups come from one of two sources:
+//   - a sequence of K pairs (frames[k] -> frames[k+1]) of one shape, groups
+//     dealt to CTAs round robin;
+//   - a batch of streams of any sizes and ranges (the batch API's stream and
+//     group tables), groups claimed from a counter, largest work first.
+// The tables of costs per row depend on p and lambda, so the producers stage
+// them with each group.
+constexpr int kTabSP = 157;
+constexpr int kTabRows = 145;   // 10 runs of 13 rows + 15
+constexpr int kTabB = 8;
+constexpr int kTabT = 13;
+
+__host__ __device__ inline int tab_bpc(int p) {
+  const int b = (kTabSP - (2 * p + 1) - 12) / 16 + 1;
+  return b < kTabB ? b : kTabB;
+}
+
+struct TabArgs {
+  // sequence source (shp == nullptr)
+  SeqFrames fr;
+  int W, H, p, K;
+  uint32_t lam;
+  int16_t* mv;
+  uint32_t* J;
+  uint32_t* sad;
+  // batch source
+  const BShape* shp;
+  const BStream* st;
+  const BFsEntry* ent;
+  int ngroups;
+  int* ctr;         // group claims (batch); null: round robin
+  int* err;         // the caller's error word; null: g_fsbm_pipe_error
+  long long lim;    // bound of every wait, SM cycles
+};
+
+struct TabGroup {
+  const uint8_t* cur;
+  const uint8_t* ref;
+  int16_t* mv;
+  uint32_t* J;
+  uint32_t* sad;
+  int W, H, p, x0, y0, nb;
+  long long obase;  // output index of the group's first block
+  uint32_t lam;
+};
+
+__device__ __forceinline__ TabGroup tab_group(const TabArgs& A, int gi) {
+  TabGroup G;
+  if (A.shp == nullptr) {
+    const int BW = A.W / 16, BH = A.H / 16, bpc = tab_bpc(A.p);
+    const int gpr = (BW + bpc - 1) / bpc;
+    const int k = gi / (BH * gpr), rem = gi - k * (BH * gpr);
+    const int by = rem / gpr, bx0 = (rem - by * gpr) * bpc;
+    G.cur = A.fr.f[k + 1];
+    G.ref = A.fr.f[k];
+    G.mv = A.mv;
+    G.J = A.J;
+    G.sad = A.sad;
+    G.W = A.W;
+    G.H = A.H;
+    G.p = A.p;
+    G.lam = A.lam;
+    G.x0 = bx0 * 16;
+    G.y0 = by * 16;
+    G.nb = min(bpc, BW - bx0);
+    G.obase = (long long)k * BW * BH + (long long)by * BW + bx0;
+  } else {
+    const BFsEntry e = A.ent[gi];
+    const BShape& s = A.shp[e.stream];
+    const BStream& a = A.st[e.stream];
+    G.cur = a.cur;
+    G.ref = a.ref;
+    G.mv = a.mv;
+    G.J = a.J;
+    G.sad = a.sad;
+    G.W = s.W;
+    G.H = s.H;
+    G.p = s.p;
+    G.lam = a.lam;
+    G.x0 = e.bx0 * 16;
+    G.y0 = e.by * 16;
+    G.nb = e.nb;
+    G.obase = (long long)e.by * (s.W / 16) + e.bx0;
+  }
+  return G;
+}
+
+template <int T>
+__host__ __device__ inline int tab_rows(int p) {
+  return ((2 * p + 1 + T - 1) / T) * T + 15;
+}
+
+__host__ __device__ inline size_t tab_smem_bytes() {
+  constexpr int WBW = (kTabSP + 6) / 4 + 1;
+  return 4 * ((size_t)kTabRows * WBW + 2 * ((size_t)kTabB * 64 + 3 * kTabRows + (size_t)kTabRows * kTabSP));
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
+  constexpr int N = 16, M = 16, NW = 4, T = kTabT, SP = kTabSP, R = kTabRows, B = kTabB;
+  constexpr int WBW = (SP + 6) / 4 + 1;
+  constexpr int PT = 32 * kPipeProducers, CT = 32 * kPipeConsumers;
+  constexpr int BST = B * M * NW + 3 * R + R * SP;   // words per buffer
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long red[2][B];
+  __shared__ TabGroup grp[2];
+  __shared__ int gid_s[2];
+  __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
+  __shared__ int err_s, go_s, claim_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
+  uint32_t* raw = smem;                       // [R][WBW], producers only
+  uint32_t* const buf0 = raw + R * WBW;       // buffer b: cur [B][M][NW], tabJ/K/Q [R], sh [R][SP]
+  int* const errw = A.err ? A.err : &g_fsbm_pipe_error;
+  if (tid < 2 * B) red[tid / B][tid % B] = kNoKey;
+  if (tid == 0) {
+    err_s = 0;
+    mbar_init(&full_bar[0], PT);
+    mbar_init(&full_bar[1], PT);
+    mbar_init(&empty_bar[0], CT);
+    mbar_init(&empty_bar[1], CT);
+  }
+  __syncthreads();
+
+  if (warp < kPipeProducers) {
+    const int pt = tid;
+    auto finish = [&](int j) {
+      const int b = j & 1;
+      if (pt == 0) {
+        const bool w = mbar_wait(&empty_bar[b], (unsigned)((j >> 1) & 1), &err_s, A.lim);
+        if (!w) atomicExch(errw, (int)ME_ERR_TIMEOUT);
+        go_s = w ? 1 : 0;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      const bool go = go_s != 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      if (!go) return false;
+      if (pt < B) {
+        const TabGroup& G = grp[b];
+        if (pt < G.nb) {
+          const Decoded d = decode_key(red[b][pt], G.p, G.lam);
+          const long long o = G.obase + pt;
+          if (G.mv) {
+            G.mv[2 * o] = (int16_t)d.mvx;
+            G.mv[2 * o + 1] = (int16_t)d.mvy;
+          }
+          if (G.J) G.J[o] = d.J;
+          if (G.sad) G.sad[o] = d.sad;
+        }
+        red[b][pt] = kNoKey;
+      }
+      // grp[b] is rewritten by the next group staged into buffer b
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      return true;
+    };
+    bool ok = true;
+    int i = 0;
+    for (;; i++) {
+      const int b = i & 1;
+      if (pt == 0) claim_s = A.ctr ? atomicAdd(A.ctr, 1) : (int)blockIdx.x + i * (int)gridDim.x;
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      const int gi = claim_s;
+      if (i >= 2 && !finish(i - 2)) { ok = false; break; }   // (its barriers order claim_s)
+      if (gi >= A.ngroups) break;
+      const TabGroup G = tab_group(A, gi);
+      if (pt == 0) {
+        grp[b] = G;
+        gid_s[b] = gi;
+      }
+      const int p = G.p, n = 2 * p + 1, rows = tab_rows<T>(p);
+      const int pos = (G.nb - 1) * N + n + N - 4;
+      uint32_t* cw = buf0 + b * BST;
+      uint32_t* tabJ = cw + B * M * NW;
+      uint32_t* tabK = tabJ + R;
+      uint32_t* tabQ = tabK + R;
+      uint32_t* sh = tabQ + R;
+      for (int e = pt; e < G.nb * M * NW; e += PT) {
+        const int blk = e / (M * NW), rm = e % (M * NW), j = rm / NW, w = rm % NW;
+        cw[e] = *reinterpret_cast<const uint32_t*>(G.cur + (size_t)(G.y0 + j) * G.W + G.x0 + blk * N +
+                                                  4 * w);
+      }
+      const int kmode = key_mode(N, M, p, G.lam);
+      for (int r = pt; r < rows; r += PT) {
+        const int mvy = r - p;
+        const int am = mvy < 0 ? -mvy : mvy;
+        tabJ[r] = G.lam * (uint32_t)mv_bits(mvy);
+        tabK[r] = ((uint32_t)am << 17) + (uint32_t)r * (uint32_t)n;
+        tabQ[r] = tabq_value(kmode, tabJ[r], mvy, p);
+      }
+      // raw window rows from the aligned word at or left of column x0 - p
+      const int wbw = (pos + 6) / 4 + 1;
+      const int wx0 = G.x0 - p;
+      const int A0 = (wx0 >> 2) << 2;
+      const int s0 = wx0 - A0;
+      const bool inside = A0 >= 0 && A0 + 4 * wbw <= G.W;
+      for (int r = warp; r < rows; r += kPipeProducers) {
+        const size_t yrow = (size_t)clampi(G.y0 - p + r, 0, G.H - 1) * G.W;
+        uint32_t* dst = raw + r * WBW;
+        for (int q = lane; q < wbw; q += 32) {
+          if (inside) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(G.ref + yrow + A0 + 4 * q)
+                         : "memory");
+          } else {
+            uint32_t v = 0;
+#pragma unroll
+            for (int bb = 0; bb < 4; bb++)
+              v |= (uint32_t)G.ref[yrow + clampi(A0 + 4 * q + bb, 0, G.W - 1)] << (8 * bb);
+            dst[q] = v;
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      // shifted words: sh[r][o] = raw bytes s0+o .. s0+o+3, four per lane
+      const int quads = (pos + 3) >> 2;
+      for (int r = warp; r < rows; r += kPipeProducers) {
+        for (int qd = lane; qd < quads; qd += 32) {
+          const int o = 4 * qd;
+          const uint32_t* row = raw + r * WBW + ((s0 + o) >> 2);
+          const uint32_t w0 = row[0], w1 = row[1], w2 = row[2];
+          const int t0 = (s0 + o) & 3;
+          uint32_t* dst = sh + r * SP + o;
+#pragma unroll
+          for (int d = 0; d < 4; d++) {
+            const int t = t0 + d;
+            if (o + d < pos)
+              dst[d] = t < 4 ? __funnelshift_r(w0, w1, 8 * t) : __funnelshift_r(w1, w2, 8 * (t - 4));
+          }
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      mbar_arrive(&full_bar[b]);
+    }
+    if (ok) {
+      // buffer i & 1 is free (group i - 2 finished): it carries the end mark
+      const int b = i & 1;
+      if (pt == 0) gid_s[b] = -1;
+      asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
+      mbar_arrive(&full_bar[b]);
+      if (i >= 1) finish(i - 1);
+    }
+    return;
+  }
+
+  // ---------------- consumers
+  const int cw_id = warp - kPipeProducers;
+  uint32_t c[M][NW];
+  for (int i = 0;; i++) {
+    const int b = i & 1;
+    int okw = 1;
+    if (lane == 0) okw = mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, A.lim) ? 1 : 0;
+    okw = __shfl_sync(FULL, okw, 0);
+    if (!okw) {
+      if (lane == 0) atomicExch(errw, (int)ME_ERR_TIMEOUT);
+      break;
+    }
+    __syncwarp();
+    mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, A.lim);
+    if (gid_s[b] < 0) break;
+    const TabGroup& G = grp[b];
+    const int p = G.p, n = 2 * p + 1, nc = n, nseg = (n + T - 1) / T;
+    const int tasks = nc * nseg, F = G.nb * tasks, Rr = (F + 31) >> 5;
+    const int q0 = (cw_id * Rr) / kPipeConsumers, q1 = ((cw_id + 1) * Rr) / kPipeConsumers;
+    const int dseg = 32 / nc, dcol = 32 - (32 / nc) * nc;
+    const uint32_t lam = G.lam;
+    const int fast = key_mode(N, M, p, lam);
+    const int rb = rank_bits(p);
+    const uint32_t* cwb = buf0 + b * BST;
+    const uint32_t* tabJ = cwb + B * M * NW;
+    const uint32_t* tabK = tabJ + R;
+    const uint32_t* tabQ = tabK + R;
+    const uint32_t* sh = tabQ + R;
+    int f = 32 * q0 + lane;
+    int blk = f / tasks;
+    const int t0 = f - blk * tasks;
+    int seg = t0 / nc, col = t0 - (t0 / nc) * nc;
+    for (int q = q0; q < q1; q++, f += 32) {
+      if (f < F) {
+#pragma unroll
+        for (int j = 0; j < M; j++)
+#pragma unroll
+          for (int w = 0; w < NW; w++) c[j][w] = cwb[(blk * M + j) * NW + w];
+        const int row0 = seg * T;
+        uint32_t acc[T];
+        fs_run_sads<N, M, T>(c, sh + row0 * SP + blk * N + col, SP, acc);
+        atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
+      }
+      seg += dseg;
+      col += dcol;
+      if (col >= nc) { col -= nc; seg++; }
+      while (seg >= nseg) { seg -= nseg; blk++; }
     }
     mbar_arrive(&empty_bar[b]);
   }
@@ -874,14 +1179,14 @@ __global__ void __launch_bounds__(kSeq2Threads, 1) k_acbm_seq2(
   // ---------------------------------------------------------------- search group
   const int ns = blockDim.x - 32 * pbm_warps;   // search threads
   const int st = tid - 32 * pbm_warps;          // index within the group
-  const bool fast = fast32_ok(N, M, p, a.lam);
+  const int fast = key_mode(N, M, p, a.lam);
   const int rb = rank_bits(p);
   for (int r = st; r < g.rows; r += ns) {
     const int mvy = r - p;
     const int am = mvy < 0 ? -mvy : mvy;
     tabJ[r] = a.lam * (uint32_t)mv_bits(mvy);
     tabK[r] = ((uint32_t)am << 17) + (uint32_t)r * (uint32_t)n;
-    tabQ[r] = (tabJ[r] << rb) + (uint32_t)(2 * am - (mvy < 0 ? 1 : 0));
+    tabQ[r] = tabq_value(fast, tabJ[r], mvy, p);
   }
   const volatile int* vstate = s_state;
   for (;;) {
@@ -1304,6 +1609,52 @@ int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, 
   return ME_ERR_ARG;
 }
 
+// ------------------------------------------------------------------ pipelined search, any p: launches
+bool pipe_tab_applies(int N, int M, int p) {
+  const char* pe = std::getenv("ME_FSBM_PIPE");
+  if (pe && pe[0] == '0') return false;
+  return N == 16 && M == 16 && p >= 1 && p <= kMaxP && tab_rows<kTabT>(p) <= kTabRows;
+}
+
+int pipe_tab_bpc(int p) { return tab_bpc(p); }
+
+static int launch_pipe_tab(const TabArgs& A, int grid, cudaStream_t s) {
+  const size_t smem = tab_smem_bytes();
+  const int st = ensure_dynamic_smem((const void*)k_fsbm_pipe_tab, smem);
+  if (st) return st;
+  if (grid < 1) return ME_OK;
+  k_fsbm_pipe_tab<<<grid, kPipeThreads, smem, s>>>(A);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+int launch_pipe_tab_seq(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
+                        int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  if (K < 1 || K > kSeqMax || !pipe_tab_applies(16, 16, p)) return ME_ERR_ARG;
+  TabArgs A;
+  std::memset(&A, 0, sizeof(A));
+  for (int k = 0; k <= K; k++) A.fr.f[k] = frames[k];
+  A.W = W; A.H = H; A.p = p; A.K = K; A.lam = lam;
+  A.mv = mv_out; A.J = J_out; A.sad = sad_out;
+  const int BW = W / 16, BH = H / 16, bpc = tab_bpc(p);
+  A.ngroups = K * BH * ((BW + bpc - 1) / bpc);
+  A.lim = wait_cycles(1000000000ll);
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
+  return launch_pipe_tab(A, std::min(nsm, A.ngroups), s);
+}
+
+int launch_pipe_tab_batch(const BShape* shp, const BStream* st, const BFsEntry* ent, int nent,
+                          int* ctr, int* err, cudaStream_t s) {
+  TabArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.shp = shp; A.st = st; A.ent = ent; A.ngroups = nent; A.ctr = ctr; A.err = err;
+  A.lim = wait_cycles(1000000000ll);
+  int nsm = 1;
+  { const int e = sm_count(&nsm); if (e) return e; }
+  return launch_pipe_tab(A, std::min(nsm, nent), s);
+}
+
 // ------------------------------------------------------------------ tuned full search
 // Full search of K pairs (frames[k] -> frames[k+1]) in one launch, with the
 // launch form chosen by the autotuner on the first call of each shape: the
@@ -1314,7 +1665,8 @@ struct FsTune {
   int dev, W, H, N, M, p, K;
   bool pipe;
   struct Cand {
-    int pipeT;    // > 0: k_fsbm_pipe with this run length; 0: k_fsbm_seq with pl
+    int pipeT;    // > 0: k_fsbm_pipe with this run length; 0: k_fsbm_seq with pl;
+                  // -1: k_fsbm_pipe_tab (any p)
     FsPlan pl;
     std::string name;
   };
@@ -1346,6 +1698,10 @@ static FsTune* fs_tune_entry(int dev, int W, int H, int N, int M, int p, int K) 
         t->cands.push_back(FsTune::Cand{T, FsPlan{T, 0, 0, 0, 1}, nm});
       }
   }
+  if (pipe_tab_applies(N, M, p)) {
+    std::snprintf(nm, sizeof(nm), "pipetab B=%d", tab_bpc(p));
+    t->cands.push_back(FsTune::Cand{-1, FsPlan{kTabT, 0, 0, 0, 1}, nm});
+  }
   for (const FsPlan& pl : fs_plans_ranked(N, M, p, W / N, pipe ? 2 : 3)) {
     std::snprintf(nm, sizeof(nm), "group T=%d G=%d thr=%d", pl.T, pl.G, pl.threads);
     t->cands.push_back(FsTune::Cand{0, pl, nm});
@@ -1357,6 +1713,8 @@ static FsTune* fs_tune_entry(int dev, int W, int H, int N, int M, int p, int K) 
 static int fs_seq_enqueue(const FsTune::Cand& cd, const uint8_t* const* frames, int K, int W,
                           int H, int N, int M, int p, uint32_t lam, int16_t* mv_out,
                           uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
+  if (cd.pipeT < 0)
+    return launch_pipe_tab_seq(frames, K, W, H, p, lam, mv_out, J_out, sad_out, s);
   if (cd.pipeT > 0) {
     PipeOut o;
     std::memset(&o, 0, sizeof(o));
