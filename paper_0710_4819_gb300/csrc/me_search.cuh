@@ -113,40 +113,33 @@ __host__ __device__ inline int pbm_win_words(int N, int M, int p) {
   return 4 * ((15 + N + 2 * p + 4 + 15) / 16) * (M + 2 * p);
 }
 
-// One candidate's SAD computed by a single lane from the staged window: M rows
-// of N/4 words, each row read as N/4+1 words and shifted into place.
+// Part of one candidate's SAD computed by a single lane from the staged
+// window: rows j0 .. j0+nrows-1 of the block, each read as N/4+1 words and
+// shifted into place.  Not inlined and rolled, so the PBM code stays small and
+// in the instruction cache between blocks, when other code has run on the SM.
 template <int N, int M>
-__device__ __forceinline__ uint32_t lane_sad_win(const uint32_t* curs, const uint32_t* win,
-                                                 const PbmWin& wg, int p, int mvx, int mvy) {
+__device__ __noinline__ uint32_t lane_sad_rows(const uint32_t* curs, const uint32_t* win, PbmWin wg,
+                                               int p, int mvx, int mvy, int j0, int nrows) {
   constexpr int NW = N / 4;
   const int o = wg.s0 + p + mvx;
-  if (!ME_CHECK(p + mvy >= 0 && p + mvy + M <= wg.rows && o >= 0 && (o >> 2) + NW < wg.wp,
-                "ME_CHECK lane_sad_win p %d mv %d,%d rows %d wp %d s0 %d\n", p, mvx, mvy, wg.rows,
-                wg.wp, wg.s0))
+  if (!ME_CHECK(p + mvy + j0 >= 0 && p + mvy + j0 + nrows <= wg.rows && o >= 0 &&
+                    (o >> 2) + NW < wg.wp,
+                "ME_CHECK lane_sad_rows p %d mv %d,%d j0 %d rows %d wp %d s0 %d\n", p, mvx, mvy,
+                j0, wg.rows, wg.wp, wg.s0))
     return 0;
-  const uint32_t* rp = win + (p + mvy) * wg.wp + (o >> 2);
+  const uint32_t* rp = win + (p + mvy + j0) * wg.wp + (o >> 2);
+  const uint32_t* cp = curs + j0 * NW;
   const unsigned sh = 8u * (unsigned)(o & 3);
   uint32_t acc = 0;
-  // rolled (4 rows per iteration): PBM code is kept small so it stays in the
-  // instruction cache between blocks, when other code has run on the SM
 #pragma unroll 4
-  for (int j = 0; j < M; j++) {
+  for (int j = 0; j < nrows; j++) {
     uint32_t wv[NW + 1];
 #pragma unroll
     for (int w = 0; w <= NW; w++) wv[w] = rp[j * wg.wp + w];
 #pragma unroll
-    for (int w = 0; w < NW; w++) acc = sad4(curs[j * NW + w], __funnelshift_r(wv[w], wv[w + 1], sh), acc);
+    for (int w = 0; w < NW; w++) acc = sad4(cp[j * NW + w], __funnelshift_r(wv[w], wv[w + 1], sh), acc);
   }
   return acc;
-}
-
-template <int N, int M>
-__device__ __noinline__ unsigned long long lane_key(const uint32_t* curs, const uint32_t* win,
-                                                    PbmWin wg, int mvx, int mvy, int p,
-                                                    uint32_t lam) {
-  const uint32_t s = lane_sad_win<N, M>(curs, win, wg, p, mvx, mvy);
-  const uint32_t J = 256u * s + lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy));
-  return make_key(J, mvx, mvy, p);
 }
 
 // Result of the PBM stage for one block (valid in every lane of the warp).
@@ -306,61 +299,121 @@ __device__ __forceinline__ void pbm_stamp(unsigned long long* tr, int i) {
   }
 }
 
+// Candidates held by lanes (position ex, ey; act: to evaluate), each
+// candidate's rows split over `parts` lanes (2, 4 or 8, at most M): lane
+// c*parts + q sums rows q*M/parts .. (q+1)*M/parts-1 of the candidate held
+// by lane c.  Returns the warp's best key (every lane).
 template <int N, int M>
-__device__ PbmResult pbm_eval(int cx, int cy, bool valid, const PbmWin& wg, int p, uint32_t lam,
-                              uint32_t intra_x, int32_t alpha, int32_t beta, int32_t gnum,
-                              int32_t gden, int32_t qp, int32_t refine, const uint32_t* curs,
-                              const uint32_t* win, unsigned long long* tr = nullptr) {
+__device__ __forceinline__ unsigned long long pbm_eval_set(int ex, int ey, bool act, int parts,
+                                                           const PbmWin& wg, int p, uint32_t lam,
+                                                           const uint32_t* curs,
+                                                           const uint32_t* win) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int c = lane / parts, q = lane - c * parts;
+  const int ccx = __shfl_sync(FULL, ex, c), ccy = __shfl_sync(FULL, ey, c);
+  const bool cact = __shfl_sync(FULL, act ? 1 : 0, c) != 0;
+  uint32_t s = cact ? lane_sad_rows<N, M>(curs, win, wg, p, ccx, ccy, q * (M / parts), M / parts) : 0u;
+  for (int o = 1; o < parts; o <<= 1) s += __shfl_xor_sync(FULL, s, o);
+  const unsigned long long key =
+      cact && q == 0 ? make_key(256u * s + lam * (uint32_t)(mv_bits(ccx) + mv_bits(ccy)), ccx, ccy, p)
+                     : kNoKey;
+  return warp_min64(key);
+}
+
+// PBM in two parts, so that the predictors known early can be evaluated
+// while the warp still waits for its spatial neighbours:
+//   pbm_part_a: the distinct clipped positions among the temporal predictors
+//               and the zero vector (lanes 4-13), best by J;
+//   pbm_part_b: the spatial predictors (lanes 0-3) not already evaluated,
+//               the +-1 ring around the best of all predictors (skipping
+//               positions already evaluated) and the two conditions.
+// Together they evaluate exactly the distinct positions of Sec. 2.2 steps
+// 1-3 (which lane evaluates a repeated position does not matter: its key is
+// the same).  Every lane passes its own predictor (cx, cy, valid).
+struct PbmPart {
+  unsigned long long best;
+  int load;
+};
+
+__device__ __forceinline__ int pbm_code(int cx, int cy, bool valid, int p) {
+  const int lane = threadIdx.x & 31;
+  return valid ? ((clampi(cy, -p, p) + p) << 8) + (clampi(cx, -p, p) + p) : -1 - lane;
+}
+
+template <int N, int M>
+__device__ PbmPart pbm_part_a(int cx, int cy, bool valid, const PbmWin& wg, int p, uint32_t lam,
+                              const uint32_t* curs, const uint32_t* win,
+                              unsigned long long* tr = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
   pbm_stamp(tr, 0);
-  cx = clampi(cx, -p, p);
-  cy = clampi(cy, -p, p);
-  const int code = valid ? ((cy + p) << 8) + (cx + p) : -1 - lane;
+  const bool mine = valid && lane >= 4 && lane < 14;
+  const int code = pbm_code(cx, cy, mine, p);
+  bool dup = false;
+#pragma unroll 1
+  for (int l = 4; l < 14; l++) {
+    const int v = __shfl_sync(FULL, code, l);
+    dup |= (l < lane) && (v == code);
+  }
+  const bool act = mine && !dup;
+  PbmPart r;
+  r.best = pbm_eval_set<N, M>(clampi(cx, -p, p), clampi(cy, -p, p), act, 2, wg, p, lam, curs, win);
+  r.load = __popc(__ballot_sync(FULL, act));
+  return r;
+}
+
+template <int N, int M>
+__device__ PbmResult pbm_part_b(int cx, int cy, bool valid, const PbmPart& pa, const PbmWin& wg,
+                                int p, uint32_t lam, uint32_t intra_x, int32_t alpha,
+                                int32_t beta, int32_t gnum, int32_t gden, int32_t qp,
+                                int32_t refine, const uint32_t* curs, const uint32_t* win,
+                                unsigned long long* tr = nullptr) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  // every predictor's code (lanes 0-13); a spatial one repeating a temporal
+  // one, or an earlier spatial one, is not evaluated again
+  const bool is_pred = valid && lane < 14;
+  const int code = pbm_code(cx, cy, is_pred, p);
   bool dup = false;
 #pragma unroll 1
   for (int l = 0; l < 14; l++) {
     const int v = __shfl_sync(FULL, code, l);
-    dup |= (l < lane) && (v == code);
+    dup |= (l >= 4 || l < lane) && l != lane && (v == code);
   }
-  const bool eval = valid && !dup;
-  // phase 0 (step 2): every distinct predictor, best by J; phase 1 (step 3):
-  // the +-1 integer ring around that best, without positions already
-  // evaluated.  One rolled loop, so the candidate code exists once.
-  unsigned long long best = kNoKey;
-  int load = 0;
-  int ex = cx, ey = cy;
-  bool act = eval;
-#pragma unroll 1
-  for (int ph = 0; ph < (refine ? 2 : 1); ph++) {
-    if (ph == 1) {
-      const Decoded d = decode_key(best, p, lam);
-      int rcode = -100 - lane;
-      ex = 0;
-      ey = 0;
-      if (lane < 8) {
-        const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
-        ex = clampi(d.mvx + o % 3 - 1, -p, p);
-        ey = clampi(d.mvy + o / 3 - 1, -p, p);
-        rcode = ((ey + p) << 8) + (ex + p);
-      }
-      const int ecode = eval ? code : -1;
-      bool rdup = false;
-#pragma unroll 1
-      for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
-#pragma unroll 1
-      for (int l = 0; l < 8; l++) {
-        const int v = __shfl_sync(FULL, rcode, l);
-        rdup |= (l < lane) && (v == rcode);
-      }
-      act = lane < 8 && !rdup;
+  const bool actb = is_pred && lane < 4 && !dup;
+  unsigned long long best =
+      umin64(pa.best, pbm_eval_set<N, M>(clampi(cx, -p, p), clampi(cy, -p, p), actb,
+                                         M >= 8 ? 8 : 4, wg, p, lam, curs, win));
+  int load = pa.load + __popc(__ballot_sync(FULL, actb));
+  pbm_stamp(tr, 1);
+  if (refine) {
+    // every predictor's position has been evaluated (by its lane or by the
+    // lane it repeats), so a ring position equal to any predictor's is skipped
+    const int ecode = is_pred ? code : -1;
+    const Decoded d = decode_key(best, p, lam);
+    int rcode = -100 - lane;
+    int ex = 0, ey = 0;
+    if (lane < 8) {
+      const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
+      ex = clampi(d.mvx + o % 3 - 1, -p, p);
+      ey = clampi(d.mvy + o / 3 - 1, -p, p);
+      rcode = ((ey + p) << 8) + (ex + p);
     }
-    const unsigned long long key = act ? lane_key<N, M>(curs, win, wg, ex, ey, p, lam) : kNoKey;
-    best = umin64(best, warp_min64(key));
+    bool rdup = false;
+#pragma unroll 1
+    for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
+#pragma unroll 1
+    for (int l = 0; l < 8; l++) {
+      const int v = __shfl_sync(FULL, rcode, l);
+      rdup |= (l < lane) && (v == rcode);
+    }
+    const bool act = lane < 8 && !rdup;
+    best = umin64(best, pbm_eval_set<N, M>(ex, ey, act, 4, wg, p, lam, curs, win));
     load += __popc(__ballot_sync(FULL, act));
-    pbm_stamp(tr, 1 + ph);
+    pbm_stamp(tr, 2);
   }
   // Sec. 3.2 conditions in exact integers (intra_x = NM * Intra_SAD)
   const Decoded d = decode_key(best, p, lam);
@@ -372,6 +425,30 @@ __device__ PbmResult pbm_eval(int cx, int cy, bool valid, const PbmWin& wg, int 
   res.load = load;
   res.pass = c1 || c2;
   return res;
+}
+
+// Whether a block whose PBM winner had this key would fail both conditions
+// (used on part a's best to start a likely full search early).
+template <int N, int M>
+__device__ __forceinline__ bool pbm_would_fail(unsigned long long key, int p, uint32_t lam,
+                                               uint32_t intra_x, int32_t alpha, int32_t beta,
+                                               int32_t gnum, int32_t gden, int32_t qp) {
+  const Decoded d = decode_key(key, p, lam);
+  const long long NM = N * M, sad = d.sad, q = qp;
+  const bool c1 = (long long)intra_x + NM * sad < NM * ((long long)alpha + (long long)beta * q * q);
+  const bool c2 = (long long)gden * NM * sad < (long long)gnum * (long long)intra_x;
+  return !(c1 || c2);
+}
+
+// The whole PBM stage of one block with every predictor in hand.
+template <int N, int M>
+__device__ PbmResult pbm_eval(int cx, int cy, bool valid, const PbmWin& wg, int p, uint32_t lam,
+                              uint32_t intra_x, int32_t alpha, int32_t beta, int32_t gnum,
+                              int32_t gden, int32_t qp, int32_t refine, const uint32_t* curs,
+                              const uint32_t* win, unsigned long long* tr = nullptr) {
+  const PbmPart pa = pbm_part_a<N, M>(cx, cy, valid, wg, p, lam, curs, win, tr);
+  return pbm_part_b<N, M>(cx, cy, valid, pa, wg, p, lam, intra_x, alpha, beta, gnum, gden, qp,
+                          refine, curs, win, tr);
 }
 
 // PBM of block (bx, by) with its predictors read from the current-frame field

@@ -713,24 +713,28 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
 // ------------------------------------------------------------------ ACBM
 
 
-// Optional per-block timeline of k_acbm_seq for latency analysis, compiled in
-// only with ME_SEQ_TRACE: [block][claimed, predecessors ready, PBM decided,
-// full search started, full search published, window staged, PBM evaluated,
-// full search evaluated] in globaltimer nanoseconds.
-#ifdef ME_SEQ_TRACE
-static __device__ __forceinline__ long long seq_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+// Speculative full searches of the ACBM sequence: the queue word of such a
+// search carries kSeqSpecBit beside the block; the block's state word (bdone,
+// cleared by the prologue) collects kSeqSearched (the search's key is in
+// bkey) and kSeqFailed (PBM failed): whichever comes second publishes.
+constexpr int kSeqSpecBit = 1 << 30;
+constexpr int kSeqSearched = 1, kSeqFailed = 2;
+
+// Publishes block o (pair k, block b of the pair) with the full-search key:
+// the flag word first (it carries the vector), then the outputs.
+__device__ __forceinline__ void seq_publish_fs(const SeqArgs& a, unsigned long long* flags, int epoch,
+                                               int o, int k, int b, int nbf, int p, int n,
+                                               unsigned long long key) {
+  const Decoded d = decode_key(key, p, a.lam);
+  atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
+  int16_t* field = a.mv + (size_t)k * nbf * 2;
+  field[2 * b] = (int16_t)d.mvx;
+  field[2 * b + 1] = (int16_t)d.mvy;
+  a.J[o] = d.J;
+  a.mask[o] = 1;
+  if (a.sad) a.sad[o] = d.sad;
+  if (a.load) a.load[o] = (uint32_t)(n * n);
 }
-__device__ unsigned long long* g_seq_trace = nullptr;
-#define SEQ_TRACE(o, j)                                                     \
-  do {                                                                      \
-    if (g_seq_trace) g_seq_trace[(size_t)(o) * 16 + (j)] = (unsigned long long)seq_ns(); \
-  } while (0)
-#else
-#define SEQ_TRACE(o, j) do { } while (0)
-#endif
 
 __global__ void k_seq_begin(SeqCtrl* c) {
   for (int i = threadIdx.x; i < kRoleSlots; i += blockDim.x) c->sm_arr[i] = 0;
@@ -807,7 +811,8 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              unsigned long long* __restrict__ q,
                                                              unsigned long long* __restrict__ bkey,
                                                              int* __restrict__ bdone, int S,
-                                                             int pbm_warps, int search_every) {
+                                                             int pbm_warps, int search_every,
+                                                             int spec) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_item, s_role, s_slice;
@@ -837,7 +842,6 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       const int i = __shfl_sync(FULL, nxt, 0);
       if (i >= total) break;
       const int o = __shfl_sync(FULL, onxt, 0);
-      if (lane == 0) SEQ_TRACE(o, 0);
       const int k = o / nbf, b = o - k * nbf;
       const int bx = b % BW, by = b / BW;
       const PbmWin wg = pbm_stage<N, M>(fr.f[k + 1], refpad + (size_t)k * padsz, pg, W, p, bx * N,
@@ -869,38 +873,39 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       } else if (lane == 13) {
         valid = true;
       }
+      // the temporal predecessors first (pair k-1: usually finished already)
       {
-        const unsigned long long w = warp_wait_flags(nidx >= 0 ? flags + nidx : nullptr, epoch,
-                                                     &ctrl->error, &ctrl->err_item,
-                                                     timeout, i);
-        if (nidx >= 0) {
+        const bool tl = lane >= 4 && nidx >= 0;
+        const unsigned long long w = warp_wait_flags(tl ? flags + nidx : nullptr, epoch,
+                                                     &ctrl->error, &ctrl->err_item, timeout, i);
+        if (tl) {
           cx = pub_mvx(w);
           cy = pub_mvy(w);
         }
       }
-#ifdef ME_SEQ_TRACE
-      __syncwarp();
-      if (lane == 0) SEQ_TRACE(o, 1);
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      if (lane == 0 && g_seq_trace) {
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        g_seq_trace[(size_t)o * 16 + 11] = ((unsigned long long)smid << 16) | ((unsigned)warp << 8) |
-                                           0u;
+      const PbmPart pa = pbm_part_a<N, M>(cx, cy, valid, wg, p, a.lam, curs, win);
+      // A block whose temporal and zero predictors already fail both
+      // conditions nearly always fails with its spatial ones too: its full
+      // search is queued now (speculatively), while the warp waits for the
+      // spatial neighbours.  The block's final result does not depend on
+      // the guess: a search whose block passes PBM is discarded.
+      const bool sp = spec && pbm_would_fail<N, M>(pa.best, p, a.lam, ix, a.alpha, a.beta, a.gnum,
+                                                   a.gden, a.qp);
+      if (sp && lane == 0) {
+        const int slot = atomicAdd(&ctrl->fs_tail, 1);
+        atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o | kSeqSpecBit);
       }
-      __syncwarp();
-      if (lane == 0) SEQ_TRACE(o, 5);
-#endif
-#ifdef ME_SEQ_TRACE
-      unsigned long long* trp = g_seq_trace ? g_seq_trace + (size_t)o * 16 + 8 : nullptr;
-#else
-      unsigned long long* trp = nullptr;
-#endif
-      const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, p, a.lam, ix, a.alpha, a.beta, a.gnum,
-                                         a.gden, a.qp, a.refine, curs, win, trp);
-#ifdef ME_SEQ_TRACE
-      if (lane == 0) SEQ_TRACE(o, 6);
-#endif
+      {
+        const bool sl = lane < 4 && nidx >= 0;
+        const unsigned long long w = warp_wait_flags(sl ? flags + nidx : nullptr, epoch,
+                                                     &ctrl->error, &ctrl->err_item, timeout, i);
+        if (sl) {
+          cx = pub_mvx(w);
+          cy = pub_mvy(w);
+        }
+      }
+      const PbmResult r = pbm_part_b<N, M>(cx, cy, valid, pa, wg, p, a.lam, ix, a.alpha, a.beta,
+                                           a.gnum, a.gden, a.qp, a.refine, curs, win);
       if (lane == 0) {
         if (r.pass) {
           // the flag word carries the vector: publish first, outputs after
@@ -913,6 +918,15 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
           a.mask[o] = 0;
           if (a.sad) a.sad[o] = d.sad;
           if (a.load) a.load[o] = (uint32_t)r.load;
+        } else if (sp) {
+          // the speculative search publishes if it finishes after this
+          // decision; if it finished before, its key is here to publish
+          const int old = atomicOr(bdone + o, kSeqFailed);
+          if (old & kSeqSearched) {
+            __threadfence();
+            seq_publish_fs(a, flags, epoch, o, k, b, nbf, p, n,
+                           *reinterpret_cast<volatile unsigned long long*>(bkey + o));
+          }
         } else {
           // S queue entries (one per column slice; slot % S is the slice),
           // each = epoch and block in one word; the tail count is ordered
@@ -920,10 +934,9 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
           const int slot = atomicAdd(&ctrl->fs_tail, S);
           for (int sl = 0; sl < S; sl++)
             atomicExch(q + slot + sl, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o);
-          __threadfence();
         }
+        __threadfence();
         atomicAdd(&ctrl->pbm_done, 1);
-        SEQ_TRACE(o, 2);
         // the next claim, once this block is out of the warp's hands (a claim
         // taken earlier would sit behind this block's wait)
         nxt = atomicAdd(&ctrl->next, 1);
@@ -950,7 +963,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         for (int it = 0;; it++) {
           if (slot >= qcap) break;
           const unsigned long long e = *rd;
-          if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
+          if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }   // block | speculative bit
           // the end-of-run and error words are shared by every poller: read
           // them on every 8th round only
           if ((it & 7) == 7) {
@@ -967,26 +980,21 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         s_item = got;
       }
       __syncthreads();
-      const int o = s_item;
-      if (o < 0) break;
+      if (s_item == -1) break;
+      const bool specj = (s_item & kSeqSpecBit) != 0;
+      const int o = s_item & ~kSeqSpecBit;
       if (o >= total) {
         // not a block of this run: report it instead of touching memory
         if (tid == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
         __syncthreads();
         continue;
       }
-      if (tid == 0) SEQ_TRACE(o, 3);
       const int k = o / nbf, b = o - k * nbf;
       // this CTA's slice of the mvx columns
       const int nc0 = (n + S - 1) / S, c0 = s_slice * nc0;
       const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x, c0, min(nc0, n - c0));
-#ifdef ME_SEQ_TRACE
-      unsigned long long* ftr = g_seq_trace ? g_seq_trace + (size_t)o * 16 + 12 : nullptr;
-#else
-      unsigned long long* ftr = nullptr;
-#endif
       fs_group<N, M, T>(fr.f[k + 1], fr.f[k], W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys,
-                        ftr, FsPad{refpad + (size_t)k * padsz, pg.pitch, pg.P, pg.rows});
+                        nullptr, FsPad{refpad + (size_t)k * padsz, pg.pitch, pg.P, pg.rows});
       bool last = true;
       unsigned long long key = keys[0];
       if (S > 1 && tid == 0) {
@@ -997,19 +1005,15 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
         last = atomicAdd(bdone + o, 1) == S - 1;
         if (last) key = atomicMin(bkey + o, kNoKey);
       }
-      if (tid == 0 && last) {
-        SEQ_TRACE(o, 7);
-        const Decoded d = decode_key(key, p, a.lam);
-        atomicExch(flags + o, pub_word(epoch, d.mvx, d.mvy));
-        int16_t* field = a.mv + (size_t)k * nbf * 2;
-        field[2 * b] = (int16_t)d.mvx;
-        field[2 * b + 1] = (int16_t)d.mvy;
-        a.J[o] = d.J;
-        a.mask[o] = 1;
-        if (a.sad) a.sad[o] = d.sad;
-        if (a.load) a.load[o] = (uint32_t)(n * n);
-        SEQ_TRACE(o, 4);
+      if (tid == 0 && specj) {
+        // a speculative search publishes only if its block has failed PBM;
+        // else the PBM warp publishes this key when it decides (or the
+        // block passed and the key is not used)
+        bkey[o] = key;
+        __threadfence();
+        last = (atomicOr(bdone + o, kSeqSearched) & kSeqFailed) != 0;
       }
+      if (tid == 0 && last) seq_publish_fs(a, flags, epoch, o, k, b, nbf, p, n, key);
       __syncthreads();
     }
   }
@@ -1360,6 +1364,7 @@ struct SeqPlan {
     int T;        // run length of the full searches
     int split;    // ver 1: every split-th SM hosts two search CTAs (0: none)
     int pw;       // ver 1: PBM warps per PBM CTA; ver 2: PBM warps per CTA
+    int spec;     // ver 1: speculative full searches (single-slice searches only)
     size_t smem;
     int grid;
     std::string name;
@@ -1440,13 +1445,23 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
   // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
   // the 8-row build at 85 registers measured 30 % slower.)
   if (per_sm >= 2) {
+    // speculation on unless ME_SEQ_SPEC=0 (A/B sweeps); the model's form is
+    // also timed without it
+    const char* se = std::getenv("ME_SEQ_SPEC");
+    const int spec = pl->S == 1 && !(se && se[0] == '0') ? 1 : 0;
     static const int splits[] = {kSeqSearchEvery, 2, 4};
     for (int sp : splits) {
       if (pl->S > 1 && sp != kSeqSearchEvery) continue;
       char nm[64];
-      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d", T, sp);
+      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d", T, sp, spec);
       if (model_T && sp == kSeqSearchEvery) pl->model = (int)pl->cands.size();
-      pl->cands.push_back(SeqPlan::Cand{1, T, sp, seq_pbm_warps(N, M, p), sm1, 2 * nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{1, T, sp, seq_pbm_warps(N, M, p), spec, sm1, 2 * nsm, nm});
+    }
+    if (spec && model_T) {
+      char nm[64];
+      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=0", T, kSeqSearchEvery);
+      pl->cands.push_back(
+          SeqPlan::Cand{1, T, kSeqSearchEvery, seq_pbm_warps(N, M, p), 0, sm1, 2 * nsm, nm});
     }
   }
   if (pl->S == 1) {
@@ -1461,7 +1476,7 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
       if (per2 < 1) continue;
       char nm[64];
       std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
-      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, sm2, nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, sm2, nsm, nm});
     }
   }
   return ME_OK;
@@ -1829,7 +1844,7 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
     else                                                                                       \
       k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
           fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total,          \
-          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split);                       \
+          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split, cd.spec);              \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)
