@@ -789,6 +789,166 @@ __global__ void __launch_bounds__(256) k_seq_prologue(SeqFrames fr, int K, PadGe
   }
 }
 
+// Shared memory (words) of one search group of k_acbm_seq: the block's raw
+// window in the PBM layout and its current pixels, the shifted words and the
+// per-row cost tables.
+template <int N, int M, int T>
+__host__ __device__ inline size_t seq_group_words(int p, int ng) {
+  const FsGeom g = fs_geom<N, M, T>(p, 1, ng);
+  // a multiple of 4 words: each group's window starts 16-byte aligned (its
+  // rows arrive by 16-byte asynchronous copies)
+  const size_t w = (size_t)pbm_win_words(N, M, p) + M * (N / 4) + (size_t)g.rows * g.pos + 3 * (size_t)g.rows;
+  return (w + 3) & ~(size_t)3;
+}
+
+// One search group of k_acbm_seq: ng threads (index gt) of the search CTA
+// that take queued blocks one at a time and search each in full, with named
+// barrier `bar` among themselves (a CTA can hold two groups, so that one
+// group stages its window while the other searches).  A group takes the
+// next queue slot, waits (bounded) for its entry or for the end of the run,
+// stages the block's window from the pair's padded reference by 16-byte
+// asynchronous copies, builds the shifted words, runs its share of the
+// (2p+1) x ceil((2p+1)/T) runs, and publishes the block (a speculative
+// search only if its block has failed PBM, see kSeqSpecBit).
+template <int N, int M, int T>
+__device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, int H, int p,
+                                 const PadGeom& pg, const uint8_t* __restrict__ refpad,
+                                 unsigned long long* __restrict__ flags, int total, SeqCtrl* ctrl,
+                                 unsigned long long* __restrict__ q,
+                                 unsigned long long* __restrict__ bkey, int* __restrict__ bdone,
+                                 int epoch, long long timeout, uint32_t* gs, int gt, int ng, int bar,
+                                 volatile int* s_item, unsigned long long* s_red) {
+  constexpr int NW = N / 4;
+  const int lane = threadIdx.x & 31;
+  const int BW = W / N, nbf = BW * (H / M);
+  const size_t padsz = (size_t)pg.pitch * pg.rows;
+  const int n = 2 * p + 1;
+  const int wwin = pbm_win_words(N, M, p);
+  const FsGeom g = fs_geom<N, M, T>(p, 1, ng);
+  uint32_t* raw = gs;                        // window [rows][wp] + current block
+  uint32_t* sh = gs + wwin + M * NW;         // [g.rows][g.pos]
+  uint32_t* tabJ = sh + g.rows * g.pos;
+  uint32_t* tabK = tabJ + g.rows;
+  uint32_t* tabQ = tabK + g.rows;
+  const int fast = key_mode(N, M, p, a.lam);
+  const int rb = rank_bits(p);
+  for (int r = gt; r < g.rows; r += ng) {
+    const int mvy = r - p;
+    const int am = mvy < 0 ? -mvy : mvy;
+    tabJ[r] = a.lam * (uint32_t)mv_bits(mvy);
+    tabK[r] = ((uint32_t)am << 17) + (uint32_t)r * (uint32_t)n;
+    tabQ[r] = tabq_value(fast, tabJ[r], mvy, p);
+  }
+  if (gt == 0) *s_red = kNoKey;
+  for (;;) {
+    if (gt == 0) {
+      const int slot = atomicAdd(&ctrl->fs_head, 1);
+      // the queue holds at most `total` entries: a slot beyond can never be
+      // filled, so the group is done without touching it
+      const volatile unsigned long long* rd = q + (slot < total ? slot : 0);
+      const volatile int* done = &ctrl->pbm_done;
+      const volatile int* tail = &ctrl->fs_tail;
+      const volatile int* err = &ctrl->error;
+      const long long t0 = clock64();
+      int got = -1;
+      unsigned nsl = 32;
+      for (int it = 0;; it++) {
+        if (slot >= total) break;
+        const unsigned long long e = *rd;
+        if (pub_epoch(e) == epoch) { got = (int)(uint32_t)e; break; }
+        if ((it & 7) == 7) {
+          if (*done == total && *tail <= slot) break;   // no more blocks will come
+          if (*err != 0) break;
+          if (clock64() - t0 > timeout) {
+            atomicExch(&ctrl->error, (int)ME_ERR_TIMEOUT);
+            break;
+          }
+        }
+        __nanosleep(nsl);
+        if (nsl < 256) nsl *= 2;
+      }
+      *s_item = got;
+    }
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
+    const int item = *s_item;
+    if (item == -1) break;
+    const bool specj = (item & kSeqSpecBit) != 0;
+    const int o = item & ~kSeqSpecBit;
+    if (o >= total) {
+      // not a block of this run: report it instead of touching memory
+      if (gt == 0) atomicExch(&ctrl->error, (int)ME_ERR_CUDA);
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
+      continue;
+    }
+    const int k = o / nbf, b = o - k * nbf;
+    const int x0 = (b % BW) * N, y0 = (b / BW) * M;
+    const PbmWin wg = pbm_win(N, M, p, x0, pg.P);
+    {
+      const uint8_t* cur = fr.f[k + 1];
+      for (int i = gt; i < M * NW; i += ng) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + wwin + i);
+        const void* src = cur + (size_t)(y0 + i / NW) * W + x0 + 4 * (i % NW);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+      }
+      const uint8_t* base = refpad + (size_t)k * padsz + (size_t)(y0 + pg.P - p) * pg.pitch +
+                            ((x0 + pg.P - p) & ~15);
+      for (int i = gt; i < wg.rows * wg.chunks; i += ng) {
+        const int r = i / wg.chunks, c = i - r * wg.chunks;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + r * wg.wp + 4 * c);
+        const void* src = base + (size_t)r * pg.pitch + 16 * c;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
+    // shifted words: sh[r][o] = window bytes s0+o .. s0+o+3 of row r (rows
+    // past the window's last row only feed candidates beyond 2p: any row)
+    for (int i = gt; i < g.rows * g.pos; i += ng) {
+      const int r = i / g.pos, oo = i - r * g.pos;
+      const int rr = r < wg.rows ? r : wg.rows - 1;
+      const int kk = wg.s0 + oo;
+      const uint32_t* row = raw + rr * wg.wp;
+      sh[r * g.pos + oo] = __funnelshift_r(row[kk >> 2], row[(kk >> 2) + 1], 8 * (kk & 3));
+    }
+    uint32_t c[M][NW];
+#pragma unroll
+    for (int j = 0; j < M; j++)
+#pragma unroll
+      for (int w = 0; w < NW; w++) c[j][w] = raw[wwin + j * NW + w];
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
+    unsigned long long best = kNoKey;
+    {
+      const int nc = g.nc;
+      int seg = gt / nc, col = gt - (gt / nc) * nc;
+      const int dseg = ng / nc, dcol = ng - (ng / nc) * nc;
+      for (int t = gt; t < g.tasks; t += ng) {
+        const int row0 = seg * T;
+        uint32_t acc[T];
+        fs_run_sads<N, M, T>(c, sh + row0 * g.pos + col, g.pos, acc);
+        best = umin64(best, fs_run_key<T>(acc, row0, col, p, n, a.lam, rb, fast, tabJ, tabK, tabQ));
+        seg += dseg;
+        col += dcol;
+        if (col >= nc) { col -= nc; seg++; }
+      }
+    }
+    best = warp_min64(best);
+    if (lane == 0 && best != kNoKey) atomicMin(s_red, best);
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
+    if (gt == 0) {
+      const unsigned long long key = *s_red;
+      *s_red = kNoKey;
+      bool pub = true;
+      if (specj) {
+        bkey[o] = key;
+        __threadfence();
+        pub = (atomicOr(bdone + o, kSeqSearched) & kSeqFailed) != 0;
+      }
+      if (pub) seq_publish_fs(a, flags, epoch, o, k, b, nbf, p, n, key);
+    }
+  }
+}
+
 // Two roles in one launch (cta_role: one CTA of each per SM).  PBM CTAs: each
 // warp claims blocks on its own in the (wave + 4*pair) order (the item table
 // maps a claim to its block), queues the block's current pixels and search
@@ -812,7 +972,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              unsigned long long* __restrict__ bkey,
                                                              int* __restrict__ bdone, int S,
                                                              int pbm_warps, int search_every,
-                                                             int spec) {
+                                                             int spec, int sgroups) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_item, s_role, s_slice;
@@ -944,6 +1104,14 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       }
       __syncwarp();
     }
+  } else if (sgroups > 0) {
+    // ---------------------------------------------------------------- search groups
+    __shared__ int s_gitem[2];
+    __shared__ unsigned long long s_gred[2];
+    const int ng = kSeqThreads / sgroups, gid = tid / ng;
+    seq_search_group<N, M, T>(fr, a, W, H, p, pg, refpad, flags, total, ctrl, q, bkey, bdone, epoch,
+                              timeout, smem + gid * seq_group_words<N, M, T>(p, ng), tid - gid * ng,
+                              ng, 1 + gid, &s_gitem[gid], &s_gred[gid]);
   } else {
     // ---------------------------------------------------------------- search CTAs
     for (;;) {
@@ -1365,6 +1533,7 @@ struct SeqPlan {
     int split;    // ver 1: every split-th SM hosts two search CTAs (0: none)
     int pw;       // ver 1: PBM warps per PBM CTA; ver 2: PBM warps per CTA
     int spec;     // ver 1: speculative full searches (single-slice searches only)
+    int sgroups;  // ver 1: search groups per search CTA (named barriers); 0: one, fs_group
     size_t smem;
     int grid;
     std::string name;
@@ -1384,9 +1553,12 @@ static int seq_pbm_warps(int N, int M, int p) {
 }
 
 template <int N, int M, int T>
-static size_t seq_smem(int p) {
+static size_t seq_smem(int p, int sgroups = 0) {
   const size_t pbm = (size_t)4 * seq_pbm_warps(N, M, p) * (pbm_win_words(N, M, p) + M * (N / 4));
-  return std::max(fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads)), pbm);
+  const size_t srch = sgroups > 0
+                          ? 4 * (size_t)sgroups * seq_group_words<N, M, T>(p, kSeqThreads / sgroups)
+                          : fs_smem_bytes<N, M, T>(fs_geom<N, M, T>(p, 1, kSeqThreads));
+  return std::max(srch, pbm);
 }
 
 // Shared memory of k_acbm_seq2 with pw PBM warps.
@@ -1434,37 +1606,40 @@ static std::vector<int> seq_Ts(int N, int M, int p) {
 template <int N, int M, int T>
 static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
   const int p = pl->p;
-  int per_sm = 0;
-  const size_t sm1 = seq_smem<N, M, T>(p);
-  {
-    const int e = ensure_dynamic_smem((const void*)k_acbm_seq<N, M, T>, sm1);
-    if (e) return e;
-  }
-  ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<N, M, T>, kSeqThreads,
-                                                        sm1));
-  // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
-  // the 8-row build at 85 registers measured 30 % slower.)
-  if (per_sm >= 2) {
-    // speculation on unless ME_SEQ_SPEC=0 (A/B sweeps); the model's form is
-    // also timed without it
-    const char* se = std::getenv("ME_SEQ_SPEC");
-    const int spec = pl->S == 1 && !(se && se[0] == '0') ? 1 : 0;
-    static const int splits[] = {kSeqSearchEvery, 2, 4};
-    for (int sp : splits) {
-      if (pl->S > 1 && sp != kSeqSearchEvery) continue;
-      char nm[64];
-      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d", T, sp, spec);
-      if (model_T && sp == kSeqSearchEvery) pl->model = (int)pl->cands.size();
-      pl->cands.push_back(SeqPlan::Cand{1, T, sp, seq_pbm_warps(N, M, p), spec, sm1, 2 * nsm, nm});
-    }
-    if (spec && model_T) {
-      char nm[64];
-      std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=0", T, kSeqSearchEvery);
-      pl->cands.push_back(
-          SeqPlan::Cand{1, T, kSeqSearchEvery, seq_pbm_warps(N, M, p), 0, sm1, 2 * nsm, nm});
-    }
-  }
+  // speculation on unless ME_SEQ_SPEC=0 (A/B sweeps); the model's form is
+  // also timed without it
+  const char* se = std::getenv("ME_SEQ_SPEC");
+  const int spec = pl->S == 1 && !(se && se[0] == '0') ? 1 : 0;
+  struct Form { int split, spec, sg; };
+  std::vector<Form> forms{{kSeqSearchEvery, spec, 0}};
   if (pl->S == 1) {
+    forms.push_back({2, spec, 0});
+    if (model_T) forms.push_back({4, spec, 0});
+    if (spec && model_T) forms.push_back({kSeqSearchEvery, 0, 0});
+    forms.push_back({kSeqSearchEvery, spec, 2});
+    forms.push_back({2, spec, 2});
+  }
+  for (const Form& f : forms) {
+    const size_t sm1 = seq_smem<N, M, T>(p, f.sg);
+    if (sm1 > 220 * 1024) continue;
+    {
+      const int e = ensure_dynamic_smem((const void*)k_acbm_seq<N, M, T>, sm1);
+      if (e) return e;
+    }
+    int per_sm = 0;
+    ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<N, M, T>, kSeqThreads,
+                                                          sm1));
+    // two CTAs per SM, one of each role (cta_role).  (A third CTA per SM with
+    // the 8-row build at 85 registers measured 30 % slower.)
+    if (per_sm < 2) continue;
+    char nm[64];
+    std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d groups=%d", T, f.split, f.spec,
+                  f.sg > 0 ? f.sg : 1);
+    if (model_T && &f == &forms[0]) pl->model = (int)pl->cands.size();
+    pl->cands.push_back(
+        SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, sm1, 2 * nsm, nm});
+  }
+  if (pl->S == 1 && model_T) {
     for (int pw = 4; pw <= 5; pw++) {
       const size_t sm2 = seq2_smem<N, M, T>(p, pw);
       if (sm2 > 220 * 1024) continue;
@@ -1476,7 +1651,7 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
       if (per2 < 1) continue;
       char nm[64];
       std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
-      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, sm2, nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, sm2, nsm, nm});
     }
   }
   return ME_OK;
@@ -1844,7 +2019,7 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
     else                                                                                       \
       k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
           fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total,          \
-          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split, cd.spec);              \
+          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups); \
     st = ME_OK;                                                                                \
   }
   ME_SEQ_NMT(X)
