@@ -180,6 +180,32 @@ def oracle_sample(frames, n_pairs: int, threads: int):
     return (time.perf_counter() - t0) / n_pairs
 
 
+def parse_tune_log(text: str) -> list:
+    """me_tune_log lines as dicts: shape, whether timed, the model's and the
+    chosen form, and every candidate form's best time in ms."""
+    out = []
+    for ln in text.splitlines():
+        head, _, rest = ln.partition(" | ")
+        if not rest:
+            continue
+        what, _, choice = head.rpartition(": ")
+        kind = "tuned" if what.endswith(" tuned") else "modelled"
+        what = what.rsplit(" ", 1)[0]
+        model = choice.split(" chosen=")[0].replace("model=", "")
+        chosen = choice.split(" chosen=")[1] if " chosen=" in choice else model
+        times = {}
+        for c in (head.split(" | ")[1:] + rest.split(" | ")):
+            name, _, t = c.strip().rpartition(" ")
+            if name.endswith(" ms") or t == "ms":
+                name, _, t = name.rpartition(" ")
+            try:
+                times[name] = float(t)
+            except ValueError:
+                pass
+        out.append({"shape": what, "kind": kind, "model": model, "chosen": chosen, "ms": times})
+    return out
+
+
 def cpu_model() -> str:
     """The host CPU's model name (x86 /proc/cpuinfo, else lscpu on Arm)."""
     try:
@@ -473,6 +499,7 @@ class ServeRig:
 
 SERVE_WORKLOAD = "serve: 200 streams CIF p16 50% / 720p p32 35% / 1080p p32 15%, Poisson arrivals, budget 40 GB"
 SERVE_SWEEP = (2000, 4000, 6000, 8000, 10000, 12000)
+SERVE_BEYOND = (16000, 20000, 24000, 32000)   # past the configured range, to find saturation
 
 
 def run_serve(args):
@@ -483,13 +510,20 @@ def run_serve(args):
     rig = ServeRig()
     if args.rate_sweep:
         curve = [rig.run(r, args.seconds) for r in SERVE_SWEEP]
+        beyond = []
+        for r in SERVE_BEYOND:
+            c = rig.run(r, args.seconds)
+            beyond.append(c)
+            if c["saturated"] or not c["submit_kept_up"]:
+                break
         rig.close()
-        kept = [c["offered_rate"] for c in curve if not c["saturated"]]
+        kept = [c["offered_rate"] for c in curve + beyond if not c["saturated"] and c["submit_kept_up"]]
         line = {"metric": "serving: frames/s and latency vs offered rate (continuous batching, 200 streams)",
                 "value": max(c["frames_per_s"] for c in curve), "unit": "frames/s", "n_gpus": 1,
                 "higher_is_better": True, "dtype": "u8", "data": "synthetic",
                 "config": {"workload": SERVE_WORKLOAD + f", {args.seconds:.1f} s per rate"},
-                "highest_rate_kept_up": max(kept) if kept else None, "curve": curve}
+                "highest_rate_kept_up": max(kept) if kept else None, "curve": curve,
+                "beyond_configured_range": beyond}
     else:
         r = rig.run(args.rate, args.seconds)
         rig.close()
@@ -805,6 +839,10 @@ def main():
         legs["serve"] = dict(rig.run(4000.0, 3.0, gpu_index), workload=SERVE_WORKLOAD)
         rig.close()
 
+    # the autotuner's record for the shapes this run used: model's and chosen
+    # launch form and every candidate's time (first call of each shape)
+    tuning = parse_tune_log(me.me_tune_log())
+
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         thr = cpu_threads()
@@ -888,6 +926,7 @@ def main():
         "gpu_launches": 4 * args.steps,   # k_fsbm_pipe; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
+        "tuning": tuning,
         **legs,
     }
     print(json.dumps(line))

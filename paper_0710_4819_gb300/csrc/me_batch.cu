@@ -199,11 +199,11 @@ int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
   return ME_OK;
 }
 
-int launch_fsbm_tab_step(BCtrl* ctrl, int epoch, const BShape* shapes, const BStream* streams,
-                         const BFsEntry* ent, int nent, cudaStream_t s) {
+int launch_fsbm_tab_step(int N, int M, BCtrl* ctrl, int epoch, const BShape* shapes,
+                         const BStream* streams, const BFsEntry* ent, int nent, cudaStream_t s) {
   k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
   ME_CUDA(cudaGetLastError());
-  return launch_pipe_tab_batch(shapes, streams, ent, nent, &ctrl->next, &ctrl->error, s);
+  return launch_pipe_tab_batch(N, M, shapes, streams, ent, nent, &ctrl->next, &ctrl->error, s);
 }
 
 static int batch_finalize(me_batch* b) {
@@ -229,10 +229,10 @@ static int batch_finalize(me_batch* b) {
   b->smem_fs = smem_fs;
   // groups of the pipelined search, largest work first
   b->fsent_tab.clear();
-  if (b->N == 16 && b->M == 16 && pipe_tab_applies(16, 16, 1)) {
+  if (pipe_tab_applies(b->N, b->M, 1)) {
     for (int si = 0; si < (int)b->shapes.size(); si++) {
       const BShape& s = b->shapes[si];
-      const int BW = s.W / 16, BH = s.H / 16, bpc = pipe_tab_bpc(s.p);
+      const int BW = s.W / b->N, BH = s.H / b->M, bpc = pipe_tab_bpc(b->N, s.p);
       for (int by = 0; by < BH; by++)
         for (int bx0 = 0; bx0 < BW; bx0 += bpc)
           b->fsent_tab.push_back(BFsEntry{si, by, bx0, std::min(bpc, BW - bx0), 0});
@@ -373,8 +373,8 @@ static std::vector<std::string> batch_forms(const me_batch* b, int mode) {
 static int batch_enqueue(me_batch* b, int mode, int c, cudaStream_t s) {
   if (mode == ME_MODE_FSBM) {
     if (c == 1)
-      return launch_fsbm_tab_step(b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent_tab,
-                                  (int)b->fsent_tab.size(), s);
+      return launch_fsbm_tab_step(b->N, b->M, b->d_ctrl, 0, b->d_shapes, b->d_streams,
+                                  b->d_fsent_tab, (int)b->fsent_tab.size(), s);
     return launch_fsbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent,
                             (int)b->fsent.size(), b->smem_fs, s);
   }

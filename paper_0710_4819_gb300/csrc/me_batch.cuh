@@ -396,11 +396,11 @@ int launch_fsbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
                      const BStream* streams, const BFsEntry* ent, int nent, size_t smem,
                      cudaStream_t s);
 
-// Enqueues one FSBM step of 16x16 streams through the pipelined search at
-// any p (begin kernel + k_fsbm_pipe_tab over the group table `ent`, groups of
-// at most pipe_tab_bpc(p) blocks, claimed from ctrl->next).
-int launch_fsbm_tab_step(BCtrl* ctrl, int epoch, const BShape* shapes, const BStream* streams,
-                         const BFsEntry* ent, int nent, cudaStream_t s);
+// Enqueues one FSBM step through the pipelined search at any p (begin kernel
+// + k_fsbm_pipe_tab over the group table `ent`, groups of at most
+// pipe_tab_bpc(N, p) blocks, claimed from ctrl->next).
+int launch_fsbm_tab_step(int N, int M, BCtrl* ctrl, int epoch, const BShape* shapes,
+                         const BStream* streams, const BFsEntry* ent, int nent, cudaStream_t s);
 
 // Run lengths worth timing for a set of streams: batch_choose_T's and those
 // whose modelled waste is within 10 % of it (model first).

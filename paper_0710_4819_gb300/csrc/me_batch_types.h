@@ -36,16 +36,18 @@ struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block
   int stream, by, bx0, nb, G;
 };
 
-// The pipelined full search of 16x16 blocks at any p <= 64 (k_fsbm_pipe_tab):
-// groups of pipe_tab_bpc(p) adjacent blocks of one block row.  The batch form
-// takes the batch's stream tables and a group table (nb <= pipe_tab_bpc of
-// the stream's p), claims groups from *ctr (zero before the launch) and
-// reports a wait that gave up in *err.
+// The pipelined full search at any p <= 64 (k_fsbm_pipe_tab): groups of
+// pipe_tab_bpc(N, p) adjacent blocks of one block row.  The batch form takes
+// the batch's stream and group tables (nb <= pipe_tab_bpc of the stream's
+// p), claims groups from *ctr (zero before the launch) and reports a wait
+// that gave up in *err.
 bool pipe_tab_applies(int N, int M, int p);
-int pipe_tab_bpc(int p);
-int launch_pipe_tab_seq(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
-                        int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s);
-int launch_pipe_tab_batch(const BShape* shp, const BStream* st, const BFsEntry* ent, int nent,
-                          int* ctr, int* err, cudaStream_t s);
+int pipe_tab_bpc(int N, int p);
+int pipe_tab_T(int N, int M);
+int launch_pipe_tab_seq(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+                        uint32_t lam, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out,
+                        cudaStream_t s);
+int launch_pipe_tab_batch(int N, int M, const BShape* shp, const BStream* st, const BFsEntry* ent,
+                          int nent, int* ctr, int* err, cudaStream_t s);
 
 }  // namespace me

@@ -408,13 +408,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
 
 // ------------------------------------------------------------------ pipelined search, any p
 //
-// The pipelined full search for 16x16 blocks at every search range p <= 64,
-// driven by a table of block groups: the same producer/consumer pipeline as
-// k_fsbm_pipe (4 producer warps stage a group into one of two shared buffers
-// while 12 consumer warps search the other), with a fixed shifted-word pitch
-// of kTabSP = 157 words and buffers of kTabRows = 145 rows, enough for a
-// group of tab_bpc(p) blocks (8 at p <= 16, 6 at p <= 32, 4 at p <= 48, 2 at
-// p <= 64) with the 13-row runs.  Groups come from one of two sources:
+// The pipelined full search for every block shape at every search range
+// p <= 64, driven by a table of block groups: the same producer/consumer
+// pipeline as k_fsbm_pipe (4 producer warps stage a group into one of two
+// shared buffers while 12 consumer warps search the other), with a fixed
+// shifted-word pitch of kTabSP = 157 words and buffers of TabCfg::R rows
+// (enough for p = 64), holding a group of tab_bpc(p) adjacent blocks (16x16:
+// 8 at p <= 16, 6 at p <= 32, 4 at p <= 48, 2 at p <= 64; narrower blocks
+// more).  Runs of 13 rows for 16x16 blocks, 8 for the other shapes.  Groups
+// come from one of two sources:
 //   - a sequence of K pairs (frames[k] -> frames[k+1]) of one shape, groups
 //     dealt to CTAs round robin;
 //   - a batch of streams of any sizes and ranges (the batch API's stream and
@@ -422,13 +424,20 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
 // The tables of costs per row depend on p and lambda, so the producers stage
 // them with each group.
 constexpr int kTabSP = 157;
-constexpr int kTabRows = 145;   // 10 runs of 13 rows + 15
-constexpr int kTabB = 8;
-constexpr int kTabT = 13;
 
+template <int N, int M>
+struct TabCfg {
+  static constexpr int T = (N == 16 && M == 16) ? 13 : 8;              // run length
+  static constexpr int B = 128 / N;                                    // blocks per group, at most
+  static constexpr int R = ((2 * kMaxP + 1 + T - 1) / T) * T + M - 1;  // rows at p = 64
+  static constexpr int WBW = (kTabSP + 6) / 4 + 1;                     // raw words per row
+  static constexpr int BST = B * M * (N / 4) + 3 * R + R * kTabSP;     // words per buffer
+};
+
+template <int N>
 __host__ __device__ inline int tab_bpc(int p) {
-  const int b = (kTabSP - (2 * p + 1) - 12) / 16 + 1;
-  return b < kTabB ? b : kTabB;
+  const int b = (kTabSP - (2 * p + 1) - (N - 4)) / N + 1;
+  return b < 128 / N ? b : 128 / N;
 }
 
 struct TabArgs {
@@ -460,10 +469,11 @@ struct TabGroup {
   uint32_t lam;
 };
 
+template <int N, int M>
 __device__ __forceinline__ TabGroup tab_group(const TabArgs& A, int gi) {
   TabGroup G;
   if (A.shp == nullptr) {
-    const int BW = A.W / 16, BH = A.H / 16, bpc = tab_bpc(A.p);
+    const int BW = A.W / N, BH = A.H / M, bpc = tab_bpc<N>(A.p);
     const int gpr = (BW + bpc - 1) / bpc;
     const int k = gi / (BH * gpr), rem = gi - k * (BH * gpr);
     const int by = rem / gpr, bx0 = (rem - by * gpr) * bpc;
@@ -476,8 +486,8 @@ __device__ __forceinline__ TabGroup tab_group(const TabArgs& A, int gi) {
     G.H = A.H;
     G.p = A.p;
     G.lam = A.lam;
-    G.x0 = bx0 * 16;
-    G.y0 = by * 16;
+    G.x0 = bx0 * N;
+    G.y0 = by * M;
     G.nb = min(bpc, BW - bx0);
     G.obase = (long long)k * BW * BH + (long long)by * BW + bx0;
   } else {
@@ -493,29 +503,32 @@ __device__ __forceinline__ TabGroup tab_group(const TabArgs& A, int gi) {
     G.H = s.H;
     G.p = s.p;
     G.lam = a.lam;
-    G.x0 = e.bx0 * 16;
-    G.y0 = e.by * 16;
+    G.x0 = e.bx0 * N;
+    G.y0 = e.by * M;
     G.nb = e.nb;
-    G.obase = (long long)e.by * (s.W / 16) + e.bx0;
+    G.obase = (long long)e.by * (s.W / N) + e.bx0;
   }
   return G;
 }
 
-template <int T>
+template <int T, int M>
 __host__ __device__ inline int tab_rows(int p) {
-  return ((2 * p + 1 + T - 1) / T) * T + 15;
+  return ((2 * p + 1 + T - 1) / T) * T + M - 1;
 }
 
+template <int N, int M>
 __host__ __device__ inline size_t tab_smem_bytes() {
-  constexpr int WBW = (kTabSP + 6) / 4 + 1;
-  return 4 * ((size_t)kTabRows * WBW + 2 * ((size_t)kTabB * 64 + 3 * kTabRows + (size_t)kTabRows * kTabSP));
+  using C = TabCfg<N, M>;
+  return 4 * ((size_t)C::R * C::WBW + 2 * (size_t)C::BST);
 }
 
+template <int N, int M>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
-  constexpr int N = 16, M = 16, NW = 4, T = kTabT, SP = kTabSP, R = kTabRows, B = kTabB;
-  constexpr int WBW = (SP + 6) / 4 + 1;
+  using C = TabCfg<N, M>;
+  constexpr int NW = N / 4, T = C::T, SP = kTabSP, R = C::R, B = C::B;
+  constexpr int WBW = C::WBW;
   constexpr int PT = 32 * kPipeProducers, CT = 32 * kPipeConsumers;
-  constexpr int BST = B * M * NW + 3 * R + R * SP;   // words per buffer
+  constexpr int BST = C::BST;   // words per buffer
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long red[2][B];
   __shared__ TabGroup grp[2];
@@ -577,12 +590,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
       const int gi = claim_s;
       if (i >= 2 && !finish(i - 2)) { ok = false; break; }   // (its barriers order claim_s)
       if (gi >= A.ngroups) break;
-      const TabGroup G = tab_group(A, gi);
+      const TabGroup G = tab_group<N, M>(A, gi);
       if (pt == 0) {
         grp[b] = G;
         gid_s[b] = gi;
       }
-      const int p = G.p, n = 2 * p + 1, rows = tab_rows<T>(p);
+      const int p = G.p, n = 2 * p + 1, rows = tab_rows<T, M>(p);
       const int pos = (G.nb - 1) * N + n + N - 4;
       uint32_t* cw = buf0 + b * BST;
       uint32_t* tabJ = cw + B * M * NW;
@@ -1803,46 +1816,60 @@ int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, 
 bool pipe_tab_applies(int N, int M, int p) {
   const char* pe = std::getenv("ME_FSBM_PIPE");
   if (pe && pe[0] == '0') return false;
-  return N == 16 && M == 16 && p >= 1 && p <= kMaxP && tab_rows<kTabT>(p) <= kTabRows;
+  return (N == 4 || N == 8 || N == 16) && (M == 4 || M == 8 || M == 16) && p >= 1 && p <= kMaxP;
 }
 
-int pipe_tab_bpc(int p) { return tab_bpc(p); }
+int pipe_tab_bpc(int N, int p) {
+  return N == 16 ? tab_bpc<16>(p) : N == 8 ? tab_bpc<8>(p) : tab_bpc<4>(p);
+}
 
-static int launch_pipe_tab(const TabArgs& A, int grid, cudaStream_t s) {
-  const size_t smem = tab_smem_bytes();
-  const int st = ensure_dynamic_smem((const void*)k_fsbm_pipe_tab, smem);
+int pipe_tab_T(int N, int M) { return N == 16 && M == 16 ? TabCfg<16, 16>::T : TabCfg<8, 8>::T; }
+
+template <int N, int M>
+static int launch_pipe_tab_t(const TabArgs& A, int grid, cudaStream_t s) {
+  const size_t smem = tab_smem_bytes<N, M>();
+  const int st = ensure_dynamic_smem((const void*)k_fsbm_pipe_tab<N, M>, smem);
   if (st) return st;
   if (grid < 1) return ME_OK;
-  k_fsbm_pipe_tab<<<grid, kPipeThreads, smem, s>>>(A);
+  k_fsbm_pipe_tab<N, M><<<grid, kPipeThreads, smem, s>>>(A);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
-int launch_pipe_tab_seq(const uint8_t* const* frames, int K, int W, int H, int p, uint32_t lam,
-                        int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
-  if (K < 1 || K > kSeqMax || !pipe_tab_applies(16, 16, p)) return ME_ERR_ARG;
+static int launch_pipe_tab(int N, int M, const TabArgs& A, int grid, cudaStream_t s) {
+#define X(n_, m_) \
+  if (N == n_ && M == m_) return launch_pipe_tab_t<n_, m_>(A, grid, s);
+  X(16, 16) X(16, 8) X(16, 4) X(8, 16) X(8, 8) X(8, 4) X(4, 16) X(4, 8) X(4, 4)
+#undef X
+  return ME_ERR_ARG;
+}
+
+int launch_pipe_tab_seq(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
+                        uint32_t lam, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out,
+                        cudaStream_t s) {
+  if (K < 1 || K > kSeqMax || !pipe_tab_applies(N, M, p)) return ME_ERR_ARG;
   TabArgs A;
   std::memset(&A, 0, sizeof(A));
   for (int k = 0; k <= K; k++) A.fr.f[k] = frames[k];
   A.W = W; A.H = H; A.p = p; A.K = K; A.lam = lam;
   A.mv = mv_out; A.J = J_out; A.sad = sad_out;
-  const int BW = W / 16, BH = H / 16, bpc = tab_bpc(p);
+  const int BW = W / N, BH = H / M, bpc = pipe_tab_bpc(N, p);
   A.ngroups = K * BH * ((BW + bpc - 1) / bpc);
   A.lim = wait_cycles(1000000000ll);
   int nsm = 1;
   { const int e = sm_count(&nsm); if (e) return e; }
-  return launch_pipe_tab(A, std::min(nsm, A.ngroups), s);
+  return launch_pipe_tab(N, M, A, std::min(nsm, A.ngroups), s);
 }
 
-int launch_pipe_tab_batch(const BShape* shp, const BStream* st, const BFsEntry* ent, int nent,
-                          int* ctr, int* err, cudaStream_t s) {
+int launch_pipe_tab_batch(int N, int M, const BShape* shp, const BStream* st, const BFsEntry* ent,
+                          int nent, int* ctr, int* err, cudaStream_t s) {
   TabArgs A;
   std::memset(&A, 0, sizeof(A));
   A.shp = shp; A.st = st; A.ent = ent; A.ngroups = nent; A.ctr = ctr; A.err = err;
   A.lim = wait_cycles(1000000000ll);
   int nsm = 1;
   { const int e = sm_count(&nsm); if (e) return e; }
-  return launch_pipe_tab(A, std::min(nsm, nent), s);
+  return launch_pipe_tab(N, M, A, std::min(nsm, nent), s);
 }
 
 // ------------------------------------------------------------------ tuned full search
@@ -1888,14 +1915,19 @@ static FsTune* fs_tune_entry(int dev, int W, int H, int N, int M, int p, int K) 
         t->cands.push_back(FsTune::Cand{T, FsPlan{T, 0, 0, 0, 1}, nm});
       }
   }
-  if (pipe_tab_applies(N, M, p)) {
-    std::snprintf(nm, sizeof(nm), "pipetab B=%d", tab_bpc(p));
-    t->cands.push_back(FsTune::Cand{-1, FsPlan{kTabT, 0, 0, 0, 1}, nm});
-  }
+  // the any-p pipeline: the model's form for 16x16 blocks past the other
+  // pipeline's ranges; after the per-group plans for the other shapes (whose
+  // short runs it feeds less well: 8x8 at 1080p p=32 measured 1.11 ms for 4
+  // pairs against 0.95 ms for the best per-group plan)
+  const bool tab = pipe_tab_applies(N, M, p), tab_first = tab && N == 16 && M == 16;
+  std::snprintf(nm, sizeof(nm), "pipetab B=%d", pipe_tab_bpc(N, p));
+  const FsTune::Cand tabc{-1, FsPlan{pipe_tab_T(N, M), 0, 0, 0, 1}, nm};
+  if (tab_first) t->cands.push_back(tabc);
   for (const FsPlan& pl : fs_plans_ranked(N, M, p, W / N, pipe ? 2 : 3)) {
     std::snprintf(nm, sizeof(nm), "group T=%d G=%d thr=%d", pl.T, pl.G, pl.threads);
     t->cands.push_back(FsTune::Cand{0, pl, nm});
   }
+  if (tab && !tab_first) t->cands.push_back(tabc);
   g_fst.push_back(t);
   return t;
 }
@@ -1904,7 +1936,7 @@ static int fs_seq_enqueue(const FsTune::Cand& cd, const uint8_t* const* frames, 
                           int H, int N, int M, int p, uint32_t lam, int16_t* mv_out,
                           uint32_t* J_out, uint32_t* sad_out, cudaStream_t s) {
   if (cd.pipeT < 0)
-    return launch_pipe_tab_seq(frames, K, W, H, p, lam, mv_out, J_out, sad_out, s);
+    return launch_pipe_tab_seq(frames, K, W, H, N, M, p, lam, mv_out, J_out, sad_out, s);
   if (cd.pipeT > 0) {
     PipeOut o;
     std::memset(&o, 0, sizeof(o));

@@ -61,7 +61,10 @@ class _Force:
 
 
 @pytest.mark.parametrize("w,h,N,M,p,K", [(352, 288, 16, 16, 16, 3), (208, 96, 8, 8, 7, 2),
-                                         (176, 144, 16, 8, 12, 1)])
+                                         (176, 144, 16, 8, 12, 1), (128, 64, 4, 4, 40, 1),
+                                         (96, 64, 4, 16, 64, 2), (160, 48, 8, 4, 33, 1),
+                                         (112, 96, 16, 4, 20, 2), (96, 112, 8, 16, 50, 1),
+                                         (64, 80, 4, 8, 9, 2), (192, 64, 16, 16, 64, 1)])
 def test_every_fsbm_candidate_gives_the_oracle(me, orc, w, h, N, M, p, K):
     import torch
     seq = synth.scene_sequence(300 + w + N + p, w, h, K + 1, n_objects=4, vmax=5)
