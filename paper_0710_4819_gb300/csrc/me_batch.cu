@@ -134,7 +134,7 @@ size_t acbm_step_smem(int N, int M, int T, int p_max) {
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
-                     unsigned long long* items, unsigned long long* q, cudaStream_t s) {
+                     unsigned long long* items, unsigned long long* q, cudaStream_t s, int spec) {
   int nsm = 1;
   { const int e = sm_count(&nsm); if (e) return e; }
   k_batch_begin<<<1, 256, 0, s>>>(ctrl, epoch);
@@ -169,7 +169,7 @@ int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* 
     if (st == ME_OK && grid < 2 * nsm) st = ME_ERR_CUDA;  /* needs two CTAs per SM */         \
     if (st == ME_OK)                                                                           \
       k_acbm_persist<n_, m_, t_><<<2 * nsm, kBatchThreads, smem, s>>>(                         \
-          shapes, streams, items, total_items, ctrl, q, pw, ww, nsm, nstreams);                \
+          shapes, streams, items, total_items, ctrl, q, pw, ww, nsm, nstreams, spec);          \
   }
   ME_BATCH_NMT(X)
 #undef X
@@ -279,7 +279,7 @@ static int batch_finalize(me_batch* b) {
   const size_t o_fsent_tab = take(sizeof(BFsEntry) * std::max<size_t>(1, b->fsent_tab.size()));
   const size_t o_items = take(8 * (size_t)std::max(1, b->total_items));
   const size_t o_q = take(8 * (size_t)std::max(1, b->total_items));
-  std::vector<size_t> o_pad(n), o_intra(n), o_flags(n);
+  std::vector<size_t> o_pad(n), o_intra(n), o_flags(n), o_bkey(n), o_bstate(n);
   b->total_pad = 0;
   b->total_blocks = 0;
   for (size_t i = 0; i < n; i++) {
@@ -288,6 +288,8 @@ static int batch_finalize(me_batch* b) {
     o_pad[i] = take((size_t)s.pg.pitch * s.pg.rows);
     o_intra[i] = take(4 * (size_t)nb);
     o_flags[i] = take(8 * (size_t)nb);
+    o_bkey[i] = take(8 * (size_t)nb);
+    o_bstate[i] = take(4 * (size_t)nb);
     s.pad_base = b->total_pad;
     s.blk_base = b->total_blocks;
     b->total_pad += (long long)s.pg.rows * (s.pg.pitch / 16);
@@ -300,6 +302,8 @@ static int batch_finalize(me_batch* b) {
     b->shapes[i].refpad = base8 + o_pad[i];
     b->shapes[i].intra = reinterpret_cast<uint32_t*>(base8 + o_intra[i]);
     b->shapes[i].flags = reinterpret_cast<unsigned long long*>(base8 + o_flags[i]);
+    b->shapes[i].bkey = reinterpret_cast<unsigned long long*>(base8 + o_bkey[i]);
+    b->shapes[i].bstate = reinterpret_cast<int*>(base8 + o_bstate[i]);
   }
   b->d_ctrl = reinterpret_cast<BCtrl*>(base8 + o_ctrl);
   b->d_shapes = reinterpret_cast<BShape*>(base8 + o_shapes);
@@ -361,10 +365,12 @@ static std::vector<std::string> batch_forms(const me_batch* b, int mode) {
     names.push_back(nm);
     if (!b->fsent_tab.empty()) names.push_back("pipetab");
   } else {
-    for (int T : b->acbm_Ts) {
-      std::snprintf(nm, sizeof(nm), "persist T=%d", T);
-      names.push_back(nm);
-    }
+    // each run length with speculative searches, then without
+    for (int spec = 1; spec >= 0; spec--)
+      for (int T : b->acbm_Ts) {
+        std::snprintf(nm, sizeof(nm), "persist T=%d spec=%d", T, spec);
+        names.push_back(nm);
+      }
   }
   return names;
 }
@@ -378,10 +384,12 @@ static int batch_enqueue(me_batch* b, int mode, int c, cudaStream_t s) {
     return launch_fsbm_step(b->N, b->M, b->T, b->d_ctrl, 0, b->d_shapes, b->d_streams, b->d_fsent,
                             (int)b->fsent.size(), b->smem_fs, s);
   }
-  return launch_acbm_step(b->N, b->M, b->acbm_Ts[c], b->d_ctrl, 0, b->d_shapes, b->d_streams,
+  const int nT = (int)b->acbm_Ts.size();
+  const int ti = c % nT, spec = c < nT ? 1 : 0;
+  return launch_acbm_step(b->N, b->M, b->acbm_Ts[ti], b->d_ctrl, 0, b->d_shapes, b->d_streams,
                           (int)b->shapes.size(), b->total_pad, b->total_blocks, b->d_segs,
-                          (int)b->segs.size(), b->total_items, b->acbm_smem[c], b->p_max,
-                          b->d_items, b->d_q, s);
+                          (int)b->segs.size(), b->total_items, b->acbm_smem[ti], b->p_max,
+                          b->d_items, b->d_q, s, spec);
 }
 
 }  // namespace me

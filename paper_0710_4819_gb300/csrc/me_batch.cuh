@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(256) k_batch_intra(const BShape* __restrict__ 
     const BShape& s = shp[lo];
     const int b = g - s.blk_base, BW = s.W / N;
     const uint32_t v = warp_intra_sad<N, M>(st[lo].cur, s.W, (b % BW) * N, (b / BW) * M);
-    if (lane == 0) s.intra[b] = v;
+    if (lane == 0) {
+      s.intra[b] = v;
+      if (s.bstate) s.bstate[b] = 0;
+    }
   }
 }
 
@@ -180,6 +183,29 @@ __host__ __device__ inline int batch_pbm_warps(int N, int M, int p) {
   return w < 1 ? 1 : (w > kBatchThreads / 32 ? kBatchThreads / 32 : w);
 }
 
+// Speculative full searches of the ACBM step: the queue word carries
+// kBatchSpecBit beside the claim index; the block's state word (BShape
+// bstate, cleared by the Intra_SAD prologue) collects kBatchSearched (the
+// key is in bkey) and kBatchFailed (PBM failed): whichever comes second
+// publishes the full-search result.
+constexpr int kBatchSpecBit = 1 << 30;
+constexpr int kBatchSearched = 1, kBatchFailed = 2;
+
+// Publishes block b of stream si with a full-search key (flag first: it
+// carries the vector; the host-chosen fault block never publishes its flag).
+__device__ __forceinline__ void batch_publish_fs(const BShape& s, const BStream& a, BCtrl* ctrl,
+                                                 int epoch, int si, int b, unsigned long long key) {
+  const Decoded d = decode_key(key, s.p, a.lam);
+  if (!(si == ctrl->skip_stream && b == ctrl->skip_block))
+    atomicExch(s.flags + b, pub_word(epoch, d.mvx, d.mvy));
+  a.mv[2 * b] = (int16_t)d.mvx;
+  a.mv[2 * b + 1] = (int16_t)d.mvy;
+  a.J[b] = d.J;
+  a.mask[b] = 1;
+  if (a.sad) a.sad[b] = d.sad;
+  if (a.load) a.load[b] = (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
+}
+
 // ACBM step over many streams, two roles in one launch (cta_role: one CTA of
 // each per SM).  PBM CTAs: every warp
 // claims blocks on its own, in wave order across streams (the item table maps
@@ -200,10 +226,10 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
                                                          int total, BCtrl* ctrl,
                                                          unsigned long long* __restrict__ q,
                                                          int pbm_warps, int win_words, int nsm,
-                                                         int nstreams) {
+                                                         int nstreams, int spec) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
-  __shared__ int s_role;
+  __shared__ int s_role, s_spec;
   __shared__ unsigned long long s_item;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -241,14 +267,13 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       // the zero vector
       int cx = 0, cy = 0;
       bool valid = false;
+      int sflag = -1;   // spatial neighbour whose flag this lane waits for
       if (lane < 4) {
         const int dx = (lane < 2) ? -1 : (lane == 2 ? 0 : 1);
         const int dy = (lane == 0) ? 0 : -1;
         const int nx = bx + dx, ny = by + dy;
         if (nx >= 0 && nx < BW && ny >= 0) {
-          const unsigned long long w = batch_wait(s.flags + ny * BW + nx, epoch, ctrl, timeout, i);
-          cx = pub_mvx(w);
-          cy = pub_mvy(w);
+          sflag = ny * BW + nx;
           valid = true;
         }
       } else if (lane < 13) {
@@ -264,8 +289,26 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         valid = true;
       }
       if (lane == 0 && nxt < total) inxt = items[nxt];
-      const PbmResult r = pbm_eval<N, M>(cx, cy, valid, wg, s.p, a.lam, ix, a.alpha, a.beta, a.gnum,
-                                         a.gden, a.qp, a.refine, curs, win);
+      // the previous field's and the zero predictors first (no wait); a block
+      // that fails both conditions with them alone has its full search queued
+      // at once (speculatively), while the warp waits for its spatial
+      // neighbours -- its result does not depend on the guess
+      const PbmPart pa = pbm_part_a<N, M>(cx, cy, valid, wg, s.p, a.lam, curs, win);
+      const bool sp = spec && s.bstate &&
+                      pbm_would_fail<N, M>(pa.best, s.p, a.lam, ix, a.alpha, a.beta, a.gnum, a.gden,
+                                           a.qp);
+      if (sp && lane == 0) {
+        const int slot = atomicAdd(&ctrl->fs_tail, 1);
+        atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)i |
+                                 kBatchSpecBit);
+      }
+      if (sflag >= 0) {
+        const unsigned long long w = batch_wait(s.flags + sflag, epoch, ctrl, timeout, i);
+        cx = pub_mvx(w);
+        cy = pub_mvy(w);
+      }
+      const PbmResult r = pbm_part_b<N, M>(cx, cy, valid, pa, wg, s.p, a.lam, ix, a.alpha, a.beta,
+                                           a.gnum, a.gden, a.qp, a.refine, curs, win);
       if (lane == 0) {
         if (r.pass) {
           // the flag word carries the vector: publish first, outputs after
@@ -278,13 +321,21 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
           a.mask[b] = 0;
           if (a.sad) a.sad[b] = d.sad;
           if (a.load) a.load[b] = (uint32_t)r.load;
+        } else if (sp) {
+          // the speculative search publishes if it finishes after this
+          // decision; if it finished before, its key is here to publish
+          if (atomicOr(s.bstate + b, kBatchFailed) & kBatchSearched) {
+            __threadfence();
+            batch_publish_fs(s, a, ctrl, epoch, si, b,
+                             *reinterpret_cast<volatile unsigned long long*>(s.bkey + b));
+          }
         } else {
           // queue entry = epoch and claim index in one word; the tail count is
           // ordered before this warp's pbm_done increment
           const int slot = atomicAdd(&ctrl->fs_tail, 1);
           atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)i);
-          __threadfence();
         }
+        __threadfence();
         atomicAdd(&ctrl->pbm_done, 1);
       }
       __syncwarp();
@@ -315,10 +366,13 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
           __nanosleep(32);
         }
         // a claim index beyond the table is not an item of this step
-        s_item = got < 0 ? ~0ull : (got < total ? items[got] : ~1ull);
+        const int ci = got & ~kBatchSpecBit;
+        s_item = got < 0 ? ~0ull : (ci < total ? items[ci] : ~1ull);
+        s_spec = got >= 0 && (got & kBatchSpecBit) != 0;
       }
       __syncthreads();
       const unsigned long long it = s_item;
+      const bool specj = s_spec != 0;
       if (it == ~0ull) break;
       const int si = (int)(it >> 32), b = (int)(uint32_t)it;
       if (it == ~1ull || si < 0 || si >= nstreams || b < 0 ||
@@ -337,15 +391,14 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       fs_group<N, M, T>(a.cur, a.ref, s.W, s.H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys,
                         nullptr, FsPad{s.refpad, s.pg.pitch, s.pg.P, s.pg.rows});
       if (tid == 0) {
-        const Decoded d = decode_key(keys[0], s.p, a.lam);
-        if (!(si == ctrl->skip_stream && b == ctrl->skip_block))
-          atomicExch(s.flags + b, pub_word(epoch, d.mvx, d.mvy));
-        a.mv[2 * b] = (int16_t)d.mvx;
-        a.mv[2 * b + 1] = (int16_t)d.mvy;
-        a.J[b] = d.J;
-        a.mask[b] = 1;
-        if (a.sad) a.sad[b] = d.sad;
-        if (a.load) a.load[b] = (uint32_t)((2 * s.p + 1) * (2 * s.p + 1));
+        bool pub = true;
+        if (specj) {
+          // published by this CTA only if the block has failed PBM already
+          s.bkey[b] = keys[0];
+          __threadfence();
+          pub = (atomicOr(s.bstate + b, kBatchSearched) & kBatchFailed) != 0;
+        }
+        if (pub) batch_publish_fs(s, a, ctrl, epoch, si, b, keys[0]);
       }
       __syncthreads();
     }
@@ -386,7 +439,8 @@ int batch_choose_T(int N, int M, const std::vector<BShape>& shapes);
 int launch_acbm_step(int N, int M, int T, BCtrl* ctrl, int epoch, const BShape* shapes,
                      const BStream* streams, int nstreams, long long total_pad, int total_blocks,
                      const BSegment* segs, int nseg, int total_items, size_t smem, int p_max,
-                     unsigned long long* items, unsigned long long* q, cudaStream_t s);
+                     unsigned long long* items, unsigned long long* q, cudaStream_t s,
+                     int spec = 0);
 
 // Dynamic shared memory of the ACBM step kernel for search ranges up to p_max.
 size_t acbm_step_smem(int N, int M, int T, int p_max);

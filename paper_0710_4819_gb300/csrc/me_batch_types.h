@@ -30,6 +30,10 @@ struct BShape {  // fixed per stream
   unsigned long long* flags;  // per block: epoch + final vector (pub_word)
   long long pad_base;  // first 16-byte chunk of this stream in the flat pad index
   int blk_base;        // first block of this stream in the flat block index
+  // speculative full searches of the ACBM step (null: none): per block the
+  // search's key and the state word (searched / PBM failed), cleared each step
+  unsigned long long* bkey;
+  int* bstate;
 };
 
 struct BFsEntry {  // FSBM: one group of adjacent blocks, G threads per block

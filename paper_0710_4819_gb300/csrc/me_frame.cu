@@ -123,15 +123,75 @@ __global__ void __launch_bounds__(256) k_acbm_prologue(AcbmArgs a, AcbmArgs* __r
   }
 }
 
+// The frame's likely fallbacks, searched before the wave chain: one CTA per
+// block; warp 0 stages the block's window and evaluates the PBM predictors
+// known before any wave runs (the previous field's 3x3 and the zero vector,
+// pbm_part_a); a block that already fails both conditions with them (it
+// nearly always fails with all of them) is searched in full by the whole CTA
+// and its key left in bkeys[b] with bdone[b] = kSpecDone, for the PBM wave to
+// publish if the block fails there.  The result never depends on the guess.
+constexpr int kSpecDone = -1;
+
+template <int N, int M, int T>
+__global__ void __launch_bounds__(256) k_acbm_spec(const AcbmArgs* __restrict__ ap,
+                                                   const uint8_t* __restrict__ refpad, PadGeom pg,
+                                                   const uint32_t* __restrict__ intra, int W, int H,
+                                                   int p, unsigned long long* __restrict__ bkeys,
+                                                   int* __restrict__ bdone) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long keys[16];
+  __shared__ int s_go;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const AcbmArgs a = *ap;
+  const int BW = W / N, BH = H / M, b = blockIdx.x;
+  const int bx = b % BW, by = b / BW;
+  if (warp == 0) {
+    uint32_t* win = smem;
+    uint32_t* curs = smem + pbm_win_words(N, M, p);
+    const PbmWin wg = pbm_stage<N, M>(a.cur, refpad, pg, W, p, bx * N, by * M, curs, win);
+    int cx = 0, cy = 0;
+    bool valid = false;
+    if (lane >= 4 && lane < 13) {
+      const int t = lane - 4, nx = bx + t % 3 - 1, ny = by + t / 3 - 1;
+      if (nx >= 0 && nx < BW && ny >= 0 && ny < BH) {
+        if (a.prev) {
+          cx = a.prev[2 * (ny * BW + nx)];
+          cy = a.prev[2 * (ny * BW + nx) + 1];
+        }
+        valid = true;
+      }
+    } else if (lane == 13) {
+      valid = true;
+    }
+    const PbmPart pa = pbm_part_a<N, M>(cx, cy, valid, wg, p, a.lam, curs, win);
+    if (lane == 0)
+      s_go = pbm_would_fail<N, M>(pa.best, p, a.lam, intra[b], a.alpha, a.beta, a.gnum, a.gden,
+                                  a.qp) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x);
+  fs_group<N, M, T>(a.cur, a.ref, W, H, bx * N, by * M, g, a.lam, smem, keys, nullptr,
+                    FsPad{refpad, pg.pitch, pg.P, pg.rows});
+  if (threadIdx.x == 0) {
+    bkeys[b] = keys[0];
+    bdone[b] = kSpecDone;
+  }
+}
+
 // ACBM, PBM stage of wave w: one warp per block of the wave.  Passing blocks
-// get their final outputs; failing ones are appended to the wave's list.
+// get their final outputs; failing ones take the result of their early full
+// search (k_acbm_spec) when there is one, else are appended to the wave's
+// list.
 template <int N, int M>
 __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ ap,
                                                   const uint8_t* __restrict__ refpad,
                                                   PadGeom pg, const uint32_t* __restrict__ intra,
                                                   int W, int H, int p, int w, int ylo, int count,
                                                   int* __restrict__ fail_count,
-                                                  int* __restrict__ fail_list) {
+                                                  int* __restrict__ fail_list,
+                                                  const unsigned long long* __restrict__ bkeys,
+                                                  const int* __restrict__ bdone) {
   __shared__ uint32_t curs[4][M * (N / 4)];
   extern __shared__ __align__(16) uint32_t wins[];   // 4 x pbm_win_words
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,6 +215,15 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
       a.mask[b] = 0;
       if (a.sad) a.sad[b] = d.sad;
       if (a.load) a.load[b] = (uint32_t)r.load;
+    } else if (bdone[b] == kSpecDone) {
+      const int n = 2 * p + 1;
+      const Decoded d = decode_key(bkeys[b], p, a.lam);
+      a.mv[2 * b] = (int16_t)d.mvx;
+      a.mv[2 * b + 1] = (int16_t)d.mvy;
+      a.J[b] = d.J;
+      a.mask[b] = 1;
+      if (a.sad) a.sad[b] = d.sad;
+      if (a.load) a.load[b] = (uint32_t)(n * n);
     } else {
       const int slot = atomicAdd(fail_count, 1);
       fail_list[slot] = b;
@@ -487,22 +556,49 @@ int launch_pad(const uint8_t* ref, int W, int H, int p, uint8_t* out, cudaStream
 template <int N, int M>
 static int launch_pbm_wave_t(const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
                              const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
-                             int* cnt, int* list, cudaStream_t s) {
+                             int* cnt, int* list, const unsigned long long* bkeys, const int* bdone,
+                             cudaStream_t s) {
   const size_t smem = 4 * 4 * (size_t)pbm_win_words(N, M, p);
   {
     const int st = ensure_dynamic_smem((const void*)k_pbm_wave<N, M>, smem);
     if (st) return st;
   }
   k_pbm_wave<N, M><<<(count + 3) / 4, 128, smem, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo,
-                                                      count, cnt, list);
+                                                      count, cnt, list, bkeys, bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
 static int launch_pbm_wave(int N, int M, const AcbmArgs* ap, const uint8_t* refpad,
                            const PadGeom& pg, const uint32_t* intra, int W, int H, int p, int w,
-                           int ylo, int count, int* cnt, int* list, cudaStream_t s) {
-  ME_DISPATCH_NM(launch_pbm_wave_t, ap, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, s);
+                           int ylo, int count, int* cnt, int* list,
+                           const unsigned long long* bkeys, const int* bdone, cudaStream_t s) {
+  ME_DISPATCH_NM(launch_pbm_wave_t, ap, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, bkeys,
+                 bdone, s);
+}
+
+template <int N, int M, int T>
+static int launch_spec_t(const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
+                         const uint32_t* intra, int W, int H, int p, unsigned long long* bkeys,
+                         int* bdone, cudaStream_t s) {
+  const FsGeom g = fs_geom<N, M, T>(p, 1, 256);
+  const size_t smem = std::max(fs_smem_bytes<N, M, T>(g),
+                               4 * ((size_t)pbm_win_words(N, M, p) + M * (N / 4)));
+  {
+    const int st = ensure_dynamic_smem((const void*)k_acbm_spec<N, M, T>, smem);
+    if (st) return st;
+  }
+  k_acbm_spec<N, M, T><<<(W / N) * (H / M), 256, smem, s>>>(ap, refpad, pg, intra, W, H, p, bkeys,
+                                                           bdone);
+  ME_CUDA(cudaGetLastError());
+  return ME_OK;
+}
+
+static int launch_spec(int N, int M, const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
+                       const uint32_t* intra, int W, int H, int p, unsigned long long* bkeys,
+                       int* bdone, cudaStream_t s) {
+  const FsPlan pl = fs_plan_latency(N, M, p);
+  ME_DISPATCH_FS(launch_spec_t, ap, refpad, pg, intra, W, H, p, bkeys, bdone, s);
 }
 
 template <int N, int M>
@@ -557,12 +653,14 @@ int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* 
   const Waves wv = make_waves(W / N, H / M);
   int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, cnt, wv.n, bkeys, bdone, s);
   if (st) return st;
+  st = launch_spec(N, M, slot, refpad, pg, intra, W, H, p, bkeys, bdone, s);
+  if (st) return st;
   int off = 0;
   for (int w = 0; w < wv.n; w++) {
     const int c = wv.count(w);
     if (c == 0) continue;
     st = launch_pbm_wave(N, M, slot, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w,
-                         list + off, s);
+                         list + off, bkeys, bdone, s);
     if (st) return st;
     st = launch_fs_list(N, M, slot, W, H, p, cnt + w, list + off, c, bkeys, bdone, s);
     if (st) return st;

@@ -142,3 +142,70 @@ def test_tuner_times_every_candidate_and_keeps_the_fastest(me):
                  for c in ln.split("|")[1:]}
         assert all(t > 0 for t in times.values()), ln
         assert times[chosen] == min(times.values()), ln
+
+
+def test_every_batch_step_form_gives_the_oracle(me, orc):
+    """The batch's step forms (FSBM: per-group persistent kernel, any-p
+    pipeline; ACBM: each run length with and without speculative searches),
+    each forced on a fresh batch of three uneven streams over two steps,
+    against the oracle (FSBM per pair, ACBM chained)."""
+    import torch
+    specs = [synth.StreamSpec("qcif", 176, 144, 16, 8101), synth.StreamSpec("cif", 352, 288, 16, 8102),
+             synth.StreamSpec("qcif", 176, 144, 32, 8103)]
+    seqs_np = [synth.stream_frames(s, 3) for s in specs]
+    seqs = [torch.from_numpy(x).cuda() for x in seqs_np]
+    lam = me.me_lambda_q8(28)
+    prm = me.params(qp=28)
+    want_f = [[orc.fsbm(x[t], x[t - 1], 16, 16, s.p, lam) for t in (1, 2)] for x, s in zip(seqs_np, specs)]
+    want_a = []
+    for x, s in zip(seqs_np, specs):
+        prev, w = None, []
+        for t in (1, 2):
+            out = orc.acbm(x[t], x[t - 1], 16, 16, s.p, lam, orc.params(qp=28), prev)
+            prev = out[0]
+            w.append(out)
+        want_a.append(w)
+    for mode, n_forms in ((0, 2), (1, 8)):
+        for c in range(n_forms):
+            with _Force(c):
+                b = me.Batch()
+                for s in specs:
+                    b.add_stream(s.w, s.height, 16, 16, s.p)
+                prev = [None] * len(specs)
+                for t in (1, 2):
+                    outs = []
+                    items = []
+                    for i, s in enumerate(specs):
+                        BH, BW = s.height // 16, s.w // 16
+                        o = dict(mv=torch.full((BH, BW, 2), -9, dtype=torch.int16, device="cuda"),
+                                 J=torch.full((BH, BW), -1, dtype=torch.int32, device="cuda"),
+                                 mask=torch.full((BH, BW), 9, dtype=torch.uint8, device="cuda"),
+                                 sad=torch.full((BH, BW), -1, dtype=torch.int32, device="cuda"),
+                                 load=torch.full((BH, BW), -1, dtype=torch.int32, device="cuda"))
+                        it = me.BatchItem()
+                        it.cur, it.ref = seqs[i][t].data_ptr(), seqs[i][t - 1].data_ptr()
+                        it.prev_mv = None if prev[i] is None else prev[i].data_ptr()
+                        it.mv_out, it.J_out, it.mask_out = o["mv"].data_ptr(), o["J"].data_ptr(), o["mask"].data_ptr()
+                        it.sad_out, it.load_out = o["sad"].data_ptr(), o["load"].data_ptr()
+                        it.lambda_q8 = lam
+                        it.prm = prm
+                        outs.append(o)
+                        items.append(it)
+                    b.run(mode, items)
+                    b.sync()
+                    for i in range(len(specs)):
+                        o = outs[i]
+                        if mode == 0:
+                            mv, J, sad = want_f[i][t - 1]
+                            checks = (("mv", o["mv"].cpu().numpy(), mv), ("J", _u32(o["J"]), J),
+                                      ("sad", _u32(o["sad"]), sad))
+                        else:
+                            mv, J, mask, sad, load = want_a[i][t - 1]
+                            checks = (("mv", o["mv"].cpu().numpy(), mv), ("J", _u32(o["J"]), J),
+                                      ("mask", o["mask"].cpu().numpy(), mask),
+                                      ("sad", _u32(o["sad"]), sad), ("load", _u32(o["load"]), load))
+                        for nm, g, w_ in checks:
+                            assert np.array_equal(g, w_), (mode, c, i, t, nm)
+                    if mode == 1:
+                        prev = [o["mv"] for o in outs]
+                b.close()
