@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-legs", action="store_true",
                     help="skip the batch64 and serve legs of the default line")
-    ap.add_argument("--workload", default="1080p", choices=["1080p", "batch64", "serve", "loadtable"],
+    ap.add_argument("--workload", default="1080p",
+                    choices=["1080p", "batch64", "serve", "loadtable", "configs"],
                     help="1080p: the default line; batch64 / serve: the multi-stream forms; "
                          "loadtable: ACBM load per block vs Qp on QCIF scenes (Table 1 layout)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
@@ -335,6 +336,84 @@ def run_batch64(args):
     print(json.dumps(line))
 
 
+def run_configs(args):
+    """Each single-stream workload (QCIF p=16, CIF p=16 at Qp 22/28/34/40,
+    1080p p=32) through the GPU sequence forms (FSBM and ACBM of all pairs,
+    one launch each; frames resident, L2 flushed, median of 5) beside the
+    oracle on a bounded sample of the same frames (FSBM on one thread and on
+    all host threads, ACBM on one thread: it is sequential per frame)."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_0710_4819_gb300 as me
+    thr = cpu_threads()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    lanes = me.me_sad_peak(0)[1]
+    rows = []
+    for name, p, frames_n, qps, sample in (("qcif", 16, 10, (28,), 3), ("cif", 16, 31, (22, 28, 34, 40), 2),
+                                            ("1080p", 32, 60, (28,), 1)):
+        seq = synth.config_sequence(name, seed=2026, n_frames=frames_n)
+        H, W = seq.shape[1:]
+        K = frames_n - 1
+        fr = torch.from_numpy(seq).cuda()
+        for qp in qps:
+            lam = me.me_lambda_q8(qp)
+            prm = me.params(qp=qp)
+            res = {}
+            clocks = ClockSampler(0)
+            clocks.start()
+            for key, fn in (("fsbm", lambda: me.me_fsbm_sequence(fr, N, M, p, lam)),
+                            ("acbm", lambda: me.me_acbm_sequence(fr, N, M, p, lam, prm))):
+                for _ in range(3):
+                    fn()
+                ts = []
+                for _ in range(5):
+                    flush.fill_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    fn()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                res[key] = statistics.median(ts) / K
+            ck = clocks.stop()
+            absd = (W // N) * (H // M) * (2 * p + 1) ** 2 * N * M
+            clk = ck.get("sm_mhz") or ck.get("sm_max_mhz") or 2070.0
+            peak = n_sm * 4 * lanes * clk * 1e6
+            olam = oracle.lambda_q8(qp)
+            t0 = time.perf_counter()
+            for t in range(1, sample + 1):
+                oracle.fsbm(seq[t], seq[t - 1], N, M, p, olam, nthreads=1)
+            f1 = (time.perf_counter() - t0) / sample
+            t0 = time.perf_counter()
+            for t in range(1, sample + 1):
+                oracle.fsbm(seq[t], seq[t - 1], N, M, p, olam, nthreads=thr)
+            fa = (time.perf_counter() - t0) / sample
+            t0 = time.perf_counter()
+            prev = None
+            for t in range(1, sample + 1):
+                prev = oracle.acbm(seq[t], seq[t - 1], N, M, p, olam, oracle.params(qp=qp), prev)[0]
+            a1 = (time.perf_counter() - t0) / sample
+            rows.append({"workload": f"{name} {W}x{H} 16x16 p={p} Qp={qp}", "pairs": K,
+                         "gpu_fsbm_ms_per_pair": res["fsbm"], "gpu_acbm_ms_per_pair": res["acbm"],
+                         "gpu_frames_per_s": 1e3 / (res["fsbm"] + res["acbm"]),
+                         "gpu_fsbm_frac_of_peak": absd / (res["fsbm"] * 1e-3) / peak,
+                         "oracle_fsbm_ms_1core": 1e3 * f1, "oracle_fsbm_ms_allcores": 1e3 * fa,
+                         "oracle_acbm_ms_1core": 1e3 * a1,
+                         "oracle_frames_per_s_1core": 1.0 / (f1 + a1),
+                         "oracle_frames_per_s_allcores": 1.0 / (fa + a1), "oracle_sample_pairs": sample,
+                         "sm_mhz": clk, "clock_reasons": ck.get("reasons")})
+    line = {"metric": "per-config frames/s: GPU sequence forms vs the oracle (1 core / all cores)",
+            "value": rows[-1]["gpu_frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "QCIF p16, CIF p16 at Qp 22/28/34/40, 1080p p32; 16x16"},
+            "cores": thr, "cpu_model": cpu_model(), "rows": rows}
+    print(json.dumps(line))
+
+
 LOAD_QPS = (30, 28, 26, 24, 22, 20, 18, 16)
 LOAD_P = 15                       # the paper's search range (961 + 8 half-pel = 969 positions)
 
@@ -542,7 +621,8 @@ def main():
         torch.cuda.set_device(0)
         import paper_0710_4819_gb300 as me
         me.load_library(build_if_missing=True)
-        {"batch64": run_batch64, "serve": run_serve, "loadtable": run_load_table}[args.workload](args)
+        {"batch64": run_batch64, "serve": run_serve, "loadtable": run_load_table,
+         "configs": run_configs}[args.workload](args)
         return
     rank, world, local, pg = dist_setup(args.gpus)
     import numpy as np
