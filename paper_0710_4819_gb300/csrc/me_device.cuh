@@ -80,6 +80,17 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
   return v;
 }
 
+// The same minimum in two 32-bit warp reductions (high word, then the low
+// word among the lanes holding the least high word).  Every lane of the warp
+// must call it.
+__device__ __forceinline__ unsigned long long warp_min64_redux(unsigned long long v) {
+  const unsigned hi = (unsigned)(v >> 32);
+  const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned lo = hi == mhi ? (unsigned)v : 0xffffffffu;
+  const unsigned mlo = __reduce_min_sync(0xffffffffu, lo);
+  return ((unsigned long long)mhi << 32) | mlo;
+}
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------------------

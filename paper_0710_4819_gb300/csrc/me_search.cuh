@@ -184,6 +184,14 @@ __device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_ev
   const int sa = atomicAdd(sm_arr + (smid & (kRoleSlots - 1)), 1);
   if (arr < 2) return arr;
   if (search_every > 0 && smid % (unsigned)search_every == 0) return 1;
+  if (search_every < 0) {
+    // segregated roles: whole SMs run PBM or searches, so PBM warps never
+    // share an SM's issue slots with the search warps' SAD loops.  -2: odd
+    // SMs search (half the SMs PBM); -3: every third SM searches (two
+    // thirds PBM)
+    const unsigned d = (unsigned)(-search_every);
+    return d == 2 ? (int)(smid & 1u) : (smid % d == 0 ? 1 : 0);
+  }
   return sa & 1;
 }
 
@@ -299,15 +307,29 @@ __device__ __forceinline__ void pbm_stamp(unsigned long long* tr, int i) {
   }
 }
 
+// The best candidate of a set: its key, vector and SAD (valid in every
+// lane; key kNoKey when the set was empty).
+struct PbmBest {
+  unsigned long long key;
+  int mvx, mvy;
+  uint32_t sad;
+};
+
+__device__ __forceinline__ PbmBest pbm_better(const PbmBest& a, const PbmBest& b) {
+  return b.key < a.key ? b : a;
+}
+
 // Candidates held by lanes (position ex, ey; act: to evaluate), each
 // candidate's rows split over `parts` lanes (2, 4 or 8, at most M): lane
 // c*parts + q sums rows q*M/parts .. (q+1)*M/parts-1 of the candidate held
-// by lane c.  Returns the warp's best key (every lane).
+// by lane c.  The minimum key is taken with two 32-bit warp reductions and
+// the winner's vector and SAD are read from its lane (no key decoding).  Not
+// inlined: the three calls share one copy, so the PBM code stays small and in
+// the instruction cache when other code has run on the SM.
 template <int N, int M>
-__device__ __forceinline__ unsigned long long pbm_eval_set(int ex, int ey, bool act, int parts,
-                                                           const PbmWin& wg, int p, uint32_t lam,
-                                                           const uint32_t* curs,
-                                                           const uint32_t* win) {
+__device__ __noinline__ PbmBest pbm_eval_set(int ex, int ey, bool act, int parts,
+                                                const PbmWin& wg, int p, uint32_t lam,
+                                                const uint32_t* curs, const uint32_t* win) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int c = lane / parts, q = lane - c * parts;
@@ -318,7 +340,14 @@ __device__ __forceinline__ unsigned long long pbm_eval_set(int ex, int ey, bool 
   const unsigned long long key =
       cact && q == 0 ? make_key(256u * s + lam * (uint32_t)(mv_bits(ccx) + mv_bits(ccy)), ccx, ccy, p)
                      : kNoKey;
-  return warp_min64(key);
+  PbmBest r;
+  r.key = warp_min64_redux(key);
+  const unsigned w = __ballot_sync(FULL, key == r.key && key != kNoKey);
+  const int src = w ? __ffs(w) - 1 : 0;
+  r.mvx = __shfl_sync(FULL, ccx, src);
+  r.mvy = __shfl_sync(FULL, ccy, src);
+  r.sad = __shfl_sync(FULL, s, src);
+  return r;
 }
 
 // PBM in two parts, so that the predictors known early can be evaluated
@@ -332,7 +361,7 @@ __device__ __forceinline__ unsigned long long pbm_eval_set(int ex, int ey, bool 
 // 1-3 (which lane evaluates a repeated position does not matter: its key is
 // the same).  Every lane passes its own predictor (cx, cy, valid).
 struct PbmPart {
-  unsigned long long best;
+  PbmBest best;
   int load;
 };
 
@@ -352,12 +381,9 @@ __device__ PbmPart pbm_part_a(int cx, int cy, bool valid, const PbmWin& wg, int 
   pbm_stamp(tr, 0);
   const bool mine = valid && lane >= 4 && lane < 14;
   const int code = pbm_code(cx, cy, mine, p);
-  bool dup = false;
-#pragma unroll 1
-  for (int l = 4; l < 14; l++) {
-    const int v = __shfl_sync(FULL, code, l);
-    dup |= (l < lane) && (v == code);
-  }
+  // repeated among lanes 4-13: an earlier lane of them holds the same code
+  const unsigned same = __match_any_sync(FULL, code);
+  const bool dup = (same & ((1u << lane) - 1u) & 0x3FF0u) != 0;
   const bool act = mine && !dup;
   PbmPart r;
   r.best = pbm_eval_set<N, M>(clampi(cx, -p, p), clampi(cy, -p, p), act, 2, wg, p, lam, curs, win);
@@ -377,51 +403,42 @@ __device__ PbmResult pbm_part_b(int cx, int cy, bool valid, const PbmPart& pa, c
   // one, or an earlier spatial one, is not evaluated again
   const bool is_pred = valid && lane < 14;
   const int code = pbm_code(cx, cy, is_pred, p);
-  bool dup = false;
-#pragma unroll 1
-  for (int l = 0; l < 14; l++) {
-    const int v = __shfl_sync(FULL, code, l);
-    dup |= (l >= 4 || l < lane) && l != lane && (v == code);
-  }
+  const unsigned same = __match_any_sync(FULL, code);
+  const bool dup = (same & (0x3FF0u | ((1u << lane) - 1u))) != 0;
   const bool actb = is_pred && lane < 4 && !dup;
-  unsigned long long best =
-      umin64(pa.best, pbm_eval_set<N, M>(clampi(cx, -p, p), clampi(cy, -p, p), actb,
-                                         M >= 8 ? 8 : 4, wg, p, lam, curs, win));
+  PbmBest best = pbm_better(pa.best, pbm_eval_set<N, M>(clampi(cx, -p, p), clampi(cy, -p, p), actb,
+                                                        M >= 8 ? 8 : 4, wg, p, lam, curs, win));
   int load = pa.load + __popc(__ballot_sync(FULL, actb));
   pbm_stamp(tr, 1);
   if (refine) {
     // every predictor's position has been evaluated (by its lane or by the
     // lane it repeats), so a ring position equal to any predictor's is skipped
     const int ecode = is_pred ? code : -1;
-    const Decoded d = decode_key(best, p, lam);
     int rcode = -100 - lane;
     int ex = 0, ey = 0;
     if (lane < 8) {
       const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
-      ex = clampi(d.mvx + o % 3 - 1, -p, p);
-      ey = clampi(d.mvy + o / 3 - 1, -p, p);
+      ex = clampi(best.mvx + o % 3 - 1, -p, p);
+      ey = clampi(best.mvy + o / 3 - 1, -p, p);
       rcode = ((ey + p) << 8) + (ex + p);
     }
     bool rdup = false;
-#pragma unroll 1
+#pragma unroll
     for (int l = 0; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
-#pragma unroll 1
-    for (int l = 0; l < 8; l++) {
-      const int v = __shfl_sync(FULL, rcode, l);
-      rdup |= (l < lane) && (v == rcode);
-    }
+    // repeated among the ring's own lanes: an earlier ring lane holds it
+    const unsigned rsame = __match_any_sync(FULL, rcode);
+    rdup |= (rsame & ((1u << lane) - 1u)) != 0;
     const bool act = lane < 8 && !rdup;
-    best = umin64(best, pbm_eval_set<N, M>(ex, ey, act, 4, wg, p, lam, curs, win));
+    best = pbm_better(best, pbm_eval_set<N, M>(ex, ey, act, 4, wg, p, lam, curs, win));
     load += __popc(__ballot_sync(FULL, act));
     pbm_stamp(tr, 2);
   }
   // Sec. 3.2 conditions in exact integers (intra_x = NM * Intra_SAD)
-  const Decoded d = decode_key(best, p, lam);
-  const long long NM = N * M, sad = d.sad, q = qp;
+  const long long NM = N * M, sad = best.sad, q = qp;
   const bool c1 = (long long)intra_x + NM * sad < NM * ((long long)alpha + (long long)beta * q * q);
   const bool c2 = (long long)gden * NM * sad < (long long)gnum * (long long)intra_x;
   PbmResult res;
-  res.key = best;
+  res.key = best.key;
   res.load = load;
   res.pass = c1 || c2;
   return res;
@@ -430,11 +447,10 @@ __device__ PbmResult pbm_part_b(int cx, int cy, bool valid, const PbmPart& pa, c
 // Whether a block whose PBM winner had this key would fail both conditions
 // (used on part a's best to start a likely full search early).
 template <int N, int M>
-__device__ __forceinline__ bool pbm_would_fail(unsigned long long key, int p, uint32_t lam,
+__device__ __forceinline__ bool pbm_would_fail(const PbmBest& b, int p, uint32_t lam,
                                                uint32_t intra_x, int32_t alpha, int32_t beta,
                                                int32_t gnum, int32_t gden, int32_t qp) {
-  const Decoded d = decode_key(key, p, lam);
-  const long long NM = N * M, sad = d.sad, q = qp;
+  const long long NM = N * M, sad = b.sad, q = qp;
   const bool c1 = (long long)intra_x + NM * sad < NM * ((long long)alpha + (long long)beta * q * q);
   const bool c2 = (long long)gden * NM * sad < (long long)gnum * (long long)intra_x;
   return !(c1 || c2);

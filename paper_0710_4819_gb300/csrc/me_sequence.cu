@@ -1631,6 +1631,9 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
     if (spec && model_T) forms.push_back({kSeqSearchEvery, 0, 0});
     forms.push_back({kSeqSearchEvery, spec, 2});
     forms.push_back({2, spec, 2});
+    // whole SMs per role: PBM on half / two thirds of the SMs
+    forms.push_back({-2, spec, 0});
+    forms.push_back({-3, spec, 0});
   }
   for (const Form& f : forms) {
     const size_t sm1 = seq_smem<N, M, T>(p, f.sg);
