@@ -184,14 +184,6 @@ __device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_ev
   const int sa = atomicAdd(sm_arr + (smid & (kRoleSlots - 1)), 1);
   if (arr < 2) return arr;
   if (search_every > 0 && smid % (unsigned)search_every == 0) return 1;
-  if (search_every < 0) {
-    // segregated roles: whole SMs run PBM or searches, so PBM warps never
-    // share an SM's issue slots with the search warps' SAD loops.  -2: odd
-    // SMs search (half the SMs PBM); -3: every third SM searches (two
-    // thirds PBM)
-    const unsigned d = (unsigned)(-search_every);
-    return d == 2 ? (int)(smid & 1u) : (smid % d == 0 ? 1 : 0);
-  }
   return sa & 1;
 }
 

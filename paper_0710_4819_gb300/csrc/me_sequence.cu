@@ -31,7 +31,13 @@ namespace me {
 
 constexpr int kSeqMax = 64;     // frame pairs per call
 constexpr int kSeqThreads = 256;
-constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order
+constexpr int kSeqLag = 4;      // waves between consecutive pairs in the claim order (least)
+// Claim orders the plan holds: lags of 4 (the least that keeps every
+// predecessor claimed before its block), 5 and 6 waves between pairs; a
+// longer lag claims a pair's blocks later, when their temporal predecessors
+// are more likely finished, so PBM warps wait less while holding a block.
+constexpr int kSeqLags[] = {4, 5, 6};
+constexpr int kSeqNLags = 3;
 // The model's role split of k_acbm_seq: every kSeqSearchEvery-th SM (by
 // %smid) hosts two search CTAs instead of one PBM and one search CTA.
 // Measured at 1080p p=32 (59 pairs): one of each on every SM 0.1196 ms of
@@ -1532,7 +1538,7 @@ struct SeqPlan {
   unsigned long long* bkey = nullptr;    // per block: minimum key over the search slices
   int* bdone = nullptr;                  // per block: search slices finished
   int S = 1;                             // column slices per full search
-  int* items = nullptr;                  // claim order -> block (pair * blocks + block)
+  int* items = nullptr;                  // per lag: claim order -> block (pair * blocks + block)
   SeqCtrl* ctrl = nullptr;
   int total = 0;
   cudaEvent_t last = nullptr;   // end of the previous run (runs of one plan never overlap)
@@ -1547,6 +1553,7 @@ struct SeqPlan {
     int pw;       // ver 1: PBM warps per PBM CTA; ver 2: PBM warps per CTA
     int spec;     // ver 1: speculative full searches (single-slice searches only)
     int sgroups;  // ver 1: search groups per search CTA (named barriers); 0: one, fs_group
+    int lag;      // claim-order table (index into kSeqLags)
     size_t smem;
     int grid;
     std::string name;
@@ -1623,17 +1630,19 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
   // also timed without it
   const char* se = std::getenv("ME_SEQ_SPEC");
   const int spec = pl->S == 1 && !(se && se[0] == '0') ? 1 : 0;
-  struct Form { int split, spec, sg; };
-  std::vector<Form> forms{{kSeqSearchEvery, spec, 0}};
+  struct Form { int split, spec, sg, lag; };
+  std::vector<Form> forms{{kSeqSearchEvery, spec, 0, 0}};
   if (pl->S == 1) {
-    forms.push_back({2, spec, 0});
-    if (model_T) forms.push_back({4, spec, 0});
-    if (spec && model_T) forms.push_back({kSeqSearchEvery, 0, 0});
-    forms.push_back({kSeqSearchEvery, spec, 2});
-    forms.push_back({2, spec, 2});
-    // whole SMs per role: PBM on half / two thirds of the SMs
-    forms.push_back({-2, spec, 0});
-    forms.push_back({-3, spec, 0});
+    forms.push_back({2, spec, 0, 0});
+    if (spec && model_T) forms.push_back({kSeqSearchEvery, 0, 0, 0});
+    forms.push_back({kSeqSearchEvery, spec, 2, 0});
+    forms.push_back({2, spec, 2, 0});
+    if (pl->K > 1) {
+      forms.push_back({kSeqSearchEvery, spec, 0, 1});
+      forms.push_back({kSeqSearchEvery, spec, 2, 1});
+      forms.push_back({kSeqSearchEvery, spec, 0, 2});
+      forms.push_back({kSeqSearchEvery, spec, 2, 2});
+    }
   }
   for (const Form& f : forms) {
     const size_t sm1 = seq_smem<N, M, T>(p, f.sg);
@@ -1649,14 +1658,14 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
     // the 8-row build at 85 registers measured 30 % slower.)
     if (per_sm < 2) continue;
     char nm[64];
-    std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d groups=%d", T, f.split, f.spec,
-                  f.sg > 0 ? f.sg : 1);
+    std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d groups=%d lag=%d", T, f.split, f.spec,
+                  f.sg > 0 ? f.sg : 1, kSeqLags[f.lag]);
     if (model_T && &f == &forms[0]) pl->model = (int)pl->cands.size();
-    pl->cands.push_back(
-        SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, sm1, 2 * nsm, nm});
+    pl->cands.push_back(SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, f.lag, sm1,
+                                      2 * nsm, nm});
   }
   if (pl->S == 1 && model_T) {
-    for (int pw = 4; pw <= 5; pw++) {
+    for (int pw = 5; pw <= 5; pw++) {
       const size_t sm2 = seq2_smem<N, M, T>(p, pw);
       if (sm2 > 220 * 1024) continue;
       const int e = ensure_dynamic_smem((const void*)k_acbm_seq2<N, M, T>, sm2);
@@ -1667,7 +1676,7 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
       if (per2 < 1) continue;
       char nm[64];
       std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
-      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, sm2, nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, 0, sm2, nsm, nm});
     }
   }
   return ME_OK;
@@ -1675,18 +1684,23 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
 
 static int build_seq_plan(SeqPlan* pl) {
   const int N = pl->N, M = pl->M, BW = pl->W / N, BH = pl->H / M, nbf = BW * BH;
-  // claim order: all blocks of all pairs by w + kSeqLag * k, then pair, then row
+  // claim orders: all blocks of all pairs by w + L * k, then pair, then row,
+  // one table per lag L (a block's spatial predecessors have keys one to
+  // three smaller, its temporal ones key + 3 - L: claimed earlier for L >= 4)
   const Waves wv = make_waves(BW, BH);
   std::vector<int> items;
-  items.reserve((size_t)nbf * pl->K);
-  const int maxkey = wv.n - 1 + kSeqLag * (pl->K - 1);
-  for (int key = 0; key <= maxkey; key++)
-    for (int k = 0; k < pl->K; k++) {
-      const int w = key - kSeqLag * k;
-      if (w < 0 || w >= wv.n) continue;
-      for (int by = wv.ylo(w); by <= wv.yhi(w); by++) items.push_back(k * nbf + by * BW + (w - 2 * by));
-    }
-  pl->total = (int)items.size();
+  items.reserve((size_t)nbf * pl->K * kSeqNLags);
+  for (int li = 0; li < kSeqNLags; li++) {
+    const int L = kSeqLags[li];
+    const int maxkey = wv.n - 1 + L * (pl->K - 1);
+    for (int key = 0; key <= maxkey; key++)
+      for (int k = 0; k < pl->K; k++) {
+        const int w = key - L * k;
+        if (w < 0 || w >= wv.n) continue;
+        for (int by = wv.ylo(w); by <= wv.yhi(w); by++) items.push_back(k * nbf + by * BW + (w - 2 * by));
+      }
+  }
+  pl->total = (int)(items.size() / kSeqNLags);
   const PadGeom pg = pad_geom(pl->W, pl->H, pl->p);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -2049,11 +2063,13 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
   if (N == n_ && M == m_ && cd.T == t_) {                                                      \
     if (cd.ver == 2)                                                                           \
       k_acbm_seq2<n_, m_, t_><<<cd.grid, kSeq2Threads, cd.smem, s>>>(                          \
-          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total, pl->ctrl,\
+          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                \
+          pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl,                         \
           pl->q, cd.pw);                                                                       \
     else                                                                                       \
       k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
-          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags, pl->items, pl->total,          \
+          fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                \
+          pl->items + (size_t)cd.lag * pl->total, pl->total,                                   \
           pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups); \
     st = ME_OK;                                                                                \
   }
