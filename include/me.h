@@ -121,10 +121,11 @@ int me_fsbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
  * sad_out (nullable), load_out (nullable; distinct positions evaluated,
  * (2p+1)^2 for a full-searched block).  The blocks are processed as
  * anti-diagonal waves x + 2y = w so every predictor is final when read.
- * The frame's launches (a prologue, then two kernels per wave) are captured
- * once per (device, W, H, N, M, p) into a CUDA graph with its own scratch
- * (the padded reference plus 4 bytes per block and per wave, about
- * pitch*rows + 8*BW*BH bytes, allocated at the first call with that shape and
+ * The frame's launches (a prologue, the early full searches of the blocks
+ * that fail with their temporal predictors, then one kernel per wave) are
+ * captured once per (device, W, H, N, M, p) into a CUDA graph with its own
+ * scratch (the padded reference plus 16 bytes per block, about
+ * pitch*rows + 16*BW*BH bytes, allocated at the first call with that shape and
  * kept until the process exits) and replayed by later calls; calls with the
  * same shape therefore run one after another on the GPU, whatever their
  * streams.  The first call with a new shape allocates and captures, so make
@@ -376,7 +377,7 @@ void me_server_destroy(me_server *s);
  * fixed device array of 4 MiB inside the library, which every GPU that loads
  * the library holds until the process exits.  A call needs the padded
  * reference, (16*ceil(W/16) + 2P + 16) x (H + 2P) bytes with
- * P = 16*ceil(p/16), plus 20 bytes per block: frames up to 1920x1088 fit at
+ * P = 16*ceil(p/16), plus 16 bytes per block: frames up to 1920x1088 fit at
  * any p for every block shape of 4x8 / 8x4 pixels or larger; 4x4 blocks fit
  * frames up to 1280x720 (not 1920x1088).  Arguments, outputs and errors are
  * those of me_acbm; a frame whose scratch would exceed the array returns

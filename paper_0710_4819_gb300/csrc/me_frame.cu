@@ -4,11 +4,12 @@
 //   me_fsbm : one launch; full search of every block (Sec. 2.3): for 16x16
 //             blocks the pipelined persistent search of me_sequence.cu
 //             (k_fsbm_pipe), else k_fsbm
-//   me_acbm : k_pad_ref, k_intra_sad, then for each anti-diagonal wave
-//             w = x + 2y of the block grid: k_pbm_wave (PBM + the Sec. 3.2 test,
-//             compaction of the failing blocks) and k_fs_list (full search of
-//             the compacted list).  Wave w+1 starts after wave w's full
-//             searches, so every spatial predictor is final when it is read.
+//   me_acbm : k_acbm_prologue (padding, Intra_SAD), k_acbm_spec (the likely
+//             fallbacks guessed from the early predictors and searched in
+//             full, all at once), then one k_pbm_wave per anti-diagonal wave
+//             w = x + 2y of the block grid (PBM + the Sec. 3.2 test; a failing
+//             block takes its early search's result).  Wave w+1 starts after
+//             wave w, so every spatial predictor is final when it is read.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,19 +84,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_fsbm(const uint8_t* __restrict_
 
 // ACBM prologue of one frame, one launch: stores the call's arguments in the
 // device slot the wave kernels read, pads the reference (a1), computes the
-// scaled Intra_SAD of every block (a2) and clears the per-wave counters.
+// scaled Intra_SAD of every block (a2) and clears the early-search states.
 template <int N, int M>
 __global__ void __launch_bounds__(256) k_acbm_prologue(AcbmArgs a, AcbmArgs* __restrict__ slot,
                                                        PadGeom pg, int W, int H,
                                                        uint8_t* __restrict__ refpad,
                                                        uint32_t* __restrict__ intra,
-                                                       int* __restrict__ cnt, int nwaves,
                                                        unsigned long long* __restrict__ keys,
                                                        int* __restrict__ done) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   if (gtid == 0) *slot = a;
-  for (long long i = gtid; i < nwaves; i += nthr) cnt[i] = 0;
   const int nblk = (W / N) * (H / M);
   for (long long i = gtid; i < nblk; i += nthr) {
     keys[i] = kNoKey;
@@ -181,15 +180,15 @@ __global__ void __launch_bounds__(256) k_acbm_spec(const AcbmArgs* __restrict__ 
 
 // ACBM, PBM stage of wave w: one warp per block of the wave.  Passing blocks
 // get their final outputs; failing ones take the result of their early full
-// search (k_acbm_spec) when there is one, else are appended to the wave's
-// list.
+// search (k_acbm_spec).  A failing block without one (its early predictors
+// passed: about 4 in a million blocks on the 1080p sequence) is searched in
+// full by its own warp from the window it has staged, so the wave needs no
+// second launch.
 template <int N, int M>
 __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ ap,
                                                   const uint8_t* __restrict__ refpad,
                                                   PadGeom pg, const uint32_t* __restrict__ intra,
                                                   int W, int H, int p, int w, int ylo, int count,
-                                                  int* __restrict__ fail_count,
-                                                  int* __restrict__ fail_list,
                                                   const unsigned long long* __restrict__ bkeys,
                                                   const int* __restrict__ bdone) {
   __shared__ uint32_t curs[4][M * (N / 4)];
@@ -200,80 +199,41 @@ __global__ void __launch_bounds__(128) k_pbm_wave(const AcbmArgs* __restrict__ a
   const AcbmArgs a = *ap;
   const int by = ylo + idx, bx = w - 2 * by;
   const int BW = W / N, b = by * BW + bx;
+  const int n = 2 * p + 1;
   if (!ME_CHECK(bx >= 0 && bx < BW && by >= 0 && by < H / M, "ME_CHECK pbm_wave w %d bx %d by %d\n",
                 w, bx, by))
     return;
+  uint32_t* win = wins + warp * pbm_win_words(N, M, p);
   const PbmResult r = warp_pbm<N, M>(a.cur, refpad, pg, W, H, p, a.lam, a.mv, a.prev, bx, by,
                                      intra[b], a.alpha, a.beta, a.gnum, a.gden, a.qp, a.refine,
-                                     curs[warp], wins + warp * pbm_win_words(N, M, p));
-  if (lane == 0) {
-    if (r.pass) {
-      const Decoded d = decode_key(r.key, p, a.lam);
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      a.mask[b] = 0;
-      if (a.sad) a.sad[b] = d.sad;
-      if (a.load) a.load[b] = (uint32_t)r.load;
-    } else if (bdone[b] == kSpecDone) {
-      const int n = 2 * p + 1;
-      const Decoded d = decode_key(bkeys[b], p, a.lam);
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      a.mask[b] = 1;
-      if (a.sad) a.sad[b] = d.sad;
-      if (a.load) a.load[b] = (uint32_t)(n * n);
+                                     curs[warp], win);
+  unsigned long long key = r.key;
+  bool full = false;
+  if (!r.pass) {
+    full = true;
+    if (bdone[b] == kSpecDone) {
+      key = bkeys[b];
     } else {
-      const int slot = atomicAdd(fail_count, 1);
-      fail_list[slot] = b;
+      // every position of the window, from the staged window (Sec. 2.3)
+      const PbmWin wg = pbm_win(N, M, p, bx * N, pg.P);
+      unsigned long long best = kNoKey;
+      for (int c = lane; c < n * n; c += 32) {
+        const int mvx = c % n - p, mvy = c / n - p;
+        const uint32_t sad = lane_sad_rows<N, M>(curs[warp], win, wg, p, mvx, mvy, 0, M);
+        best = umin64(best, make_key(256u * sad + a.lam * (uint32_t)(mv_bits(mvx) + mv_bits(mvy)),
+                                     mvx, mvy, p));
+      }
+      key = warp_min64(best);
     }
   }
-}
-
-// ACBM full-search fallback of one wave: list entry i is searched by S CTAs
-// (blockIdx = i*S + slice), each over a slice of the mvx columns; the slices'
-// winning keys meet in an atomic 64-bit minimum (the key order is total, so
-// the result does not depend on the order), and the last slice to finish
-// writes the block's outputs.
-template <int N, int M, int T>
-__global__ void __launch_bounds__(kMaxThreads) k_fs_list(const AcbmArgs* __restrict__ ap, int W,
-                                                         int H, int p, int S,
-                                                         const int* __restrict__ fail_count,
-                                                         const int* __restrict__ fail_list,
-                                                         unsigned long long* __restrict__ bkeys,
-                                                         int* __restrict__ bdone) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ unsigned long long keys[16];
-  const int item = blockIdx.x / S, sl = blockIdx.x - (blockIdx.x / S) * S;
-  if (item >= *fail_count) return;
-  const AcbmArgs a = *ap;
-  const int BW = W / N, n = 2 * p + 1;
-  const int b = fail_list[item];
-  const int c0 = sl * n / S, c1 = (sl + 1) * n / S;
-  const FsGeom g = fs_geom<N, M, T>(p, 1, blockDim.x, c0, c1 - c0);
-  fs_group<N, M, T>(a.cur, a.ref, W, H, (b % BW) * N, (b / BW) * M, g, a.lam, smem, keys);
-  if (threadIdx.x == 0) {
-    unsigned long long key = keys[0];
-    bool last = true;
-    if (S > 1) {
-      atomicMin(bkeys + b, key);
-      __threadfence();
-      last = atomicAdd(bdone + b, 1) == S - 1;
-      if (last) {
-        __threadfence();
-        key = atomicMin(bkeys + b, kNoKey);   // reads the merged minimum
-      }
-    }
-    if (last) {
-      const Decoded d = decode_key(key, p, a.lam);
-      a.mv[2 * b] = (int16_t)d.mvx;
-      a.mv[2 * b + 1] = (int16_t)d.mvy;
-      a.J[b] = d.J;
-      a.mask[b] = 1;
-      if (a.sad) a.sad[b] = d.sad;
-      if (a.load) a.load[b] = (uint32_t)(n * n);
-    }
+  if (lane == 0) {
+    const Decoded d = decode_key(key, p, a.lam);
+    a.mv[2 * b] = (int16_t)d.mvx;
+    a.mv[2 * b + 1] = (int16_t)d.mvy;
+    a.J[b] = d.J;
+    a.mask[b] = full ? 1 : 0;
+    if (a.sad) a.sad[b] = d.sad;
+    if (a.load) a.load[b] = full ? (uint32_t)(n * n) : (uint32_t)r.load;
   }
 }
 
@@ -420,8 +380,8 @@ FsPlan fs_plan_fixed(int N, int M, int T, int p, int thr, int bpc_max, size_t sm
   return best;
 }
 
-// Plan for searching single blocks where latency matters (the ACBM fallback
-// sits on the wave chain): S CTAs per block, each over a slice of about n/S
+// Plan for searching single blocks where latency matters (the early ACBM
+// searches run before the wave chain starts): S CTAs per block, each over a slice of about n/S
 // mvx columns with one task per thread (at most 512 threads), choosing the run
 // length and S with the fewest instructions per thread, plus a per-slice
 // charge for the merge and for the SMs the extra CTAs take.
@@ -488,20 +448,6 @@ static int launch_fsbm_t(const uint8_t* cur, const uint8_t* ref, int W, int H, i
   return ME_OK;
 }
 
-template <int N, int M, int T>
-static int launch_fs_list_t(const AcbmArgs* ap, int W, int H, int p, const int* cnt,
-                            const int* list, int grid, unsigned long long* bkeys, int* bdone,
-                            const FsPlan& pl, cudaStream_t s) {
-  auto kern = k_fs_list<N, M, T>;
-  {
-    const int st = ensure_dynamic_smem((const void*)kern, pl.smem);
-    if (st) return st;
-  }
-  kern<<<grid * pl.S, pl.threads, pl.smem, s>>>(ap, W, H, p, pl.S, cnt, list, bkeys, bdone);
-  ME_CUDA(cudaGetLastError());
-  return ME_OK;
-}
-
 int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, int p,
                 uint32_t lam, int16_t* mv, uint32_t* J, uint32_t* sad, cudaStream_t s) {
   FsPlan pl = fs_plan(N, M, p, W / N);
@@ -510,13 +456,6 @@ int launch_fsbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int
     return fsbm_tuned(frames, 1, W, H, N, M, p, lam, mv, J, sad, s);
   }
   ME_DISPATCH_FS(launch_fsbm_t, cur, ref, W, H, p, lam, mv, J, sad, pl, s);
-}
-
-static int launch_fs_list(int N, int M, const AcbmArgs* ap, int W, int H, int p, const int* cnt,
-                          const int* list, int grid, unsigned long long* bkeys, int* bdone,
-                          cudaStream_t s) {
-  const FsPlan pl = fs_plan_latency(N, M, p);
-  ME_DISPATCH_FS(launch_fs_list_t, ap, W, H, p, cnt, list, grid, bkeys, bdone, pl, s);
 }
 
 #define ME_DISPATCH_NM(FN, ...)                                  \
@@ -556,25 +495,23 @@ int launch_pad(const uint8_t* ref, int W, int H, int p, uint8_t* out, cudaStream
 template <int N, int M>
 static int launch_pbm_wave_t(const AcbmArgs* ap, const uint8_t* refpad, const PadGeom& pg,
                              const uint32_t* intra, int W, int H, int p, int w, int ylo, int count,
-                             int* cnt, int* list, const unsigned long long* bkeys, const int* bdone,
-                             cudaStream_t s) {
+                             const unsigned long long* bkeys, const int* bdone, cudaStream_t s) {
   const size_t smem = 4 * 4 * (size_t)pbm_win_words(N, M, p);
   {
     const int st = ensure_dynamic_smem((const void*)k_pbm_wave<N, M>, smem);
     if (st) return st;
   }
   k_pbm_wave<N, M><<<(count + 3) / 4, 128, smem, s>>>(ap, refpad, pg, intra, W, H, p, w, ylo,
-                                                      count, cnt, list, bkeys, bdone);
+                                                      count, bkeys, bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
 static int launch_pbm_wave(int N, int M, const AcbmArgs* ap, const uint8_t* refpad,
                            const PadGeom& pg, const uint32_t* intra, int W, int H, int p, int w,
-                           int ylo, int count, int* cnt, int* list,
-                           const unsigned long long* bkeys, const int* bdone, cudaStream_t s) {
-  ME_DISPATCH_NM(launch_pbm_wave_t, ap, refpad, pg, intra, W, H, p, w, ylo, count, cnt, list, bkeys,
-                 bdone, s);
+                           int ylo, int count, const unsigned long long* bkeys, const int* bdone,
+                           cudaStream_t s) {
+  ME_DISPATCH_NM(launch_pbm_wave_t, ap, refpad, pg, intra, W, H, p, w, ylo, count, bkeys, bdone, s);
 }
 
 template <int N, int M, int T>
@@ -603,36 +540,32 @@ static int launch_spec(int N, int M, const AcbmArgs* ap, const uint8_t* refpad, 
 
 template <int N, int M>
 static int launch_prologue_t(const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg, int W, int H,
-                             uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
-                             unsigned long long* bkeys, int* bdone, cudaStream_t s) {
+                             uint8_t* refpad, uint32_t* intra, unsigned long long* bkeys,
+                             int* bdone, cudaStream_t s) {
   const long long work = std::max<long long>((long long)pg.rows * (pg.pitch / 16),
                                              32LL * (W / N) * (H / M));
   int nsm = 1;
   { const int e = sm_count(&nsm); if (e) return e; }
   const int grid = (int)std::min<long long>((work + 255) / 256, nsm * 8LL);
-  k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, cnt, nwaves, bkeys,
-                                             bdone);
+  k_acbm_prologue<N, M><<<grid, 256, 0, s>>>(a, slot, pg, W, H, refpad, intra, bkeys, bdone);
   ME_CUDA(cudaGetLastError());
   return ME_OK;
 }
 
 static int launch_prologue(int N, int M, const AcbmArgs& a, AcbmArgs* slot, const PadGeom& pg,
-                           int W, int H, uint8_t* refpad, uint32_t* intra, int* cnt, int nwaves,
+                           int W, int H, uint8_t* refpad, uint32_t* intra,
                            unsigned long long* bkeys, int* bdone, cudaStream_t s) {
-  ME_DISPATCH_NM(launch_prologue_t, a, slot, pg, W, H, refpad, intra, cnt, nwaves, bkeys, bdone, s);
+  ME_DISPATCH_NM(launch_prologue_t, a, slot, pg, W, H, refpad, intra, bkeys, bdone, s);
 }
 
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p) {
   const PadGeom pg = pad_geom(W, H, p);
   const int nb = (W / N) * (H / M);
-  const Waves wv = make_waves(W / N, H / M);
   AcbmScratch l;
   l.off_args = 0;
   l.off_pad = align_up(sizeof(AcbmArgs), 256);
   l.off_intra = align_up(l.off_pad + (size_t)pg.pitch * pg.rows, 256);
-  l.off_cnt = align_up(l.off_intra + 4 * (size_t)nb, 256);
-  l.off_list = align_up(l.off_cnt + 4 * (size_t)wv.n, 256);
-  l.off_keys = align_up(l.off_list + 4 * (size_t)nb, 256);
+  l.off_keys = align_up(l.off_intra + 4 * (size_t)nb, 256);
   l.off_done = align_up(l.off_keys + 8 * (size_t)nb, 256);
   l.total = align_up(l.off_done + 4 * (size_t)nb, 256);
   return l;
@@ -646,32 +579,25 @@ int enqueue_acbm(const AcbmArgs& a, int W, int H, int N, int M, int p, uint8_t* 
   AcbmArgs* slot = reinterpret_cast<AcbmArgs*>(scratch + l.off_args);
   uint8_t* refpad = scratch + l.off_pad;
   uint32_t* intra = reinterpret_cast<uint32_t*>(scratch + l.off_intra);
-  int* cnt = reinterpret_cast<int*>(scratch + l.off_cnt);
-  int* list = reinterpret_cast<int*>(scratch + l.off_list);
   unsigned long long* bkeys = reinterpret_cast<unsigned long long*>(scratch + l.off_keys);
   int* bdone = reinterpret_cast<int*>(scratch + l.off_done);
   const Waves wv = make_waves(W / N, H / M);
-  int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, cnt, wv.n, bkeys, bdone, s);
+  int st = launch_prologue(N, M, a, slot, pg, W, H, refpad, intra, bkeys, bdone, s);
   if (st) return st;
   st = launch_spec(N, M, slot, refpad, pg, intra, W, H, p, bkeys, bdone, s);
   if (st) return st;
-  int off = 0;
   for (int w = 0; w < wv.n; w++) {
     const int c = wv.count(w);
     if (c == 0) continue;
-    st = launch_pbm_wave(N, M, slot, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, cnt + w,
-                         list + off, bkeys, bdone, s);
+    st = launch_pbm_wave(N, M, slot, refpad, pg, intra, W, H, p, w, wv.ylo(w), c, bkeys, bdone, s);
     if (st) return st;
-    st = launch_fs_list(N, M, slot, W, H, p, cnt + w, list + off, c, bkeys, bdone, s);
-    if (st) return st;
-    off += c;
   }
   return ME_OK;
 }
 
 // ------------------------------------------------------------------ ACBM plans
 // One cached plan per (device, W, H, N, M, p): scratch memory and a CUDA graph
-// of the whole frame (prologue + two kernels per wave), captured once and
+// of the whole frame (prologue, early searches, one kernel per wave), captured once and
 // replayed.  A call updates the prologue node's by-value arguments and
 // launches the graph; CUDA orders launches of one executable graph, so calls
 // that share a plan (even on different streams) never overlap on the GPU.

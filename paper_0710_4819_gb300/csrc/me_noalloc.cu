@@ -20,9 +20,9 @@ namespace me {
 
 // Maximum scratch of one no-alloc ACBM call.  A call needs the padded
 // reference, (16*ceil(W/16) + 2P + 16) x (H + 2P) bytes with P = 16*ceil(p/16),
-// plus 20 bytes per block and a few small tables.  That fits frames up to
+// plus 16 bytes per block and a few small tables.  That fits frames up to
 // 1920x1088 at any p <= 64 for every block shape of 32 pixels or more (4x8
-// and larger; 3.7 MB at worst), but not 4x4 blocks at 1920x1088 (4.6-4.9 MB):
+// and larger; 3.6 MB at worst), but not 4x4 blocks at 1920x1088 (4.3-4.6 MB):
 // 4x4 blocks fit frames up to 1280x720.  Every GPU that loads the library
 // holds this array until the process exits.
 constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;

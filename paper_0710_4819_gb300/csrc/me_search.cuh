@@ -573,11 +573,10 @@ int fsbm_tuned(const uint8_t* const* frames, int K, int W, int H, int N, int M, 
   } while (0)
 
 // Scratch layout of one ACBM frame (the call's arguments, padded reference,
-// scaled Intra_SAD per block, failing-block count per wave, compacted
-// failing-block lists, per-block merge key and slice counter of the sliced
-// fallback search), in bytes from the start of one 256-byte aligned region.
+// scaled Intra_SAD per block, and per block the key and state word of its
+// early full search), in bytes from the start of one 256-byte aligned region.
 struct AcbmScratch {
-  size_t off_args, off_pad, off_intra, off_cnt, off_list, off_keys, off_done, total;
+  size_t off_args, off_pad, off_intra, off_keys, off_done, total;
 };
 AcbmScratch acbm_scratch_layout(int W, int H, int N, int M, int p);
 
