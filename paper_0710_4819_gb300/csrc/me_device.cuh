@@ -240,6 +240,55 @@ __device__ __forceinline__ void fs_run_sads(const uint32_t (&c)[M][N / 4], const
   }
 }
 
+// A shared-memory word read that the compiler keeps in program order (a
+// volatile load): fs_run_sads_lr issues each row's words where the row is
+// first needed, so that at most T + 1 reference rows are live in registers.
+__device__ __forceinline__ uint32_t lds_ordered(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];"
+               : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+// The same SADs with the current block read from shared memory (cs: [M][N/4]
+// packed words) one row at a time instead of held in registers: current row
+// j meets reference rows j .. j+T-1, so only those (and the next row, loaded
+// one step ahead) stay in registers, and each enters once.  About N*M/4
+// fewer registers than fs_run_sads at the same loads per run, for kernels
+// that keep more warps resident.  Same sums (integer additions in another
+// order).
+template <int N, int M, int T>
+__device__ __forceinline__ void fs_run_sads_lr(const uint32_t* cs, const uint32_t* shp, int sp,
+                                               uint32_t (&acc)[T]) {
+  constexpr int NW = N / 4;
+  uint32_t rr[T + M][NW];
+#pragma unroll
+  for (int r = 0; r < T; r++)
+#pragma unroll
+    for (int w = 0; w < NW; w++) rr[r][w] = lds_ordered(shp + r * sp + 4 * w);
+#pragma unroll
+  for (int j = 0; j < M; j++) {
+    if (j + T < T + M - 1) {
+#pragma unroll
+      for (int w = 0; w < NW; w++) rr[j + T][w] = lds_ordered(shp + (j + T) * sp + 4 * w);
+    }
+    uint32_t cw[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) cw[w] = lds_ordered(cs + j * NW + w);
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+#pragma unroll
+      for (int k = 0; k < T; k++) {
+        if (j == 0 && w == 0)
+          acc[k] = sad4_first(cw[0], rr[k][0]);
+        else
+          acc[k] = sad4(cw[w], rr[j + k][w], acc[k]);
+      }
+    }
+  }
+}
+
 // The best key of one run (candidates row0 .. row0+T-1 of window column wcol,
 // those past row n-1 skipped), reduced as key mode `mode` says (key_mode):
 // 32-bit minima using tabQ where the mode allows it for this run, else

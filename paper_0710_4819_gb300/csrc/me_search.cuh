@@ -175,16 +175,18 @@ __host__ __device__ __forceinline__ int pub_mvy(unsigned long long w) {
 // ---------------------------------------------------------------------------
 constexpr int kRoleSlots = 1024;   // > any %smid
 
-// search_every > 0: the CTAs of every search_every-th SM (by %smid) both take
-// the search role (more search CTAs than PBM CTAs).
-__device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_every = 0) {
+// search_every > 0: the CTAs of every search_every-th SM (by %smid) all take
+// the search role (more search CTAs than PBM CTAs).  With cps CTAs per SM,
+// the first pbm_per_sm CTAs to arrive on an SM run PBM and the rest search.
+__device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_every = 0,
+                                        int cps = 2, int pbm_per_sm = 1) {
   const int arr = atomicAdd(started, 1);
   unsigned smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
   const int sa = atomicAdd(sm_arr + (smid & (kRoleSlots - 1)), 1);
   if (arr < 2) return arr;
   if (search_every > 0 && smid % (unsigned)search_every == 0) return 1;
-  return sa & 1;
+  return sa % cps < pbm_per_sm ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------

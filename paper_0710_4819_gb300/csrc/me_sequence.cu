@@ -828,8 +828,10 @@ __host__ __device__ inline size_t seq_group_words(int p, int ng) {
 // stages the block's window from the pair's padded reference by 16-byte
 // asynchronous copies, builds the shifted words, runs its share of the
 // (2p+1) x ceil((2p+1)/T) runs, and publishes the block (a speculative
-// search only if its block has failed PBM, see kSeqSpecBit).
-template <int N, int M, int T>
+// search only if its block has failed PBM, see kSeqSpecBit).  LR: the
+// current block is read from shared memory row by row (fs_run_sads_lr), for
+// the three-CTAs-per-SM build.
+template <int N, int M, int T, bool LR = false>
 __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, int H, int p,
                                  const PadGeom& pg, const uint8_t* __restrict__ refpad,
                                  unsigned long long* __restrict__ flags, int total, SeqCtrl* ctrl,
@@ -930,11 +932,13 @@ __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, i
       const uint32_t* row = raw + rr * wg.wp;
       sh[r * g.pos + oo] = __funnelshift_r(row[kk >> 2], row[(kk >> 2) + 1], 8 * (kk & 3));
     }
-    uint32_t c[M][NW];
+    uint32_t c[LR ? 1 : M][LR ? 1 : NW];
+    if constexpr (!LR) {
 #pragma unroll
-    for (int j = 0; j < M; j++)
+      for (int j = 0; j < M; j++)
 #pragma unroll
-      for (int w = 0; w < NW; w++) c[j][w] = raw[wwin + j * NW + w];
+        for (int w = 0; w < NW; w++) c[j][w] = raw[wwin + j * NW + w];
+    }
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
     unsigned long long best = kNoKey;
     {
@@ -944,7 +948,10 @@ __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, i
       for (int t = gt; t < g.tasks; t += ng) {
         const int row0 = seg * T;
         uint32_t acc[T];
-        fs_run_sads<N, M, T>(c, sh + row0 * g.pos + col, g.pos, acc);
+        if constexpr (LR)
+          fs_run_sads_lr<N, M, T>(raw + wwin, sh + row0 * g.pos + col, g.pos, acc);
+        else
+          fs_run_sads<N, M, T>(c, sh + row0 * g.pos + col, g.pos, acc);
         best = umin64(best, fs_run_key<T>(acc, row0, col, p, n, a.lam, rb, fast, tabJ, tabK, tabQ));
         seg += dseg;
         col += dcol;
@@ -978,9 +985,11 @@ __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, i
 // each with the whole CTA.  A PBM warp only waits for blocks claimed before
 // its own, and a search CTA only for a queue entry that a running PBM warp
 // will write (or for the end of the run), so every wait ends; each wait is
-// also bounded in time.
-template <int N, int M, int T>
-__global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
+// also bounded in time.  MINB = 3: three CTAs per SM (cps = 3, pbm_per_sm of
+// them PBM), registers held to a third of the SM's, search groups only, with
+// the low-register SAD runs.
+template <int N, int M, int T, int MINB = 2>
+__global__ void __launch_bounds__(kSeqThreads, MINB) k_acbm_seq(SeqFrames fr, SeqArgs a, int W, int H,
                                                              int p, PadGeom pg,
                                                              const uint8_t* __restrict__ refpad,
                                                              const uint32_t* __restrict__ intra,
@@ -991,7 +1000,8 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
                                                              unsigned long long* __restrict__ bkey,
                                                              int* __restrict__ bdone, int S,
                                                              int pbm_warps, int search_every,
-                                                             int spec, int sgroups) {
+                                                             int spec, int sgroups, int cps,
+                                                             int pbm_per_sm) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_item, s_role, s_slice;
@@ -1002,7 +1012,7 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
   const long long timeout = ctrl->timeout_cycles;
   const size_t padsz = (size_t)pg.pitch * pg.rows;
   const int n = 2 * p + 1;
-  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr, search_every);
+  if (tid == 0) s_role = cta_role(&ctrl->started, ctrl->sm_arr, search_every, cps, pbm_per_sm);
   __syncthreads();
 
   if (s_role == 0) {
@@ -1123,14 +1133,15 @@ __global__ void __launch_bounds__(kSeqThreads, 2) k_acbm_seq(SeqFrames fr, SeqAr
       }
       __syncwarp();
     }
-  } else if (sgroups > 0) {
+  } else if (sgroups > 0 || MINB >= 3) {
     // ---------------------------------------------------------------- search groups
     __shared__ int s_gitem[2];
     __shared__ unsigned long long s_gred[2];
-    const int ng = kSeqThreads / sgroups, gid = tid / ng;
-    seq_search_group<N, M, T>(fr, a, W, H, p, pg, refpad, flags, total, ctrl, q, bkey, bdone, epoch,
-                              timeout, smem + gid * seq_group_words<N, M, T>(p, ng), tid - gid * ng,
-                              ng, 1 + gid, &s_gitem[gid], &s_gred[gid]);
+    const int ng = kSeqThreads / (sgroups > 0 ? sgroups : 1), gid = tid / ng;
+    seq_search_group<N, M, T, (MINB >= 3)>(fr, a, W, H, p, pg, refpad, flags, total, ctrl, q, bkey,
+                                           bdone, epoch, timeout,
+                                           smem + gid * seq_group_words<N, M, T>(p, ng),
+                                           tid - gid * ng, ng, 1 + gid, &s_gitem[gid], &s_gred[gid]);
   } else {
     // ---------------------------------------------------------------- search CTAs
     for (;;) {
@@ -1554,6 +1565,9 @@ struct SeqPlan {
     int spec;     // ver 1: speculative full searches (single-slice searches only)
     int sgroups;  // ver 1: search groups per search CTA (named barriers); 0: one, fs_group
     int lag;      // claim-order table (index into kSeqLags)
+    int lr;       // ver 1: the low-register build (registers for three CTAs per SM)
+    int cps;      // ver 1: CTAs per SM the roles are dealt over (2 or 3)
+    int ppsm;     // ver 1: PBM CTAs per SM
     size_t smem;
     int grid;
     std::string name;
@@ -1593,6 +1607,15 @@ static size_t seq2_smem(int p, int pw) {
   X(16, 16, 8) X(16, 16, 11) X(16, 16, 13) X(16, 16, 16) X(16, 8, 8) X(16, 4, 8) X(8, 16, 8)   \
   X(8, 8, 8) X(8, 4, 8) X(4, 16, 8) X(4, 8, 8) X(4, 4, 8)
 
+// The run lengths built for three CTAs per SM, and the shared memory each of
+// those CTAs may take (three of them, plus the per-CTA reserve, fit the SM).
+#define ME_SEQ3_NMT(X) X(16, 16, 8)
+constexpr size_t kSeq3SmemCap = 74 * 1024;
+template <int N, int M, int T>
+constexpr bool seq3_built() {
+  return N == 16 && M == 16 && T == 8;
+}
+
 // Modelled cost of a run length: staged rows per column and the per-run
 // epilogue (16x16 has four instantiated run lengths, the other shapes one).
 static double seq_T_cost(int M, int p, int T) {
@@ -1617,6 +1640,41 @@ static std::vector<int> seq_Ts(int N, int M, int p) {
   for (int T : Ts)
     if (T != bestT && seq_T_cost(M, p, T) <= 1.10 * best) out.push_back(T);
   return out;
+}
+
+// Adds the low-register form of k_acbm_seq (run length 8, the build for
+// three CTAs per SM): one PBM and two search CTAs per SM.  (Measured at 1080p
+// p=32 over 59 pairs: 5.80-5.90 ms against 5.85-5.87 for the best two-CTA
+// form; two PBM CTAs per SM 7.1, two search groups per search CTA 6.2-6.3.)
+template <int N, int M>
+static int seq_add_cands3(SeqPlan* pl, int nsm, int spec) {
+  constexpr int T = 8;
+  if constexpr (seq3_built<N, M, T>()) {
+    const int p = pl->p;
+    const size_t per = (size_t)4 * (pbm_win_words(N, M, p) + M * (N / 4));
+    struct Form3 { int cps, ppsm, split, sg; };
+    const Form3 f3s[] = {{3, 1, 0, 1}};
+    for (const Form3& f : f3s) {
+      const size_t srch = 4 * (size_t)f.sg * seq_group_words<N, M, T>(p, kSeqThreads / f.sg);
+      const int pw = (int)std::min<size_t>(kSeqThreads / 32, kSeq3SmemCap / per);
+      if (pw < 1 || srch > kSeq3SmemCap) continue;
+      const size_t sm3 = std::max(srch, (size_t)pw * per);
+      {
+        const int e = ensure_dynamic_smem((const void*)k_acbm_seq<N, M, T, 3>, sm3);
+        if (e) return e;
+      }
+      int per_sm = 0;
+      ME_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acbm_seq<N, M, T, 3>,
+                                                            kSeqThreads, sm3));
+      if (per_sm < f.cps) continue;
+      char nm[80];
+      std::snprintf(nm, sizeof(nm), "seq3 T=%d pbm=%d/%d split=%d spec=%d groups=%d lag=%d", T,
+                    f.ppsm, f.cps, f.split, spec, f.sg, kSeqLags[1]);
+      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, sm3,
+                                        f.cps * nsm, nm});
+    }
+  }
+  return ME_OK;
 }
 
 // Adds the launch candidates of run length T to the plan: k_acbm_seq with
@@ -1661,8 +1719,12 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
     std::snprintf(nm, sizeof(nm), "seq T=%d split=%d spec=%d groups=%d lag=%d", T, f.split, f.spec,
                   f.sg > 0 ? f.sg : 1, kSeqLags[f.lag]);
     if (model_T && &f == &forms[0]) pl->model = (int)pl->cands.size();
-    pl->cands.push_back(SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, f.lag, sm1,
-                                      2 * nsm, nm});
+    pl->cands.push_back(SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, f.lag, 0,
+                                      2, 1, sm1, 2 * nsm, nm});
+  }
+  if (pl->S == 1 && pl->K > 1 && model_T) {
+    const int e = seq_add_cands3<N, M>(pl, nsm, spec);
+    if (e) return e;
   }
   if (pl->S == 1 && model_T) {
     for (int pw = 5; pw <= 5; pw++) {
@@ -1676,7 +1738,7 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
       if (per2 < 1) continue;
       char nm[64];
       std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
-      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, 0, sm2, nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, 0, 0, 1, 1, sm2, nsm, nm});
     }
   }
   return ME_OK;
@@ -2066,14 +2128,24 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
           fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                \
           pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl,                         \
           pl->q, cd.pw);                                                                       \
-    else                                                                                       \
+    else if (!cd.lr)                                                                           \
       k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
           fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                \
-          pl->items + (size_t)cd.lag * pl->total, pl->total,                                   \
-          pl->ctrl, pl->q, pl->bkey, pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups); \
-    st = ME_OK;                                                                                \
+          pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl, pl->q, pl->bkey,        \
+          pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, 2, 1);                       \
+    st = !cd.lr || cd.ver == 2 ? ME_OK : ME_ERR_ARG;                                           \
   }
   ME_SEQ_NMT(X)
+#undef X
+#define X(n_, m_, t_)                                                                          \
+  if (N == n_ && M == m_ && cd.T == t_ && cd.ver == 1 && cd.lr) {                             \
+    k_acbm_seq<n_, m_, t_, 3><<<cd.grid, kSeqThreads, cd.smem, s>>>(                           \
+        fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                  \
+        pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl, pl->q, pl->bkey,          \
+        pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, cd.cps, cd.ppsm);              \
+    st = ME_OK;                                                                                \
+  }
+  ME_SEQ3_NMT(X)
 #undef X
   if (st) return st;
   ME_CUDA(cudaGetLastError());
