@@ -981,7 +981,7 @@ def main():
         "motion_study": {"form": "me_motion_study: CIF original + 9 frames moved by known global "
                                  "vectors, 16x16, p=16, lambda=0, one launch",
                          "ms": study_ms, "classes": study_classes},
-        "per_pair": {"form": "me_fsbm + me_acbm (wave launches, graph-replayed) per pair",
+        "per_pair": {"form": "me_fsbm + me_acbm per pair (each in the form the tuner chose)",
                      "frames_per_s": 1e3 / statistics.mean(pair_ms),
                      "acbm_ms": statistics.mean(pair_acbm_ms), "fsbm_ms": statistics.mean(pair_fsbm_ms),
                      "p50_ms": pct(pair_ms, 0.5), "p99_ms": pct(pair_ms, 0.99),

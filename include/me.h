@@ -119,17 +119,23 @@ int me_fsbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, 
  * prev_mv_field [BH][BW][2] is the previous frame's output (NULL = zeros).
  * Outputs: mv_out, J_out, fullsearch_mask_out (1 = full search ran),
  * sad_out (nullable), load_out (nullable; distinct positions evaluated,
- * (2p+1)^2 for a full-searched block).  The blocks are processed as
- * anti-diagonal waves x + 2y = w so every predictor is final when read.
- * The frame's launches (a prologue, the early full searches of the blocks
- * that fail with their temporal predictors, then one kernel per wave) are
- * captured once per (device, W, H, N, M, p) into a CUDA graph with its own
- * scratch (the padded reference plus 16 bytes per block, about
- * pitch*rows + 16*BW*BH bytes, allocated at the first call with that shape and
- * kept until the process exits) and replayed by later calls; calls with the
- * same shape therefore run one after another on the GPU, whatever their
- * streams.  The first call with a new shape allocates and captures, so make
- * it outside any stream capture of your own. */
+ * (2p+1)^2 for a full-searched block).  Every predictor is final when
+ * read.  Two forms, the same outputs; the first call with a shape times both
+ * (see me_tune_log) and later calls use the faster:
+ *  - the wave graph: the blocks as anti-diagonal waves x + 2y = w; the
+ *    frame's launches (a prologue, the early full searches of the blocks
+ *    that fail with their temporal predictors, then one kernel per wave) are
+ *    captured once per (device, W, H, N, M, p) into a CUDA graph with its
+ *    own scratch (the padded reference plus 16 bytes per block, about
+ *    pitch*rows + 16*BW*BH bytes) and replayed;
+ *  - the persistent kernel of me_acbm_sequence over this one pair (K = 1),
+ *    with its own plan; a bounded wait that ran out is reported by
+ *    me_acbm_sequence_status(W, H, N, M, p, 1).
+ * Both are allocated at the first call with that shape and kept until the
+ * process exits; calls with the same shape run one after another on the
+ * GPU, whatever their streams.  The first call with a new shape allocates,
+ * tunes and captures, so make it outside any stream capture of your own;
+ * calls made while their stream is being captured use the wave graph. */
 int me_acbm(const uint8_t *cur, const uint8_t *ref, int W, int H, int N, int M, int p,
             uint32_t lambda_q8, const int16_t *prev_mv_field, const me_acbm_params *prm,
             int16_t *mv_out, uint32_t *J_out, uint8_t *fullsearch_mask_out, uint32_t *sad_out,

@@ -739,7 +739,7 @@ int me_acbm(const uint8_t* cur, const uint8_t* ref, int W, int H, int N, int M, 
   AcbmPlan* pl = nullptr;
   st = get_plan(W, H, N, M, p, &pl);
   if (st) return st;
-  return launch_plan(pl, a, s);
+  return acbm_pair_tuned(a, W, H, N, M, p, s, [&]() { return launch_plan(pl, a, s); });
 }
 
 }  // extern "C"

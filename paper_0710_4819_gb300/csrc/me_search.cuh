@@ -3,6 +3,7 @@
 // ACBM for one block (one warp), and the full-search plan (tile choice).
 #pragma once
 #include <cstdio>
+#include <functional>
 #include <vector>
 
 #include "../../include/me.h"
@@ -550,6 +551,14 @@ int launch_fsbm_pipe_mode(int mode, const uint8_t* const* frames, int K, int W, 
 // call; every form gives the same outputs).
 int fsbm_tuned(const uint8_t* const* frames, int K, int W, int H, int N, int M, int p,
                uint32_t lam, int16_t* mv_out, uint32_t* J_out, uint32_t* sad_out, cudaStream_t s);
+
+// ACBM of one pair in the form the autotuner picked for the shape: candidate
+// 0 is `waves` (the per-frame wave graph), the others the persistent
+// two-role kernel over this one pair (the launch forms of the sequence plan
+// with K = 1).  Every form gives the same outputs.  While s is being
+// captured, `waves` runs.
+int acbm_pair_tuned(const AcbmArgs& a, int W, int H, int N, int M, int p, cudaStream_t s,
+                    const std::function<int()>& waves);
 
 // Calls FN<N, M, T>(...) for the run lengths instantiated per block shape
 // (pl.T chooses among them for 16x16); expects N, M and pl in scope.

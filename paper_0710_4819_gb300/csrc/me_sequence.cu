@@ -2234,3 +2234,75 @@ int me_acbm_sequence_status(int W, int H, int N, int M, int p, int K, me_stream_
 }
 
 }  // extern "C"
+
+namespace me {
+
+// Tuning record of me_acbm per (device, shape): the chosen candidate of
+// acbm_pair_tuned's list.
+struct AcbmPairTune {
+  int dev, W, H, N, M, p;
+  int chosen = -1;
+  std::mutex mu;
+};
+static std::mutex g_apt_mu;
+static std::vector<AcbmPairTune*> g_apt;
+
+int acbm_pair_tuned(const AcbmArgs& a, int W, int H, int N, int M, int p, cudaStream_t s,
+                    const std::function<int()>& waves) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ME_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return waves();
+  int dev = 0;
+  ME_CUDA(cudaGetDevice(&dev));
+  AcbmPairTune* t = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_apt_mu);
+    for (AcbmPairTune* e : g_apt)
+      if (e->dev == dev && e->W == W && e->H == H && e->N == N && e->M == M && e->p == p) t = e;
+    if (!t) {
+      t = new AcbmPairTune;
+      t->dev = dev; t->W = W; t->H = H; t->N = N; t->M = M; t->p = p;
+      g_apt.push_back(t);
+    }
+  }
+  SeqPlan* pl = nullptr;
+  int st = get_seq_plan(W, H, N, M, p, 1, &pl);
+  if (st) return st;
+  SeqFrames fr;
+  std::memset(&fr, 0, sizeof(fr));
+  fr.f[0] = a.ref;
+  fr.f[1] = a.cur;
+  SeqArgs sa;
+  sa.prev0 = a.prev;
+  sa.mv = a.mv; sa.J = a.J; sa.mask = a.mask; sa.sad = a.sad; sa.load = a.load;
+  sa.lam = a.lam;
+  sa.alpha = a.alpha; sa.beta = a.beta; sa.gnum = a.gnum; sa.gden = a.gden;
+  sa.qp = a.qp; sa.refine = a.refine;
+  auto run = [&](int c) -> int {
+    if (c == 0) return waves();
+    // runs that share the plan's scratch are ordered on the GPU
+    std::lock_guard<std::mutex> lk(pl->mu);
+    return seq_enqueue(pl, c - 1, fr, sa, s);
+  };
+  std::lock_guard<std::mutex> lk(t->mu);
+  const int n = 1 + (int)pl->cands.size();
+  int c = tune_forced(n);
+  if (c < 0) {
+    if (t->chosen < 0) {
+      char what[96];
+      std::snprintf(what, sizeof(what), "acbm %dx%d %dx%d p=%d", W, H, N, M, p);
+      std::vector<std::string> names{"waves"};
+      for (const SeqPlan::Cand& cd : pl->cands) names.push_back("persistent " + cd.name);
+      // model: the persistent kernel (one launch; the wave graph pays a
+      // launch per wave on the chain)
+      int ch = 1 + pl->model;
+      st = tune_select(what, names, 1 + pl->model, s, run, &ch);
+      if (st) return st;
+      t->chosen = ch;
+    }
+    c = t->chosen;
+  }
+  return run(c);
+}
+
+}  // namespace me

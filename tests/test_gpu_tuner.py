@@ -209,3 +209,38 @@ def test_every_batch_step_form_gives_the_oracle(me, orc):
                     if mode == 1:
                         prev = [o["mv"] for o in outs]
                 b.close()
+
+
+@pytest.mark.parametrize("w,h,N,M,p", [(352, 288, 16, 16, 16), (208, 96, 8, 8, 7), (176, 144, 16, 8, 12),
+                                       (128, 64, 4, 4, 40), (96, 64, 4, 16, 64), (160, 48, 8, 4, 33)])
+def test_every_acbm_pair_candidate_gives_the_oracle(me, orc, w, h, N, M, p):
+    """me_acbm's forms (the wave graph, the persistent kernel over one pair in
+    each of its launch forms), each forced over two chained pairs, against
+    the oracle chained the same way."""
+    import torch
+    seq = synth.scene_sequence(500 + w + N + p, w, h, 3, n_objects=4, vmax=5)
+    frames = torch.from_numpy(seq).cuda()
+    lam = orc.lambda_q8(30)
+    prm = me.params(qp=30)
+    me.me_acbm(frames[1], frames[0], N, M, p, lam, prm)        # the tuned first call
+    torch.cuda.synchronize()
+    names = _candidates(me, f"acbm {w}x{h} {N}x{M} p={p}")
+    assert names and names[0] == "waves" and len(names) >= 2, me.me_tune_log()
+    want, prev = [], None
+    for k in range(2):
+        out = orc.acbm(seq[k + 1], seq[k], N, M, p, lam, orc.params(qp=30), prev)
+        prev = out[0]
+        want.append(out)
+    for c in range(len(names)):
+        prev = None
+        for k, (mv, J, mask, sad, load) in enumerate(want):
+            with _Force(c):
+                r = me.me_acbm(frames[k + 1], frames[k], N, M, p, lam, prm, prev_mv=prev)
+                torch.cuda.synchronize()
+            if c > 0:
+                me.me_acbm_sequence_status(w, h, N, M, p, 1)   # raises on a run that timed out
+            for nm, g, w_ in (("mv", r.mv.cpu().numpy(), mv), ("J", _u32(r.J), J),
+                              ("mask", r.mask.cpu().numpy(), mask), ("sad", _u32(r.sad), sad),
+                              ("load", _u32(r.load), load)):
+                assert np.array_equal(g, w_), (names[c], k, nm)
+            prev = r.mv.clone()
