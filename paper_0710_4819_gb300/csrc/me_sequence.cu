@@ -345,11 +345,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
   }
 
   // ---------------- consumers
+  // A group's R warp-tasks (32 consecutive tasks each) are dealt round robin
+  // over the consumer warps, continuing from where the previous group's
+  // dealing stopped: the warps that took one more warp-task of this group
+  // take one fewer of the next, so no warp is the slowest of every group.
   const int cw_id = warp - kPipeProducers;
   const int F = B * g.tasks;
   const int R = (F + 31) >> 5;
-  const int q0 = (cw_id * R) / kPipeConsumers, q1 = ((cw_id + 1) * R) / kPipeConsumers;
-  const int dseg = 32 / nc, dcol = 32 - (32 / nc) * nc;
+  constexpr int KC = kPipeConsumers;
+  // one step = 32 * KC tasks = dblk whole blocks + dseg runs + dcol columns
+  const int dblk = (32 * KC) / g.tasks, drem = 32 * KC - dblk * g.tasks;
+  const int dseg = drem / nc, dcol = drem - (drem / nc) * nc;
   uint32_t c[M][NW];
   for (int i = 0; i < mine; i++) {
     const int b = i & 1;
@@ -370,11 +376,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
                        : nullptr;
     const uint32_t* cwb = buf0 + b * bstride;
     const uint32_t* sh = cwb + B * M * NW;
-    int f = 32 * q0 + lane;
+    const int qs = (cw_id - (int)(((long long)i * R) % KC) + KC) % KC;
+    int f = 32 * qs + lane;
     int blk = f / g.tasks;
     const int t0 = f - blk * g.tasks;
     int seg = t0 / nc, col = t0 - (t0 / nc) * nc;
-    for (int q = q0; q < q1; q++, f += 32) {
+    for (int q = qs; q < R; q += KC, f += 32 * KC) {
       if (f < F && blk < nb) {
 #pragma unroll
         for (int j = 0; j < M; j++)
@@ -403,10 +410,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
           atomicMin(&smin_s[b][blk], mn);
         }
       }
-      seg += dseg;
       col += dcol;
       if (col >= nc) { col -= nc; seg++; }
-      while (seg >= g.nseg) { seg -= g.nseg; blk++; }
+      seg += dseg;
+      if (seg >= g.nseg) { seg -= g.nseg; blk++; }
+      blk += dblk;
     }
     mbar_arrive(&empty_bar[b]);
   }
@@ -678,7 +686,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
   }
 
   // ---------------- consumers
+  // warp-tasks dealt round robin over the consumer warps, continuing across
+  // groups (roff: where the previous group's dealing stopped)
   const int cw_id = warp - kPipeProducers;
+  constexpr int KC = kPipeConsumers;
+  int roff = 0;
   uint32_t c[M][NW];
   for (int i = 0;; i++) {
     const int b = i & 1;
@@ -695,8 +707,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
     const TabGroup& G = grp[b];
     const int p = G.p, n = 2 * p + 1, nc = n, nseg = (n + T - 1) / T;
     const int tasks = nc * nseg, F = G.nb * tasks, Rr = (F + 31) >> 5;
-    const int q0 = (cw_id * Rr) / kPipeConsumers, q1 = ((cw_id + 1) * Rr) / kPipeConsumers;
-    const int dseg = 32 / nc, dcol = 32 - (32 / nc) * nc;
+    const int qs = (cw_id - roff + KC) % KC;
+    roff = (roff + Rr) % KC;
+    // one step = 32 * KC tasks = dblk whole blocks + dseg runs + dcol columns
+    const int dblk = (32 * KC) / tasks, drem = 32 * KC - dblk * tasks;
+    const int dseg = drem / nc, dcol = drem - (drem / nc) * nc;
     const uint32_t lam = G.lam;
     const int fast = key_mode(N, M, p, lam);
     const int rb = rank_bits(p);
@@ -705,11 +720,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
     const uint32_t* tabK = tabJ + R;
     const uint32_t* tabQ = tabK + R;
     const uint32_t* sh = tabQ + R;
-    int f = 32 * q0 + lane;
+    int f = 32 * qs + lane;
     int blk = f / tasks;
     const int t0 = f - blk * tasks;
     int seg = t0 / nc, col = t0 - (t0 / nc) * nc;
-    for (int q = q0; q < q1; q++, f += 32) {
+    for (int q = qs; q < Rr; q += KC, f += 32 * KC) {
       if (f < F) {
 #pragma unroll
         for (int j = 0; j < M; j++)
@@ -720,10 +735,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
         fs_run_sads<N, M, T>(c, sh + row0 * SP + blk * N + col, SP, acc);
         atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
       }
-      seg += dseg;
       col += dcol;
       if (col >= nc) { col -= nc; seg++; }
-      while (seg >= nseg) { seg -= nseg; blk++; }
+      seg += dseg;
+      if (seg >= nseg) { seg -= nseg; blk++; }
+      blk += dblk;
     }
     mbar_arrive(&empty_bar[b]);
   }
