@@ -38,9 +38,13 @@ BW, BH = W // N, H_PAD // M
 NBLK = BW * BH
 NCAND = (2 * P + 1) ** 2
 ABSDIFF_PER_FRAME = NBLK * NCAND * N * M          # 8.83e9 for FSBM
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fsbm_pipe<16,16,13>
-# on 13 frames (12 pairs): 27.202560 MB + 0 B, i.e. per frame of the sequence
-FSBM_SEQ_DRAM_BYTES_PER_FRAME = 27.202560e6 / 13
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of each pipelined FSBM
+# kernel the tuner may pick for the sequence, on 13 frames (12 pairs), per
+# frame of the sequence: k_fsbm_pipe<16,16,13> 27.202560 MB + 0 B,
+# k_fsbm_pipe_tab<16,16> 27.203840 MB + 0 B (every frame read once)
+FSBM_SEQ_DRAM_BYTES_PER_FRAME = {"k_fsbm_pipe": 27.202560e6 / 13, "k_fsbm_pipe_tab": 27.203840e6 / 13}
+# the kernel behind each full-search form of the tuner's record
+FSBM_FORM_KERNEL = (("pipetab", "k_fsbm_pipe_tab"), ("pipe", "k_fsbm_pipe"), ("group", "k_fsbm_seq"))
 WORKLOAD = "1080p 1920x1088 16x16 p=32 Qp=28, 60-frame synthetic sequence"
 # one metric string for both arms (the native step and the oracle's), so the
 # two lines can be divided; candidate-SADs/s, the roofline and p99 are keys
@@ -922,6 +926,11 @@ def main():
     # the autotuner's record for the shapes this run used: model's and chosen
     # launch form and every candidate's time (first call of each shape)
     tuning = parse_tune_log(me.me_tune_log())
+    # the dominant kernel: the full-search form the tuner chose for the step
+    fs_form = next((t["chosen"] for t in tuning
+                    if t["shape"] == f"fsbm {W}x{H_PAD} {N}x{M} p={P} K={pairs}"), "pipe")
+    fs_kernel = next(k for pre, k in FSBM_FORM_KERNEL if fs_form.startswith(pre))
+    fs_traffic = FSBM_SEQ_DRAM_BYTES_PER_FRAME.get(fs_kernel)
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -987,13 +996,13 @@ def main():
                      "p50_ms": pct(pair_ms, 0.5), "p99_ms": pct(pair_ms, 0.99),
                      "outputs_identical_to_sequence": identical},
         "p99_ms": pct(pair_ms, 0.99),
-        "roofline": {"bound": "alu", "kernel": "k_fsbm_pipe", "achieved": achieved / 1e12,
+        "roofline": {"bound": "alu", "kernel": fs_kernel, "form": fs_form, "achieved": achieved / 1e12,
                      "peak": peak_absdiff / 1e12, "unit": "T absdiff/s",
                      "frac": achieved / peak_absdiff,
                      # DRAM bytes of one launch over the whole sequence: ncu
                      # dram__bytes_read+write of the same kernel on the 13-frame
                      # case (27.20 MB, every frame read once), scaled by frames
-                     "traffic": FSBM_SEQ_DRAM_BYTES_PER_FRAME * (pairs + 1),
+                     "traffic": None if fs_traffic is None else fs_traffic * (pairs + 1),
                      "traffic_unit": "bytes/launch",
                      "algorithmic_bytes": (pairs + 1) * W * H_PAD,
                      "peak_source": f"{n_sm} SMs x {lanes_per_clk:.2f} packed-SAD lanes/clk/SM "
@@ -1003,7 +1012,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "outputs_identical": same_e2e,
                 "form": "frames up in 4 chunks on a copy stream, each chunk's full search "
                         "as soon as it is in; median of 3"},
-        "gpu_launches": 4 * args.steps,   # k_fsbm_pipe; k_seq_begin, k_seq_prologue, k_acbm_seq
+        "gpu_launches": 4 * args.steps,   # the full search; k_seq_begin, k_seq_prologue, k_acbm_seq
         "clocks": clk,
         "cpu_baseline": cpu_base,
         "tuning": tuning,

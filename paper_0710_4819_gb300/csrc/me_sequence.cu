@@ -424,34 +424,47 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe(SeqFrames fr, int
 //
 // The pipelined full search for every block shape at every search range
 // p <= 64, driven by a table of block groups: the same producer/consumer
-// pipeline as k_fsbm_pipe (4 producer warps stage a group into one of two
-// shared buffers while 12 consumer warps search the other), with a fixed
-// shifted-word pitch of kTabSP = 157 words and buffers of TabCfg::R rows
-// (enough for p = 64), holding a group of tab_bpc(p) adjacent blocks (16x16:
-// 8 at p <= 16, 6 at p <= 32, 4 at p <= 48, 2 at p <= 64; narrower blocks
-// more).  Runs of 13 rows for 16x16 blocks, 8 for the other shapes.  Groups
-// come from one of two sources:
+// pipeline as k_fsbm_pipe (4 producer warps stage a work item into one of
+// two shared buffers while 12 consumer warps search the other), with a fixed
+// shifted-word pitch of kTabSP words.  A group is tab_bpc(p) adjacent blocks
+// of one block row (16x16: 8 at p = 64, 12 at p = 32, 14 at p = 16; narrower
+// blocks more).  Its candidate rows (mvy) are split into bands of at most
+// TabCfg::HB rows (65 for 16x16: five runs of 13; 72 for the other shapes:
+// nine runs of 8), one work item per band: a window band of HB + M - 1 rows
+// is staged at a time, so that the shifted words of many blocks fit the
+// buffers at any p and the producers' staging is spread over more SAD work.
+// The bands of a group meet in the per-block minimum (red), which the
+// producers decode after the group's last band.  Groups come from one of
+// two sources:
 //   - a sequence of K pairs (frames[k] -> frames[k+1]) of one shape, groups
 //     dealt to CTAs round robin;
 //   - a batch of streams of any sizes and ranges (the batch API's stream and
 //     group tables), groups claimed from a counter, largest work first.
 // The tables of costs per row depend on p and lambda, so the producers stage
-// them with each group.
-constexpr int kTabSP = 157;
+// them with each work item.
+constexpr int kTabSP = 253;
 
 template <int N, int M>
 struct TabCfg {
   static constexpr int T = (N == 16 && M == 16) ? 13 : 8;              // run length
-  static constexpr int B = 128 / N;                                    // blocks per group, at most
-  static constexpr int R = ((2 * kMaxP + 1 + T - 1) / T) * T + M - 1;  // rows at p = 64
+  static constexpr int HB = ((65 + T - 1) / T) * T;                    // candidate rows per band
+  static constexpr int RB = HB + M - 1;                                // staged rows per band
+  static constexpr int RT = 2 * HB;                                    // cost-table rows (p <= 64)
+  static constexpr int B = 256 / N;                                    // blocks per group, at most
   static constexpr int WBW = (kTabSP + 6) / 4 + 1;                     // raw words per row
-  static constexpr int BST = B * M * (N / 4) + 3 * R + R * kTabSP;     // words per buffer
+  static constexpr int BST = B * M * (N / 4) + 3 * RT + RB * kTabSP;   // words per buffer
 };
 
 template <int N>
 __host__ __device__ inline int tab_bpc(int p) {
   const int b = (kTabSP - (2 * p + 1) - (N - 4)) / N + 1;
-  return b < 128 / N ? b : 128 / N;
+  return b < 256 / N ? b : 256 / N;
+}
+
+// Bands of a group at range p (one while 2p+1 <= HB, else two).
+template <int N, int M>
+__host__ __device__ inline int tab_nbands(int p) {
+  return 2 * p + 1 <= TabCfg<N, M>::HB ? 1 : 2;
 }
 
 struct TabArgs {
@@ -525,36 +538,35 @@ __device__ __forceinline__ TabGroup tab_group(const TabArgs& A, int gi) {
   return G;
 }
 
-template <int T, int M>
-__host__ __device__ inline int tab_rows(int p) {
-  return ((2 * p + 1 + T - 1) / T) * T + M - 1;
-}
-
 template <int N, int M>
 __host__ __device__ inline size_t tab_smem_bytes() {
   using C = TabCfg<N, M>;
-  return 4 * ((size_t)C::R * C::WBW + 2 * (size_t)C::BST);
+  return 4 * ((size_t)C::RB * C::WBW + 2 * (size_t)C::BST);
 }
 
 template <int N, int M>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
   using C = TabCfg<N, M>;
-  constexpr int NW = N / 4, T = C::T, SP = kTabSP, R = C::R, B = C::B;
+  constexpr int NW = N / 4, T = C::T, SP = kTabSP, RB = C::RB, RT = C::RT, HB = C::HB, B = C::B;
   constexpr int WBW = C::WBW;
   constexpr int PT = 32 * kPipeProducers, CT = 32 * kPipeConsumers;
   constexpr int BST = C::BST;   // words per buffer
   extern __shared__ __align__(16) uint32_t smem[];
+  // per group slot (two groups can be in flight): the group and its blocks'
+  // running minima over the bands searched so far
   __shared__ unsigned long long red[2][B];
   __shared__ TabGroup grp[2];
-  __shared__ int gid_s[2];
+  // per buffer: the work item's group (-1: end mark), group slot, first
+  // candidate row of its band, candidate rows, last band of its group
+  __shared__ int gid_s[2], slot_s[2], r0_s[2], nrow_s[2], last_s[2];
   __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
-  __shared__ int err_s, go_s, claim_s;
+  __shared__ int err_s, go_s, claim_s, band_s, newg_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned FULL = 0xffffffffu;
-  uint32_t* raw = smem;                       // [R][WBW], producers only
-  uint32_t* const buf0 = raw + R * WBW;       // buffer b: cur [B][M][NW], tabJ/K/Q [R], sh [R][SP]
+  uint32_t* raw = smem;                       // [RB][WBW], producers only
+  uint32_t* const buf0 = raw + RB * WBW;      // buffer b: cur [B][M][NW], tabJ/K/Q [RT], sh [RB][SP]
   int* const errw = A.err ? A.err : &g_fsbm_pipe_error;
-  if (tid < 2 * B) red[tid / B][tid % B] = kNoKey;
+  for (int i = tid; i < 2 * B; i += blockDim.x) red[i / B][i % B] = kNoKey;
   if (tid == 0) {
     err_s = 0;
     mbar_init(&full_bar[0], PT);
@@ -566,6 +578,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
 
   if (warp < kPipeProducers) {
     const int pt = tid;
+    // the decisions of producer thread 0: current group, its band, its bands
+    int cur_g = -1, cur_band = 0, cur_nb = 0, gj = 0, gcount = 0;
     auto finish = [&](int j) {
       const int b = j & 1;
       if (pt == 0) {
@@ -577,21 +591,24 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
       const bool go = go_s != 0;
       asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
       if (!go) return false;
-      if (pt < B) {
-        const TabGroup& G = grp[b];
-        if (pt < G.nb) {
-          const Decoded d = decode_key(red[b][pt], G.p, G.lam);
-          const long long o = G.obase + pt;
-          if (G.mv) {
-            G.mv[2 * o] = (int16_t)d.mvx;
-            G.mv[2 * o + 1] = (int16_t)d.mvy;
+      if (last_s[b]) {
+        const int sl = slot_s[b];
+        const TabGroup& G = grp[sl];
+        for (int e = pt; e < B; e += PT) {
+          if (e < G.nb) {
+            const Decoded d = decode_key(red[sl][e], G.p, G.lam);
+            const long long o = G.obase + e;
+            if (G.mv) {
+              G.mv[2 * o] = (int16_t)d.mvx;
+              G.mv[2 * o + 1] = (int16_t)d.mvy;
+            }
+            if (G.J) G.J[o] = d.J;
+            if (G.sad) G.sad[o] = d.sad;
           }
-          if (G.J) G.J[o] = d.J;
-          if (G.sad) G.sad[o] = d.sad;
+          red[sl][e] = kNoKey;
         }
-        red[b][pt] = kNoKey;
       }
-      // grp[b] is rewritten by the next group staged into buffer b
+      // the buffer's item fields and grp[] are rewritten after this
       asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
       return true;
     };
@@ -599,44 +616,70 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
     int i = 0;
     for (;; i++) {
       const int b = i & 1;
-      if (pt == 0) claim_s = A.ctr ? atomicAdd(A.ctr, 1) : (int)blockIdx.x + i * (int)gridDim.x;
+      if (pt == 0) {
+        // the next band of the current group, or the first band of the next
+        if (cur_g >= 0 && cur_band + 1 < cur_nb) {
+          cur_band++;
+          newg_s = 0;
+        } else {
+          cur_g = A.ctr ? atomicAdd(A.ctr, 1) : (int)blockIdx.x + gj * (int)gridDim.x;
+          gj++;
+          cur_band = 0;
+          cur_nb = cur_g < A.ngroups ? tab_nbands<N, M>(tab_group<N, M>(A, cur_g).p) : 1;
+          newg_s = 1;
+        }
+        claim_s = cur_g;
+        band_s = cur_band;
+      }
       asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
-      const int gi = claim_s;
-      if (i >= 2 && !finish(i - 2)) { ok = false; break; }   // (its barriers order claim_s)
+      const int gi = claim_s, band = band_s, newg = newg_s;
+      if (i >= 2 && !finish(i - 2)) { ok = false; break; }   // (its barriers order the reads above)
       if (gi >= A.ngroups) break;
       const TabGroup G = tab_group<N, M>(A, gi);
+      const int p = G.p, n = 2 * p + 1, nbands = tab_nbands<N, M>(p);
+      const int R0 = band * HB, nrow = min(n - R0, HB), nseg = (nrow + T - 1) / T;
+      const int rows = nseg * T + M - 1;
       if (pt == 0) {
-        grp[b] = G;
+        if (newg) {
+          grp[gcount & 1] = G;
+          gcount++;
+        }
         gid_s[b] = gi;
+        slot_s[b] = (gcount - 1) & 1;
+        r0_s[b] = R0;
+        nrow_s[b] = nrow;
+        last_s[b] = band == nbands - 1 ? 1 : 0;
       }
-      const int p = G.p, n = 2 * p + 1, rows = tab_rows<T, M>(p);
       const int pos = (G.nb - 1) * N + n + N - 4;
       uint32_t* cw = buf0 + b * BST;
       uint32_t* tabJ = cw + B * M * NW;
-      uint32_t* tabK = tabJ + R;
-      uint32_t* tabQ = tabK + R;
-      uint32_t* sh = tabQ + R;
+      uint32_t* tabK = tabJ + RT;
+      uint32_t* tabQ = tabK + RT;
+      uint32_t* sh = tabQ + RT;
       for (int e = pt; e < G.nb * M * NW; e += PT) {
         const int blk = e / (M * NW), rm = e % (M * NW), j = rm / NW, w = rm % NW;
         cw[e] = *reinterpret_cast<const uint32_t*>(G.cur + (size_t)(G.y0 + j) * G.W + G.x0 + blk * N +
                                                   4 * w);
       }
+      // costs of every candidate row of the group (indexed by the row in the
+      // whole window, r = mvy + p)
       const int kmode = key_mode(N, M, p, G.lam);
-      for (int r = pt; r < rows; r += PT) {
+      for (int r = pt; r < nbands * HB; r += PT) {
         const int mvy = r - p;
         const int am = mvy < 0 ? -mvy : mvy;
         tabJ[r] = G.lam * (uint32_t)mv_bits(mvy);
         tabK[r] = ((uint32_t)am << 17) + (uint32_t)r * (uint32_t)n;
         tabQ[r] = tabq_value(kmode, tabJ[r], mvy, p);
       }
-      // raw window rows from the aligned word at or left of column x0 - p
+      // raw window rows of the band, from the aligned word at or left of
+      // column x0 - p
       const int wbw = (pos + 6) / 4 + 1;
       const int wx0 = G.x0 - p;
       const int A0 = (wx0 >> 2) << 2;
       const int s0 = wx0 - A0;
       const bool inside = A0 >= 0 && A0 + 4 * wbw <= G.W;
       for (int r = warp; r < rows; r += kPipeProducers) {
-        const size_t yrow = (size_t)clampi(G.y0 - p + r, 0, G.H - 1) * G.W;
+        const size_t yrow = (size_t)clampi(G.y0 - p + R0 + r, 0, G.H - 1) * G.W;
         uint32_t* dst = raw + r * WBW;
         for (int q = lane; q < wbw; q += 32) {
           if (inside) {
@@ -675,7 +718,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
       mbar_arrive(&full_bar[b]);
     }
     if (ok) {
-      // buffer i & 1 is free (group i - 2 finished): it carries the end mark
+      // buffer i & 1 is free (item i - 2 finished): it carries the end mark
       const int b = i & 1;
       if (pt == 0) gid_s[b] = -1;
       asm volatile("bar.sync 1, %0;" ::"r"(PT) : "memory");
@@ -687,7 +730,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
 
   // ---------------- consumers
   // warp-tasks dealt round robin over the consumer warps, continuing across
-  // groups (roff: where the previous group's dealing stopped)
+  // work items (roff: where the previous item's dealing stopped)
   const int cw_id = warp - kPipeProducers;
   constexpr int KC = kPipeConsumers;
   int roff = 0;
@@ -704,8 +747,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
     __syncwarp();
     mbar_wait(&full_bar[b], (unsigned)((i >> 1) & 1), &err_s, A.lim);
     if (gid_s[b] < 0) break;
-    const TabGroup& G = grp[b];
-    const int p = G.p, n = 2 * p + 1, nc = n, nseg = (n + T - 1) / T;
+    const int sl = slot_s[b], R0 = r0_s[b], nrow = nrow_s[b];
+    const TabGroup& G = grp[sl];
+    const int p = G.p, n = 2 * p + 1, nc = n, nseg = (nrow + T - 1) / T;
     const int tasks = nc * nseg, F = G.nb * tasks, Rr = (F + 31) >> 5;
     const int qs = (cw_id - roff + KC) % KC;
     roff = (roff + Rr) % KC;
@@ -717,9 +761,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
     const int rb = rank_bits(p);
     const uint32_t* cwb = buf0 + b * BST;
     const uint32_t* tabJ = cwb + B * M * NW;
-    const uint32_t* tabK = tabJ + R;
-    const uint32_t* tabQ = tabK + R;
-    const uint32_t* sh = tabQ + R;
+    const uint32_t* tabK = tabJ + RT;
+    const uint32_t* tabQ = tabK + RT;
+    const uint32_t* sh = tabQ + RT;
     int f = 32 * qs + lane;
     int blk = f / tasks;
     const int t0 = f - blk * tasks;
@@ -733,7 +777,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fsbm_pipe_tab(TabArgs A) {
         const int row0 = seg * T;
         uint32_t acc[T];
         fs_run_sads<N, M, T>(c, sh + row0 * SP + blk * N + col, SP, acc);
-        atomicMin(&red[b][blk], fs_run_key<T>(acc, row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
+        atomicMin(&red[sl][blk],
+                  fs_run_key<T>(acc, R0 + row0, col, p, n, lam, rb, fast, tabJ, tabK, tabQ));
       }
       col += dcol;
       if (col >= nc) { col -= nc; seg++; }
