@@ -985,13 +985,26 @@ __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, i
     }
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(ng) : "memory");
     // shifted words: sh[r][o] = window bytes s0+o .. s0+o+3 of row r (rows
-    // past the window's last row only feed candidates beyond 2p: any row)
-    for (int i = gt; i < g.rows * g.pos; i += ng) {
-      const int r = i / g.pos, oo = i - r * g.pos;
-      const int rr = r < wg.rows ? r : wg.rows - 1;
-      const int kk = wg.s0 + oo;
-      const uint32_t* row = raw + rr * wg.wp;
-      sh[r * g.pos + oo] = __funnelshift_r(row[kk >> 2], row[(kk >> 2) + 1], 8 * (kk & 3));
+    // past the window's last row only feed candidates beyond 2p: any row),
+    // a row per warp of the group, four consecutive words per lane
+    {
+      const int gw = gt >> 5, ngw = ng >> 5, quads = (g.pos + 3) >> 2;
+      for (int r = gw; r < g.rows; r += ngw) {
+        const uint32_t* row = raw + (r < wg.rows ? r : wg.rows - 1) * wg.wp;
+        for (int qd = lane; qd < quads; qd += 32) {
+          const int oo = 4 * qd;
+          const uint32_t* rw = row + ((wg.s0 + oo) >> 2);
+          const uint32_t w0 = rw[0], w1 = rw[1], w2 = rw[2];
+          const int t0 = (wg.s0 + oo) & 3;
+          uint32_t* dst = sh + r * g.pos + oo;
+#pragma unroll
+          for (int d = 0; d < 4; d++) {
+            const int t = t0 + d;
+            if (oo + d < g.pos)
+              dst[d] = t < 4 ? __funnelshift_r(w0, w1, 8 * t) : __funnelshift_r(w1, w2, 8 * (t - 4));
+          }
+        }
+      }
     }
     uint32_t c[LR ? 1 : M][LR ? 1 : NW];
     if constexpr (!LR) {
@@ -1550,12 +1563,25 @@ __global__ void __launch_bounds__(kSeq2Threads, 1) k_acbm_seq2(
     }
     // shifted words: sh[r][o] = window bytes s0+o .. s0+o+3 of row r (rows
     // past the window's last row only feed candidates beyond 2p: any row)
-    for (int i = st; i < g.rows * g.pos; i += ns) {
-      const int r = i / g.pos, oo = i - r * g.pos;
-      const int rr = r < wg.rows ? r : wg.rows - 1;
-      const int kk = wg.s0 + oo;
-      const uint32_t* row = raw + rr * wg.wp;
-      sh[r * g.sp + oo] = __funnelshift_r(row[kk >> 2], row[(kk >> 2) + 1], 8 * (kk & 3));
+    {
+      // a row per warp of the group, four consecutive words per lane
+      const int gw = st >> 5, ngw = ns >> 5, quads = (g.pos + 3) >> 2;
+      for (int r = gw; r < g.rows; r += ngw) {
+        const uint32_t* row = raw + (r < wg.rows ? r : wg.rows - 1) * wg.wp;
+        for (int qd = lane; qd < quads; qd += 32) {
+          const int oo = 4 * qd;
+          const uint32_t* rw = row + ((wg.s0 + oo) >> 2);
+          const uint32_t w0 = rw[0], w1 = rw[1], w2 = rw[2];
+          const int t0 = (wg.s0 + oo) & 3;
+          uint32_t* dst = sh + r * g.sp + oo;
+#pragma unroll
+          for (int d = 0; d < 4; d++) {
+            const int t = t0 + d;
+            if (oo + d < g.pos)
+              dst[d] = t < 4 ? __funnelshift_r(w0, w1, 8 * t) : __funnelshift_r(w1, w2, 8 * (t - 4));
+          }
+        }
+      }
     }
     uint32_t c[M][NW];
 #pragma unroll
