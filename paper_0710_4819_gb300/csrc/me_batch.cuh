@@ -302,13 +302,25 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)i |
                                  kBatchSpecBit);
       }
+      // the ring around part a's best, evaluated now if a spatial neighbour
+      // is still running (part b uses it when no spatial predictor beats
+      // part a's best; the result never depends on it)
+      PbmRing ring0 = pbm_no_ring();
+      if (a.refine) {
+        const bool ready = sflag < 0 ||
+                           pub_epoch(*reinterpret_cast<const volatile unsigned long long*>(
+                               s.flags + sflag)) == epoch;
+        if (!__all_sync(0xffffffffu, ready))
+          ring0 = pbm_ring_early<N, M>(cx, cy, valid, pa, wg, s.p, a.lam, curs, win);
+      }
       if (sflag >= 0) {
         const unsigned long long w = batch_wait(s.flags + sflag, epoch, ctrl, timeout, i);
         cx = pub_mvx(w);
         cy = pub_mvy(w);
       }
       const PbmResult r = pbm_part_b<N, M>(cx, cy, valid, pa, wg, s.p, a.lam, ix, a.alpha, a.beta,
-                                           a.gnum, a.gden, a.qp, a.refine, curs, win);
+                                           a.gnum, a.gden, a.qp, a.refine, curs, win, nullptr,
+                                           ring0);
       if (lane == 0) {
         if (r.pass) {
           // the flag word carries the vector: publish first, outputs after

@@ -386,12 +386,66 @@ __device__ PbmPart pbm_part_a(int cx, int cy, bool valid, const PbmWin& wg, int 
   return r;
 }
 
+// The +-1 ring around part a's best, evaluated early (while the warp waits
+// for its spatial neighbours): ring positions equal to a temporal or zero
+// predictor, or to an earlier ring lane's, are skipped, as in part b.  Part b
+// uses it when no spatial predictor beats part a's best, so that the ring is
+// the same one (positions equal to a spatial predictor then only drop out of
+// the load count: their keys are already in the running best).
+struct PbmRing {
+  PbmBest best;   // best of the ring's evaluated positions (kNoKey: none)
+  int rcode;      // this lane's ring position (lanes 0-7)
+  bool act;       // this lane's position was evaluated
+  bool valid;     // the early ring exists
+};
+
+__device__ __forceinline__ PbmRing pbm_no_ring() {
+  PbmRing r;
+  r.best.key = kNoKey;
+  r.best.mvx = r.best.mvy = 0;
+  r.best.sad = 0u;
+  r.rcode = -1;
+  r.act = false;
+  r.valid = false;
+  return r;
+}
+
+template <int N, int M>
+__device__ PbmRing pbm_ring_early(int cx, int cy, bool valid, const PbmPart& pa, const PbmWin& wg,
+                                  int p, uint32_t lam, const uint32_t* curs, const uint32_t* win) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  // the temporal and zero predictors' codes (lanes 4-13)
+  const bool is_tz = valid && lane >= 4 && lane < 14;
+  const int ecode = is_tz ? pbm_code(cx, cy, true, p) : -1;
+  int rcode = -100 - lane;
+  int ex = 0, ey = 0;
+  if (lane < 8) {
+    const int o = lane < 4 ? lane : lane + 1;  // skip the centre of the 3x3
+    ex = clampi(pa.best.mvx + o % 3 - 1, -p, p);
+    ey = clampi(pa.best.mvy + o / 3 - 1, -p, p);
+    rcode = ((ey + p) << 8) + (ex + p);
+  }
+  bool rdup = false;
+#pragma unroll
+  for (int l = 4; l < 14; l++) rdup |= (__shfl_sync(FULL, ecode, l) == rcode);
+  const unsigned rsame = __match_any_sync(FULL, rcode);
+  rdup |= (rsame & ((1u << lane) - 1u)) != 0;
+  PbmRing r;
+  r.act = lane < 8 && !rdup;
+  r.rcode = rcode;
+  r.best = pbm_eval_set<N, M>(ex, ey, r.act, 4, wg, p, lam, curs, win);
+  r.valid = true;
+  return r;
+}
+
 template <int N, int M>
 __device__ PbmResult pbm_part_b(int cx, int cy, bool valid, const PbmPart& pa, const PbmWin& wg,
                                 int p, uint32_t lam, uint32_t intra_x, int32_t alpha,
                                 int32_t beta, int32_t gnum, int32_t gden, int32_t qp,
                                 int32_t refine, const uint32_t* curs, const uint32_t* win,
-                                unsigned long long* tr = nullptr) {
+                                unsigned long long* tr = nullptr,
+                                const PbmRing& early = pbm_no_ring()) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   // every predictor's code (lanes 0-13); a spatial one repeating a temporal
@@ -405,7 +459,17 @@ __device__ PbmResult pbm_part_b(int cx, int cy, bool valid, const PbmPart& pa, c
                                                         M >= 8 ? 8 : 4, wg, p, lam, curs, win));
   int load = pa.load + __popc(__ballot_sync(FULL, actb));
   pbm_stamp(tr, 1);
-  if (refine) {
+  if (refine && early.valid && best.key == pa.best.key) {
+    // no spatial predictor beat part a's best: the early ring is this ring;
+    // its positions equal to a spatial predictor leave the load count
+    const int scode = is_pred && lane < 4 ? code : -1;
+    bool sdup = false;
+#pragma unroll
+    for (int l = 0; l < 4; l++) sdup |= (__shfl_sync(FULL, scode, l) == early.rcode);
+    best = pbm_better(best, early.best);
+    load += __popc(__ballot_sync(FULL, early.act && !sdup));
+    pbm_stamp(tr, 2);
+  } else if (refine) {
     // every predictor's position has been evaluated (by its lane or by the
     // lane it repeats), so a ring position equal to any predictor's is skipped
     const int ecode = is_pred ? code : -1;

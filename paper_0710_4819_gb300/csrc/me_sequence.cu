@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(kSeqThreads, MINB) k_acbm_seq(SeqFrames fr, Se
                                                              int* __restrict__ bdone, int S,
                                                              int pbm_warps, int search_every,
                                                              int spec, int sgroups, int cps,
-                                                             int pbm_per_sm) {
+                                                             int pbm_per_sm, int early) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long keys[16];
   __shared__ int s_item, s_role, s_slice;
@@ -1158,6 +1158,17 @@ __global__ void __launch_bounds__(kSeqThreads, MINB) k_acbm_seq(SeqFrames fr, Se
         const int slot = atomicAdd(&ctrl->fs_tail, 1);
         atomicExch(q + slot, ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)o | kSeqSpecBit);
       }
+      // the ring around part a's best, evaluated now if a spatial neighbour
+      // is still running (part b uses it when no spatial predictor beats
+      // part a's best; the result never depends on it)
+      PbmRing ring0 = pbm_no_ring();
+      if (a.refine && early) {
+        bool ready = true;
+        if (lane < 4 && nidx >= 0)
+          ready = pub_epoch(*reinterpret_cast<const volatile unsigned long long*>(flags + nidx)) == epoch;
+        if (!__all_sync(FULL, ready))
+          ring0 = pbm_ring_early<N, M>(cx, cy, valid, pa, wg, p, a.lam, curs, win);
+      }
       {
         const bool sl = lane < 4 && nidx >= 0;
         const unsigned long long w = warp_wait_flags(sl ? flags + nidx : nullptr, epoch,
@@ -1168,7 +1179,8 @@ __global__ void __launch_bounds__(kSeqThreads, MINB) k_acbm_seq(SeqFrames fr, Se
         }
       }
       const PbmResult r = pbm_part_b<N, M>(cx, cy, valid, pa, wg, p, a.lam, ix, a.alpha, a.beta,
-                                           a.gnum, a.gden, a.qp, a.refine, curs, win);
+                                           a.gnum, a.gden, a.qp, a.refine, curs, win, nullptr,
+                                           ring0);
       if (lane == 0) {
         if (r.pass) {
           // the flag word carries the vector: publish first, outputs after
@@ -1655,6 +1667,7 @@ struct SeqPlan {
     int lr;       // ver 1: the low-register build (registers for three CTAs per SM)
     int cps;      // ver 1: CTAs per SM the roles are dealt over (2 or 3)
     int ppsm;     // ver 1: PBM CTAs per SM
+    int early;    // ver 1: the ring around part a's best evaluated during the spatial wait
     size_t smem;
     int grid;
     std::string name;
@@ -1757,8 +1770,11 @@ static int seq_add_cands3(SeqPlan* pl, int nsm, int spec) {
       char nm[80];
       std::snprintf(nm, sizeof(nm), "seq3 T=%d pbm=%d/%d split=%d spec=%d groups=%d lag=%d", T,
                     f.ppsm, f.cps, f.split, spec, f.sg, kSeqLags[1]);
-      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, sm3,
+      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, 1, sm3,
                                         f.cps * nsm, nm});
+      // and with the ring evaluated after the spatial predictors only
+      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, 0, sm3,
+                                        f.cps * nsm, std::string(nm) + " ring=late"});
     }
   }
   return ME_OK;
@@ -1807,7 +1823,10 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
                   f.sg > 0 ? f.sg : 1, kSeqLags[f.lag]);
     if (model_T && &f == &forms[0]) pl->model = (int)pl->cands.size();
     pl->cands.push_back(SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, f.lag, 0,
-                                      2, 1, sm1, 2 * nsm, nm});
+                                      2, 1, 1, sm1, 2 * nsm, nm});
+    if (f.split == kSeqSearchEvery && f.sg == 2 && f.lag == 1)
+      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, seq_pbm_warps(N, M, p), f.spec, f.sg, f.lag,
+                                        0, 2, 1, 0, sm1, 2 * nsm, std::string(nm) + " ring=late"});
   }
   if (pl->S == 1 && pl->K > 1 && model_T) {
     const int e = seq_add_cands3<N, M>(pl, nsm, spec);
@@ -1825,7 +1844,7 @@ static int seq_add_cands(SeqPlan* pl, int nsm, bool model_T) {
       if (per2 < 1) continue;
       char nm[64];
       std::snprintf(nm, sizeof(nm), "seq2 T=%d pw=%d", T, pw);
-      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, 0, 0, 1, 1, sm2, nsm, nm});
+      pl->cands.push_back(SeqPlan::Cand{2, T, 0, pw, 0, 0, 0, 0, 1, 1, 1, sm2, nsm, nm});
     }
   }
   return ME_OK;
@@ -2219,7 +2238,7 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
       k_acbm_seq<n_, m_, t_><<<cd.grid, kSeqThreads, cd.smem, s>>>(                            \
           fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                \
           pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl, pl->q, pl->bkey,        \
-          pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, 2, 1);                       \
+          pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, 2, 1, cd.early);             \
     st = !cd.lr || cd.ver == 2 ? ME_OK : ME_ERR_ARG;                                           \
   }
   ME_SEQ_NMT(X)
@@ -2229,7 +2248,7 @@ static int seq_enqueue(SeqPlan* pl, int c, const SeqFrames& fr, const SeqArgs& a
     k_acbm_seq<n_, m_, t_, 3><<<cd.grid, kSeqThreads, cd.smem, s>>>(                           \
         fr, a, W, H, p, pg, pl->refpad, pl->intra, pl->flags,                                  \
         pl->items + (size_t)cd.lag * pl->total, pl->total, pl->ctrl, pl->q, pl->bkey,          \
-        pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, cd.cps, cd.ppsm);              \
+        pl->bdone, pl->S, cd.pw, cd.split, cd.spec, cd.sgroups, cd.cps, cd.ppsm, cd.early);    \
     st = ME_OK;                                                                                \
   }
   ME_SEQ3_NMT(X)
