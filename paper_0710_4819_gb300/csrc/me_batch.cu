@@ -5,12 +5,15 @@
 // k_batch_intra (padded references and scaled Intra_SAD of every stream), then
 // one persistent kernel whose CTAs pull work items from a global counter:
 //   FSBM: items are groups of adjacent blocks of one block row of one stream,
-//         largest search ranges first;
+//         largest search ranges first (the per-group kernel, or the table-
+//         driven pipelined search of me_sequence.cu, whichever the tuner
+//         measured faster);
 //   ACBM: items are single blocks, ordered by anti-diagonal wave w = x + 2y
-//         (all streams' wave 0, then wave 1, ...).  A block waits (bounded) until
-//         its left, up-left, up and up-right neighbours are final, then runs
-//         PBM and the Sec. 3.2 test with one warp and, if it fails, the full
-//         search with the whole CTA, and publishes its vector.
+//         (all streams' wave 0, then wave 1, ...).  PBM warps claim blocks,
+//         run part a of PBM, queue a likely fallback's full search at once,
+//         wait (bounded) until the left, up-left, up and up-right neighbours
+//         are final, finish PBM and the Sec. 3.2 test and publish; search
+//         CTAs take queued blocks and search each in full.
 // Items are claimed in an order in which every dependency comes first, and a
 // CTA never waits for a later item, so the waits always end (each one is also
 // bounded in time and reports ME_ERR_TIMEOUT instead of hanging).

@@ -1,15 +1,18 @@
 // me_frame.cu -- the per-frame C ABI: padding, Intra_SAD, FSBM and ACBM for
 // one frame pair, with their kernels.
 //
-//   me_fsbm : one launch; full search of every block (Sec. 2.3): for 16x16
-//             blocks the pipelined persistent search of me_sequence.cu
-//             (k_fsbm_pipe), else k_fsbm
-//   me_acbm : k_acbm_prologue (padding, Intra_SAD), k_acbm_spec (the likely
-//             fallbacks guessed from the early predictors and searched in
-//             full, all at once), then one k_pbm_wave per anti-diagonal wave
-//             w = x + 2y of the block grid (PBM + the Sec. 3.2 test; a failing
-//             block takes its early search's result).  Wave w+1 starts after
-//             wave w, so every spatial predictor is final when it is read.
+//   me_fsbm : one launch; full search of every block (Sec. 2.3) in the form
+//             the autotuner picked for the shape: the pipelined searches of
+//             me_sequence.cu (k_fsbm_pipe, k_fsbm_pipe_tab) or the per-group
+//             k_fsbm
+//   me_acbm : tuned between the persistent kernel of me_sequence.cu over the
+//             one pair and the wave graph here: k_acbm_prologue (padding,
+//             Intra_SAD), k_acbm_spec (the likely fallbacks guessed from the
+//             early predictors and searched in full, all at once), then one
+//             k_pbm_wave per anti-diagonal wave w = x + 2y of the block grid
+//             (PBM + the Sec. 3.2 test; a failing block takes its early
+//             search's result).  Wave w+1 starts after wave w, so every
+//             spatial predictor is final when it is read.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,19 +1,27 @@
 // me_sequence.cu -- FSBM and ACBM over K consecutive frame pairs of one
 // sequence in one launch each.
 //
-// FSBM: the frame kernel with one grid row per pair (no dependencies between
-// pairs; the long grid also removes the last-wave tail of a single frame).
+// FSBM (Sec. 2.3): no dependencies between blocks or pairs.  Launch forms,
+// chosen per shape by the autotuner: the per-group kernel with one grid row
+// per pair (k_fsbm_seq); the pipelined persistent search for 16x16 blocks at
+// p <= 34 (k_fsbm_pipe: producer warps stage block groups' shifted windows
+// while consumer warps search, mbarrier hand-over); the table-driven
+// pipelined search for every shape and p <= 64 (k_fsbm_pipe_tab: groups of
+// adjacent blocks searched in bands of candidate rows, from a sequence or
+// from the batch's group table).
 //
-// ACBM: the causal order of the method (Sec. 2.2: spatial predictors must be
-// final in the current frame; temporal predictors come from the previous
-// frame's field) allows pairs to overlap: block (x, y) of pair k needs the
-// final vectors of its left, up-left, up and up-right neighbours in pair k
-// (anti-diagonal waves w-1 .. w-3, with w = x + 2y) and of its 3x3
-// neighbourhood in pair k-1 (waves up to w+3).  Ordering all blocks of all
-// pairs by w + 4k therefore puts every dependency first, and one persistent
-// launch walks the whole sequence with about 4 waves between consecutive
-// pairs instead of a full frame: the GPU sees many pairs in flight at once.
-// Each block waits (bounded in time) for its 4 + 9 predecessors' ready flags.
+// ACBM (Sec. 3.2): the causal order of the method (Sec. 2.2: spatial
+// predictors must be final in the current frame; temporal predictors come
+// from the previous frame's field) allows pairs to overlap: block (x, y) of
+// pair k needs the final vectors of its left, up-left, up and up-right
+// neighbours in pair k (anti-diagonal waves w-1 .. w-3, with w = x + 2y) and
+// of its 3x3 neighbourhood in pair k-1 (waves up to w+3).  Claiming all
+// blocks of all pairs in the order w + L*k (L >= 4) therefore puts every
+// dependency first, and one persistent launch (k_acbm_seq: PBM CTAs and
+// full-search CTAs) walks the whole sequence with L waves between
+// consecutive pairs instead of a full frame: the GPU sees many pairs in
+// flight at once.  Each block waits (bounded in time) for its 4 + 9
+// predecessors' flags.
 #include <cuda_runtime.h>
 
 #include <algorithm>
