@@ -194,7 +194,8 @@ __device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_ev
 // Warp-wide bounded wait of the persistent kernels: every lane with a
 // non-null flag f waits until its word carries epoch `want` (pub_word) and
 // gets the word back.  One load per lane first; then a single pending lane
-// polls (short back-off) and the others re-read once it is ready, so a
+// polls (sleeps of 32, then 64 ns: the chain of small frames is bound by
+// how soon a published flag is seen) and the others re-read once it is ready, so a
 // waiting warp keeps about one load in flight.  Gives up after `lim` SM
 // cycles (recording ME_ERR_TIMEOUT and `item` in *err / *err_item) or as soon
 // as *err is set by another wait.
@@ -220,7 +221,7 @@ __device__ __forceinline__ unsigned long long warp_wait_flags(const unsigned lon
       unsigned ns = 32;
       for (;;) {
         __nanosleep(ns);
-        if (ns < 256) ns *= 2;
+        if (ns < 64) ns *= 2;
         w = *reinterpret_cast<const volatile unsigned long long*>(f);
         if (pub_epoch(w) == want) break;
         if (*verr != 0) break;
