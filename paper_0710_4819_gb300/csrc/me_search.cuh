@@ -193,12 +193,13 @@ __device__ __forceinline__ int cta_role(int* started, int* sm_arr, int search_ev
 // ---------------------------------------------------------------------------
 // Warp-wide bounded wait of the persistent kernels: every lane with a
 // non-null flag f waits until its word carries epoch `want` (pub_word) and
-// gets the word back.  One load per lane first; then a single pending lane
-// polls (sleeps of 32, then 64 ns: the chain of small frames is bound by
-// how soon a published flag is seen) and the others re-read once it is ready, so a
-// waiting warp keeps about one load in flight.  Gives up after `lim` SM
-// cycles (recording ME_ERR_TIMEOUT and `item` in *err / *err_item) or as soon
-// as *err is set by another wait.
+// gets the word back.  One load per lane first; then every pending lane
+// re-reads its own flag after each short sleep (32, then 64 ns), all at
+// once: the dependency chain is bound by how soon a published flag is seen,
+// and polling one pending flag at a time added a round trip per flag.  The
+// decision to give up is lane 0's, for the whole warp: after `lim` SM
+// cycles (recording ME_ERR_TIMEOUT and `item` in *err / *err_item) or as
+// soon as *err is set by another wait.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long warp_wait_flags(const unsigned long long* f, int want,
                                                               int* err, int* err_item,
@@ -215,31 +216,26 @@ __device__ __forceinline__ unsigned long long warp_wait_flags(const unsigned lon
   unsigned pend = __ballot_sync(FULL, need);
   if (!pend) return w;
   const long long t0 = clock64();
+  unsigned ns = 32;
   while (pend) {
-    const int l = 31 - __clz((int)pend);
-    if (lane == l) {
-      unsigned ns = 32;
-      for (;;) {
-        __nanosleep(ns);
-        if (ns < 64) ns *= 2;
-        w = *reinterpret_cast<const volatile unsigned long long*>(f);
-        if (pub_epoch(w) == want) break;
-        if (*verr != 0) break;
-        if (clock64() - t0 > lim) {
-          atomicExch(err, (int)ME_ERR_TIMEOUT);
-          atomicExch(err_item, item);
-          break;
-        }
-      }
-      need = false;
-    }
-    __syncwarp();
-    if (*verr != 0) break;
+    __nanosleep(ns);
+    if (ns < 64) ns *= 2;
     if (need) {
       w = *reinterpret_cast<const volatile unsigned long long*>(f);
       need = pub_epoch(w) != want;
     }
+    int stop = 0;
+    if (lane == 0) {
+      if (*verr != 0) {
+        stop = 1;
+      } else if (clock64() - t0 > lim) {
+        atomicExch(err, (int)ME_ERR_TIMEOUT);
+        atomicExch(err_item, item);
+        stop = 1;
+      }
+    }
     pend = __ballot_sync(FULL, need);
+    if (__shfl_sync(FULL, stop, 0)) break;
   }
   return w;
 }

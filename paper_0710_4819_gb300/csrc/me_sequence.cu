@@ -955,7 +955,7 @@ __device__ void seq_search_group(const SeqFrames& fr, const SeqArgs& a, int W, i
           }
         }
         __nanosleep(nsl);
-        if (nsl < 256) nsl *= 2;
+        if (nsl < 64) nsl *= 2;   // a queued search starts on the chain's clock
       }
       *s_item = got;
     }
@@ -1267,7 +1267,7 @@ __global__ void __launch_bounds__(kSeqThreads, MINB) k_acbm_seq(SeqFrames fr, Se
             }
           }
           __nanosleep(ns);
-          if (ns < 256) ns *= 2;
+          if (ns < 64) ns *= 2;   // a queued search starts on the chain's clock
         }
         s_item = got;
       }
