@@ -261,7 +261,6 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       const int bx = b % BW, by = b / BW;
       const PbmWin wg = pbm_stage<N, M>(a.cur, s.refpad, s.pg, s.W, s.p, bx * N, by * M, curs, win);
       const uint32_t ix = s.intra[b];
-      if (lane == 0) nxt = atomicAdd(&ctrl->next, 1);
       // predictors: lanes 0-3 the spatial ones (final vectors of this step,
       // carried by their flags), lanes 4-12 the previous field's 3x3, lane 13
       // the zero vector
@@ -288,7 +287,6 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
       } else if (lane == 13) {
         valid = true;
       }
-      if (lane == 0 && nxt < total) inxt = items[nxt];
       // the previous field's and the zero predictors first (no wait); a block
       // that fails both conditions with them alone has its full search queued
       // at once (speculatively), while the warp waits for its spatial
@@ -349,6 +347,9 @@ __global__ void __launch_bounds__(256, 2) k_acbm_persist(const BShape* __restric
         }
         __threadfence();
         atomicAdd(&ctrl->pbm_done, 1);
+        // the next claim, once this block is out of the warp's hands
+        nxt = atomicAdd(&ctrl->next, 1);
+        inxt = nxt < total ? items[nxt] : 0;
       }
       __syncwarp();
     }
