@@ -1751,7 +1751,8 @@ static std::vector<int> seq_Ts(int N, int M, int p) {
 }
 
 // Adds the low-register form of k_acbm_seq (run length 8, the build for
-// three CTAs per SM): one PBM and two search CTAs per SM.  (Measured at 1080p
+// three CTAs per SM): one PBM and two search CTAs per SM, at claim-order lags
+// of 5, 4 and 6 waves.  (Measured at 1080p
 // p=32 over 59 pairs: 5.80-5.90 ms against 5.85-5.87 for the best two-CTA
 // form; two PBM CTAs per SM 7.1, two search groups per search CTA 6.2-6.3.)
 template <int N, int M>
@@ -1760,8 +1761,8 @@ static int seq_add_cands3(SeqPlan* pl, int nsm, int spec) {
   if constexpr (seq3_built<N, M, T>()) {
     const int p = pl->p;
     const size_t per = (size_t)4 * (pbm_win_words(N, M, p) + M * (N / 4));
-    struct Form3 { int cps, ppsm, split, sg; };
-    const Form3 f3s[] = {{3, 1, 0, 1}};
+    struct Form3 { int cps, ppsm, split, sg, lag; };
+    const Form3 f3s[] = {{3, 1, 0, 1, 1}, {3, 1, 0, 1, 0}, {3, 1, 0, 1, 2}};
     for (const Form3& f : f3s) {
       const size_t srch = 4 * (size_t)f.sg * seq_group_words<N, M, T>(p, kSeqThreads / f.sg);
       const int pw = (int)std::min<size_t>(kSeqThreads / 32, kSeq3SmemCap / per);
@@ -1777,12 +1778,13 @@ static int seq_add_cands3(SeqPlan* pl, int nsm, int spec) {
       if (per_sm < f.cps) continue;
       char nm[80];
       std::snprintf(nm, sizeof(nm), "seq3 T=%d pbm=%d/%d split=%d spec=%d groups=%d lag=%d", T,
-                    f.ppsm, f.cps, f.split, spec, f.sg, kSeqLags[1]);
-      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, 1, sm3,
-                                        f.cps * nsm, nm});
+                    f.ppsm, f.cps, f.split, spec, f.sg, kSeqLags[f.lag]);
+      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, f.lag, 1, f.cps, f.ppsm, 1,
+                                        sm3, f.cps * nsm, nm});
       // and with the ring evaluated after the spatial predictors only
-      pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, 1, 1, f.cps, f.ppsm, 0, sm3,
-                                        f.cps * nsm, std::string(nm) + " ring=late"});
+      if (f.lag == 1)
+        pl->cands.push_back(SeqPlan::Cand{1, T, f.split, pw, spec, f.sg, f.lag, 1, f.cps, f.ppsm, 0,
+                                          sm3, f.cps * nsm, std::string(nm) + " ring=late"});
     }
   }
   return ME_OK;
